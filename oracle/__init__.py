@@ -1,0 +1,228 @@
+"""FP64 CPU oracle of the 3D long-characteristics formal solution and ALI.
+
+TEST INFRASTRUCTURE. Only the tests, ``__graft_entry__.smoke()`` and the CPU
+legs of ``bench.py`` may import this package. It shares no code with the CUDA
+path (``paper_2102_01734_gb300``) and imports nothing from it.
+
+The C library (``rt3d_oracle.c``) holds the arithmetic; this module only
+marshals numpy arrays, plus two plain linear-algebra helpers used as pins:
+the brute-force Lambda matrix built column by column from the formal solution
+(Eq. frmsol, J = Lambda S) and the direct dense solve of the scattering
+problem that the ALI iteration (Eqs. alisol, alo) converges to.
+
+Array convention: grids are numpy arrays of shape (nz, ny, nx), x fastest,
+so the flat index is v = x + nx (y + ny z). Lambda* is returned as (N, 27)
+with d = (dx+1) + 3 (dy+1) + 9 (dz+1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        c_int, c_double, c_long = ctypes.c_int, ctypes.c_double, ctypes.c_long
+        lib.orc_directions.argtypes = [c_int, c_int, _dp, _dp, _dp, _dp]
+        lib.orc_trace_cart.argtypes = [c_int, c_int, c_int, _dp, c_int, c_int, c_int, _ip, _dp]
+        lib.orc_trace_cart.restype = c_int
+        lib.orc_kmax_cart.argtypes = [c_int, c_int, c_int, _dp]
+        lib.orc_kmax_cart.restype = c_int
+        lib.orc_e012.argtypes = [c_double, _dp, _dp, _dp]
+        lib.orc_coef.argtypes = [c_int, c_double, c_double, _dp, _dp, _dp, _dp]
+        lib.orc_ray_fs.argtypes = [c_int, _dp, _dp, c_double, c_int, _dp, _dp, _dp, _dp, _dp]
+        lib.orc_fs_cart.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp,
+                                    c_double, _dp, c_double, _dp, _dp, _dp, c_int]
+        lib.orc_fs_cart.restype = c_int
+        lib.orc_fs_cart_voxel.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp,
+                                          c_double, _dp, c_double, _dp, c_long, c_int, c_int,
+                                          _dp, _dp]
+        lib.orc_fs_cart_voxel.restype = c_int
+        lib.orc_os_jacobi.argtypes = [c_int, c_int, c_int, _dp, _dp, _dp, _dp, c_int, c_double]
+        lib.orc_os_jacobi.restype = c_int
+        lib.orc_ali_solve.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp, _dp,
+                                      c_double, _dp, c_double, _dp, _dp, c_double, c_int, c_int,
+                                      c_double, c_int, _dp, _dp]
+        lib.orc_ali_solve.restype = c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def default_threads() -> int:
+    return max(1, min(os.cpu_count() or 1, 64))
+
+
+def directions(ntheta: int, nphi: int):
+    """A1 direction set: (mu, phi, dir (n,3), w), angle index o = i*nphi + j."""
+    lib = _load()
+    n = ntheta * nphi
+    mu, phi, w = np.zeros(n), np.zeros(n), np.zeros(n)
+    d = np.zeros((n, 3))
+    lib.orc_directions(ntheta, nphi, _ptr(mu), _ptr(phi), _ptr(d), _ptr(w))
+    return mu, phi, d, w
+
+
+def trace_cart(shape, d, x0: int = 0, y0: int = 0):
+    """A2: voxel indices and chords of the characteristic of direction d from
+    the centre of inflow-face cell (x0, y0). shape = (nz, ny, nx)."""
+    lib = _load()
+    nz, ny, nx = shape
+    d = _f64(d)
+    kmax = lib.orc_kmax_cart(nx, ny, nz, _ptr(d))
+    vox = np.zeros(kmax, dtype=np.int32)
+    ln = np.zeros(kmax)
+    K = lib.orc_trace_cart(nx, ny, nz, _ptr(d), x0, y0, kmax,
+                           vox.ctypes.data_as(_ip), _ptr(ln))
+    if K < 0:
+        raise RuntimeError(f"trace failed ({K})")
+    return vox[:K].copy(), ln[:K].copy()
+
+
+def e012(u: float):
+    lib = _load()
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib.orc_e012(float(u), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return a.value, b.value, c.value
+
+
+def coef(parabolic: bool, u: float, w: float):
+    """(E, alpha, beta, gamma) of one interval."""
+    lib = _load()
+    out = [ctypes.c_double() for _ in range(4)]
+    lib.orc_coef(int(parabolic), float(u), float(w), *[ctypes.byref(o) for o in out])
+    return tuple(o.value for o in out)
+
+
+def ray_fs(chil, S, I0: float, parabolic: bool):
+    """A4+A5 along one characteristic: returns (I, E, alpha, beta, gamma)."""
+    lib = _load()
+    chil, S = _f64(chil), _f64(S)
+    K = chil.size
+    outs = [np.zeros(K) for _ in range(5)]
+    lib.orc_ray_fs(K, _ptr(chil), _ptr(S), float(I0), int(parabolic), *[_ptr(o) for o in outs])
+    return tuple(outs)
+
+
+def _bc_args(shape, bc):
+    nz, ny, nx = shape
+    bc = bc or {}
+    top = bc.get("I_top", 0.0)
+    bot = bc.get("I_bottom", 0.0)
+    top_face = None if np.isscalar(top) else _f64(np.broadcast_to(top, (ny, nx)))
+    bot_face = None if np.isscalar(bot) else _f64(np.broadcast_to(bot, (ny, nx)))
+    return (float(top) if top_face is None else 0.0, top_face,
+            float(bot) if bot_face is None else 0.0, bot_face)
+
+
+def fs_cart(chi, S, ntheta: int, nphi: int, parabolic: bool = False, bc=None,
+            lstar: bool = False, nthreads: int | None = None):
+    """A2-A7: J = Lambda S on the periodic box (and Lambda* as (N,27))."""
+    lib = _load()
+    chi, S = _f64(chi), _f64(S)
+    nz, ny, nx = chi.shape
+    J = np.zeros(chi.shape)
+    L = np.zeros((chi.size, 27)) if lstar else None
+    t, tf, b, bf = _bc_args(chi.shape, bc)
+    err = lib.orc_fs_cart(nx, ny, nz, ntheta, nphi, int(parabolic), _ptr(chi), _ptr(S),
+                          t, _ptr(tf), b, _ptr(bf), _ptr(J), _ptr(L),
+                          nthreads or default_threads())
+    if err:
+        raise RuntimeError(f"oracle formal solution failed ({err})")
+    return (J, L) if lstar else J
+
+
+def fs_cart_voxel(chi, S, ntheta: int, nphi: int, v: int, parabolic: bool = False, bc=None,
+                  lstar: bool = False, angles=None):
+    """J_v (and the Lambda* row of v) for one voxel, all or a range of angles."""
+    lib = _load()
+    chi, S = _f64(chi), _f64(S)
+    nz, ny, nx = chi.shape
+    Jv = ctypes.c_double()
+    row = np.zeros(27) if lstar else None
+    lo, hi = angles if angles is not None else (0, ntheta * nphi)
+    t, tf, b, bf = _bc_args(chi.shape, bc)
+    err = lib.orc_fs_cart_voxel(nx, ny, nz, ntheta, nphi, int(parabolic), _ptr(chi), _ptr(S),
+                                t, _ptr(tf), b, _ptr(bf), int(v), int(lo), int(hi),
+                                ctypes.byref(Jv), _ptr(row))
+    if err:
+        raise RuntimeError(f"oracle voxel formal solution failed ({err})")
+    return (Jv.value, row) if lstar else Jv.value
+
+
+def os_jacobi(lstar, eps, r, max_sweeps: int = 50, tol: float = 1e-3):
+    """A8: Jacobi solve of [1 - L*(1-eps)] dJ = r. Returns (dJ, sweeps)."""
+    lib = _load()
+    eps, r = _f64(eps), _f64(r)
+    nz, ny, nx = r.shape
+    L = _f64(lstar)
+    dJ = np.zeros(r.shape)
+    m = lib.orc_os_jacobi(nx, ny, nz, _ptr(L), _ptr(eps), _ptr(r), _ptr(dJ), max_sweeps, tol)
+    return dJ, m
+
+
+def ali_solve(chi, eps, B, ntheta: int, nphi: int, parabolic: bool = False, bc=None, J0=None,
+              tol: float = 1e-13, max_iter: int = 500, max_sweeps: int = 50,
+              sweep_tol: float = 1e-3, nthreads: int | None = None):
+    """A8+A9: ALI iteration to rel dJ < tol. Returns (J, iterations, history, lstar)."""
+    lib = _load()
+    chi, eps, B = _f64(chi), _f64(eps), _f64(B)
+    nz, ny, nx = chi.shape
+    J = _f64(np.zeros(chi.shape) if J0 is None else J0).copy()
+    L = np.zeros((chi.size, 27))
+    hist = np.zeros(max_iter)
+    t, tf, b, bf = _bc_args(chi.shape, bc)
+    it = lib.orc_ali_solve(nx, ny, nz, ntheta, nphi, int(parabolic), _ptr(chi), _ptr(eps),
+                           _ptr(B), t, _ptr(tf), b, _ptr(bf), _ptr(J), tol, max_iter,
+                           max_sweeps, sweep_tol, nthreads or default_threads(), _ptr(L),
+                           _ptr(hist))
+    if it <= -1000:
+        raise RuntimeError(f"oracle ALI failed ({it})")
+    return J, it, hist[:abs(it)], L
+
+
+def lambda_matrix(chi, ntheta: int, nphi: int, parabolic: bool = False,
+                  nthreads: int | None = None):
+    """Brute-force Lambda: column u is J(e_u) with zero boundary intensity."""
+    N = chi.size
+    M = np.zeros((N, N))
+    e = np.zeros(chi.shape)
+    flat = e.reshape(-1)
+    for u in range(N):
+        flat[:] = 0.0
+        flat[u] = 1.0
+        M[:, u] = fs_cart(chi, e, ntheta, nphi, parabolic, bc=None,
+                          nthreads=nthreads).reshape(-1)
+    return M
+
+
+def direct_solve(chi, eps, B, ntheta: int, nphi: int, parabolic: bool = False, bc=None):
+    """Fixed point of the scattering problem, J = Lambda((1-eps)J + eps B) + J_bc,
+    by a dense LU solve of (1 - Lambda (1-eps)) J = Lambda(eps B) + J_bc."""
+    M = lambda_matrix(chi, ntheta, nphi, parabolic)
+    eps_f, B_f = _f64(eps).reshape(-1), _f64(B).reshape(-1)
+    Jbc = fs_cart(chi, np.zeros(chi.shape), ntheta, nphi, parabolic, bc=bc).reshape(-1)
+    rhs = M @ (eps_f * B_f) + Jbc
+    A = np.eye(chi.size) - M * (1.0 - eps_f)[None, :]
+    return np.linalg.solve(A, rhs).reshape(chi.shape)

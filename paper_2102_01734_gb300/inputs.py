@@ -1,0 +1,86 @@
+"""Seeded synthetic atmospheres shaped like the paper's test cases.
+
+Input generation only: nothing here computes any step of the formal solution
+or of the ALI iteration. Both the CUDA path and the CPU oracle are fed from
+these arrays.
+
+Workloads (they stand in for the paper's PBC test atmosphere, Sec. 3.1; no
+dataset is involved):
+
+* ``vertical_chi(nz)``: chi(z) = 10^(-4 + 6 (nz-1-z)/(nz-1)) per unit length,
+  z = 0 the inner (bottom) layer, so the outer layer has chi = 1e-4 and the
+  inner one 1e2 (per-voxel vertical optical depth 1e-4 .. 1e2).
+* ``powerlaw_field(shape, seed)``: Gaussian random field with power spectrum
+  P(k) ~ k^-3: seeded white noise, FFT, amplitude times |k|^-3/2, k = 0 mode
+  removed, inverse FFT, scaled to unit standard deviation and clipped to
+  +-4.5 so that B = 1 + 0.2 g stays positive.
+* ``cartesian_config(...)``: chi = vertical_chi * exp(0.5 g) (sigma_ln = 0.5),
+  B = 1 + 0.2 g, uniform eps; boundary: no incoming intensity at the top,
+  I = B of the entered bottom voxel at the bottom.
+
+Arrays have shape (nz, ny, nx), x fastest.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def vertical_chi(nz: int) -> np.ndarray:
+    z = np.arange(nz, dtype=np.float64)
+    if nz == 1:
+        return np.full(1, 1e-4)
+    return 10.0 ** (-4.0 + 6.0 * (nz - 1 - z) / (nz - 1))
+
+
+def powerlaw_field(shape, seed: int, slope: float = -3.0, clip: float = 4.5) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal(shape)
+    f = np.fft.fftn(white)
+    ks = np.meshgrid(*[np.fft.fftfreq(n) for n in shape], indexing="ij")
+    k = np.sqrt(sum(kk * kk for kk in ks))
+    amp = np.zeros_like(k)
+    nz = k > 0
+    amp[nz] = k[nz] ** (slope / 2.0)
+    g = np.real(np.fft.ifftn(f * amp))
+    g -= g.mean()
+    g /= g.std()
+    return np.clip(g, -clip, clip)
+
+
+def cartesian_config(n, eps: float, seed: int | None = None, sigma_ln: float = 0.5,
+                     b_amp: float = 0.2):
+    """(chi, eps, B, bc) on a box of n = (nx, ny, nz) voxels (or an int)."""
+    if np.isscalar(n):
+        n = (int(n),) * 3
+    nx, ny, nz = n
+    shape = (nz, ny, nx)
+    chi = np.broadcast_to(vertical_chi(nz)[:, None, None], shape).copy()
+    if seed is None:
+        B = np.ones(shape)
+    else:
+        g = powerlaw_field(shape, seed)
+        chi = chi * np.exp(sigma_ln * g)
+        B = 1.0 + b_amp * g
+    epsa = np.full(shape, float(eps))
+    bc = {"I_top": 0.0, "I_bottom": B[0].copy()}
+    return chi, epsa, B, bc
+
+
+# Named workloads (sizes of the benchmark configurations).
+CONFIGS = {
+    # plain method, FP64: 33^3 box, 8 x 16 angles, linear interpolation
+    "box33_fp64": dict(n=33, eps=1e-2, seed=None, ntheta=8, nphi=16, parabolic=False),
+    # 129^3 box with the k^-3 lognormal field, 32 x 64 angles, parabolic
+    "box129_field": dict(n=129, eps=1e-6, seed=1, ntheta=32, nphi=64, parabolic=True),
+    # 97^3 box, 16 x 32 angles, batched wavelengths
+    "box97_batched": dict(n=97, eps=None, seed=1, ntheta=16, nphi=32, parabolic=True),
+}
+
+
+def batched_wavelengths(nlambda: int, seed: int = 3):
+    """Per-wavelength eps (log-uniform in [1e-8, 1e-1]) and opacity scale
+    10^U(-3, 3), seeded."""
+    rng = np.random.default_rng(seed)
+    eps = 10.0 ** rng.uniform(-8.0, -1.0, nlambda)
+    scale = 10.0 ** rng.uniform(-3.0, 3.0, nlambda)
+    return eps, scale
