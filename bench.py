@@ -1,0 +1,327 @@
+"""Benchmark of the long-characteristics formal solution + ALI on one GB300.
+
+A step is one converged solve (all steps of the path: tracer cache reused,
+FP32 formal solutions with the Lambda* band built in the first iteration,
+FP64 Jacobi OS solves, FP64 defect correction and FP64 certification) of the
+box129_field workload: 129^3 periodic box, 32 x 64 solid angles, parabolic
+interpolation, eps = 1e-6, chi = vertical profile x lognormal k^-3 field
+(seed 1), B = 1 + 0.2 g, I_top = 0, I_bottom = B, from J = B to an estimated
+relative error of 1e-8 against FP64.
+
+value = ray-segment updates (all formal solutions of the timed steps) per
+second of the timed region; solves_per_s is the second metric.
+
+--impl reference times the FP64 CPU oracle on a bounded angle sample of the
+same workload (the reference arm of this build: a plain CPU program).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("ray-segment updates/s (formal sol.); converged solves/s at rel ΔJ≤1e-8 vs FP64")
+UNIT = "ray-segment updates/s"
+WORKLOAD = "box129_field"
+DESCR = ("129^3 periodic box, 32x64 angles, parabolic, eps=1e-6, chi=10^(-4+6(nz-1-z)/(nz-1))"
+         " x exp(0.5 g), g ~ k^-3 Gaussian field (seed 1), B=1+0.2g; FP32 formal solution,"
+         " FP64 ALI/Jacobi/refinement/certification; converged to est. rel error 1e-8 from J=B")
+# algorithmic FP32-pipe operations per parabolic segment (see the design doc:
+# interval optical depth, exp, 1/(u+w), 1/w, a, a0, d, s, q, coefficients,
+# intensity update, J weight)
+OPS_PER_SEGMENT = 28
+SMS = 152
+LANES = 128
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_info():
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_sample(chi, S, bc, ntheta, nphi, angles):
+    """Time the FP64 CPU oracle's formal solution over a list of angles;
+    returns (segments/s, seconds, threads, segments)."""
+    import oracle
+
+    mu, phi, d, w = oracle.directions(ntheta, nphi)
+    nz, ny, nx = chi.shape
+    seg = sum(len(oracle.trace_cart(chi.shape, d[o])[0]) for o in angles) * nx * ny
+    threads = oracle.default_threads()
+    t = time.perf_counter()
+    oracle.fs_cart_angles(chi, S, ntheta, nphi, angles, True, bc, nthreads=threads)
+    dt = time.perf_counter() - t
+    return seg / dt, dt, threads, seg
+
+
+def sample_angles(ntheta, nphi, count):
+    """`count` solid angles spread over theta and phi."""
+    n = ntheta * nphi
+    return [int(round(i * n / count + (i % nphi))) % n for i in range(count)]
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2102_01734_gb300 import inputs
+
+    cfg = inputs.CONFIGS[WORKLOAD]
+    chi, eps, B, bc = inputs.cartesian_config(cfg["n"], cfg["eps"], seed=cfg["seed"])
+    angles = sample_angles(cfg["ntheta"], cfg["nphi"], args.ref_angles)
+    rates, secs = [], []
+    for i in range(args.warmup + args.steps):
+        rate, dt, threads, seg = oracle_sample(chi, B, bc, cfg["ntheta"], cfg["nphi"], angles)
+        if i >= args.warmup:
+            rates.append(rate)
+            secs.append(dt)
+    value = float(np.sum([r * s for r, s in zip(rates, secs)]) / np.sum(secs))
+    cores, model = cpu_info()
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "description": DESCR, "parallelism": "cpu-openmp"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"formal solution (parabolic, FP64) over {len(angles)} of "
+                                   f"{cfg['ntheta'] * cfg['nphi']} solid angles of the "
+                                   f"workload per step; cpu: {model} ({cores} cores)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2102_01734_gb300 import build, inputs, rt3d
+
+    rank, world, local = dist_env()
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = inputs.CONFIGS[WORKLOAD]
+    n = cfg["n"]
+    # weak scaling: every rank solves its own atmosphere (independent problems)
+    chi, eps, B, bc = inputs.cartesian_config(n, cfg["eps"], seed=cfg["seed"] + rank)
+    g = rt3d.Grid(n, cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+    info = g.info()
+    seg_per_fs = info["segments"]
+    tchi, teps, tB = (torch.from_numpy(a).to(dev) for a in (chi, eps, B))
+    tbc = {"I_top": 0.0, "I_bottom": torch.from_numpy(bc["I_bottom"]).to(dev)}
+    J = torch.empty_like(tB)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one(timed_stats):
+        J.copy_(tB)
+        st = g.solve(tchi, teps, tB, tbc, J, tol=args.tol, max_iter=args.max_iter)
+        timed_stats.append(st)
+
+    warm = []
+    for _ in range(args.warmup):
+        one(warm)
+    sampler = ClockSampler(local)
+    stats = []
+    times = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between steps (256 MB > 129 MB L2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one(stats)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clocks = sampler.stop()
+    total = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+        torch.distributed.barrier()
+    fs_count = sum(s["fs_fp32"] + s["fs_fp64"] for s in stats)
+    segs = fs_count * seg_per_fs * world
+    value = segs / total
+    solves_per_s = args.steps * world / total
+    fs32_ms = sum(s["fs32_ms"] for s in stats)
+    n32 = sum(s["fs_fp32"] for s in stats)
+    fs_rate = n32 * seg_per_fs / (fs32_ms / 1e3) if fs32_ms > 0 else 0.0
+    peaks, peak_kind = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SMS * LANES * sm_max * 1e6
+    achieved = OPS_PER_SEGMENT * fs_rate
+    launches = int(sum(s["launches"] for s in stats))
+
+    # end to end through the C ABI with pinned host buffers (copies inside)
+    hchi = torch.from_numpy(chi).pin_memory()
+    heps = torch.from_numpy(eps).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hbot = torch.from_numpy(bc["I_bottom"]).pin_memory()
+    hJ = torch.empty(chi.shape, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    e2e_segs = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hJ.copy_(hB)
+        st = g.solve(hchi, heps, hB, {"I_top": 0.0, "I_bottom": hbot}, hJ, tol=args.tol,
+                     max_iter=args.max_iter)
+        e2e_segs += (st["fs_fp32"] + st["fs_fp64"]) * seg_per_fs
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    N = chi.size
+    h2d = (4 * N + hbot.numel()) * 8
+    d2h = N * 8
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        angles = sample_angles(cfg["ntheta"], cfg["nphi"], args.ref_angles)
+        rate, dt, threads, seg = oracle_sample(chi, B, bc, cfg["ntheta"], cfg["nphi"], angles)
+        cores, model = cpu_info()
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"FP64 oracle formal solution (parabolic) over {len(angles)} of "
+                         f"{cfg['ntheta'] * cfg['nphi']} solid angles of the workload, "
+                         f"{seg:.3g} segments in {dt:.1f} s; cpu: {model} ({cores} cores)"}
+    last = stats[-1]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "description": DESCR, "grid": [n, n, n],
+                   "angles": [cfg["ntheta"], cfg["nphi"]], "segments_per_fs": seg_per_fs,
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "solves_per_s": solves_per_s,
+        "solve": {"iterations": last["iterations"], "fs_fp32": last["fs_fp32"],
+                  "fs_fp64": last["fs_fp64"], "residual64": last["residual64"],
+                  "est_error": last["est_error"]},
+        "fs_kernel_segments_per_s": fs_rate,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops,
+                     "traffic": None, "kernel": "fs_kernel<float, parabolic>",
+                     "peak_source": f"{SMS} SMs x {LANES} FP32 lanes x {sm_max:.0f} MHz "
+                                    f"(sm_max_mhz, {peak_kind})",
+                     "ops_per_segment": OPS_PER_SEGMENT},
+        "e2e": {"value": e2e_segs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-iter", type=int, default=4000)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--ref-angles", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * rt3d.h -- C ABI of the GB300 (sm_103a) long-characteristics 3D radiative
+ * transfer library: formal solution, non-local Lambda* band and
+ * operator-splitting (ALI) solver of Hauschildt & Baron, "A 3D radiative
+ * transfer framework XII" (arXiv:2102.01734).
+ *
+ * Problem (Sec. 2.1, Eq. 1; Sec. 2.2, Eqs. frmsol, alisol, alodef, alo):
+ *   n . grad I = chi (S - I),  J = Lambda S,  S = (1 - eps) J + eps B,
+ *   [1 - Lambda*(1 - eps)] (J_new - J_old) = J_FS - J_old.
+ *
+ * Grid: a Cartesian box of nx * ny * nz unit voxels, periodic in x and y;
+ * z = 0 is the inner (bottom) boundary layer, z = nz-1 the outer (top) one
+ * (Sec. 3.1). Every voxel holds one value of each quantity (Sec. 2).
+ *
+ * Layouts. Every per-voxel array is double[N], N = nx*ny*nz, x fastest:
+ * v = x + nx*(y + ny*z). Lambda* arrays are double[27][N] (offset-major):
+ * element [d][v] = dJ_v / dS_{v+d}, with d = (dx+1) + 3(dy+1) + 9(dz+1),
+ * dx,dy periodic, and 0 where v+d lies outside the box in z. Face arrays are
+ * double[ny][nx] (index x + nx*y).
+ *
+ * Pointers. Every array argument may be host or device memory; the library
+ * tells them apart with cudaPointerGetAttributes and stages host arrays
+ * through device buffers owned by the grid (copies on the grid's stream).
+ * The caller owns all arrays it passes; the library owns the grid, its
+ * geometry cache and its work buffers. Calls on one grid are not thread
+ * safe. All work is issued on the stream given in the descriptor; a call
+ * returns after its results are complete (it synchronises that stream).
+ *
+ * Errors. Every entry point returns an rt3d_status and never aborts;
+ * rt3d_last_error() gives a thread-local message for the last failure.
+ */
+#ifndef RT3D_H
+#define RT3D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt3d_grid rt3d_grid; /* opaque, library-owned */
+
+typedef enum {
+    RT3D_OK = 0,
+    RT3D_EINVAL = 1,         /* bad descriptor, size or argument */
+    RT3D_ENOMEM = 2,         /* device or host allocation failed */
+    RT3D_ECUDA = 3,          /* a CUDA call failed */
+    RT3D_ENOTCONVERGED = 4,  /* iteration cap reached; J holds the last iterate */
+    RT3D_ETIMEOUT = 5,       /* a bounded device-side wait ran out */
+    RT3D_ENUMERIC = 6        /* NaN/Inf met in a residual or change */
+} rt3d_status;
+
+enum { RT3D_CARTESIAN_PERIODIC_XY = 0 };
+enum { RT3D_LINEAR = 0, RT3D_PARABOLIC = 1 };
+enum {
+    RT3D_FP64 = 0,            /* formal solution and ALI in FP64 */
+    RT3D_FP32_FS_FP64_ALI = 1 /* FP32 formal solution, FP64 ALI/residual, FP64 refinement */
+};
+
+typedef struct {
+    int geometry;     /* RT3D_CARTESIAN_PERIODIC_XY */
+    int n[3];         /* nx, ny, nz: 4 <= nx, ny <= 2047, 1 <= nz <= 1023 */
+    int ntheta, nphi; /* direction set: mu_i = -1 + (2i+1)/ntheta,
+                         phi_j = (2j+1) pi / nphi, weight 1/(ntheta nphi) */
+    int interp;       /* RT3D_LINEAR or RT3D_PARABOLIC source interpolation */
+    int precision;    /* RT3D_FP64 or RT3D_FP32_FS_FP64_ALI */
+    int nlambda;      /* reserved: must be 0 or 1 */
+    void *cuda_stream;/* cudaStream_t to run on, or NULL for the legacy stream */
+} rt3d_grid_desc;
+
+/* Boundary intensities (Sec. 3.1: I = 0 incoming at the outer boundary; the
+ * inner boundary is given by the caller, e.g. I = B of the entered voxel).
+ * A characteristic with mu < 0 enters through the top face, one with mu > 0
+ * through the bottom face, at the centre of face cell (x0, y0). A non-NULL
+ * face array (double[ny][nx], host or device) overrides the scalar. */
+typedef struct {
+    double I_top;
+    double I_bottom;
+    const double *I_top_face;
+    const double *I_bottom_face;
+} rt3d_bc;
+
+typedef struct {
+    int iterations;     /* ALI iterations of the main loop */
+    int fs_fp32;        /* formal solutions done in FP32 */
+    int fs_fp64;        /* formal solutions done in FP64 */
+    int jacobi_sweeps;  /* Jacobi sweeps of all OS solves */
+    double rel_change;  /* last max_v |dJ_v| / |J_v| */
+    double residual64;  /* max_v |J_FS64(S(J))_v - J_v| / |J_v| of the returned J
+                           (FP64 formal solution; 0 if not computed) */
+    double est_error;   /* estimated max relative error of the returned J */
+    double seconds;     /* wall time of the call */
+    double fs32_ms;     /* summed device time of the FP32 formal-solution kernels
+                           (CUDA events on the grid's stream) */
+    double fs64_ms;     /* same for the FP64 formal-solution kernels */
+    long long launches; /* kernels launched by the call */
+} rt3d_solve_stats;
+
+typedef struct {
+    int nangles;              /* ntheta * nphi */
+    int kmax;                 /* longest characteristic, points */
+    long long segments;       /* ray-segment updates per formal solution:
+                                 nx*ny * sum over angles of points per ray */
+    long long device_bytes;   /* device memory held by the grid */
+} rt3d_grid_info;
+
+/* Creates a grid: builds the direction set (host, FP64) and traces one
+ * characteristic per solid angle on the device (Sec. 4, the tracker; the
+ * geometry cache of Sec. 4.1). All nx*ny characteristics of an angle are
+ * integer translates of that one. Returns RT3D_EINVAL for sizes outside the
+ * limits above, a zero direction component along z (impossible with this
+ * direction set), or a Lambda* window longer than 9 points. */
+rt3d_status rt3d_grid_create(const rt3d_grid_desc *desc, rt3d_grid **out);
+
+/* Releases the grid and all device memory it holds. NULL is ignored. */
+void rt3d_grid_destroy(rt3d_grid *grid);
+
+rt3d_status rt3d_grid_get_info(const rt3d_grid *grid, rt3d_grid_info *info);
+
+/* The traced characteristic of solid angle `angle` from face cell (0,0):
+ * points K (in/out: capacity on input), voxel indices vox[K] and FP64 chords
+ * len[K], in host memory. Tracer rule: crossing parameters (m - 1/2)/|d_x|,
+ * (m - 1/2)/|d_y| and m/|mu|, each one IEEE division; ties advance all tied
+ * axes; chord = difference of consecutive crossing parameters. */
+rt3d_status rt3d_grid_template(const rt3d_grid *grid, int angle, int *K, int32_t *vox,
+                               double *len);
+
+/* Formal solution J = Lambda S (Eq. frmsol) over all solid angles, in the
+ * grid's precision (FP64, or FP32 for RT3D_FP32_FS_FP64_ALI; results are
+ * returned as double either way):
+ *   J_v = sum_Omega w (sum_{k in v} l_k I_k) / (sum_{k in v} l_k),
+ *   I_k = exp(-dtau) I_{k-1} + alpha S_{k-1} + beta S_k + gamma S_{k+1}.
+ * chi > 0 (per unit length) and S: double[N]. J_out: double[N] (written).
+ * lstar_out: nullable double[27][N]; when given, the passage-local Lambda*
+ * band (Sec. 4, "non-local Lambda*") is built as well. bc: nullable (zero
+ * incoming intensity). */
+rt3d_status rt3d_formal_solution(rt3d_grid *grid, const double *chi, const double *S,
+                                 const rt3d_bc *bc, double *J_out, double *lstar_out);
+
+/* OS linear system of Eq. alo for the correction dJ = J_new - J_old:
+ * [1 - Lambda*(1 - eps)] dJ = r, by Jacobi sweeps (Sec. 4, OS iteration):
+ * dJ^0 = r / diag; stops when max|dJ^{m+1} - dJ^m| <= tol * max|dJ^{m+1}|
+ * or after max_sweeps (1..256). lstar: double[27][N] as written by
+ * rt3d_formal_solution; eps, r, dJ_out: double[N]. sweeps_out (nullable,
+ * host) receives the number of sweeps. */
+rt3d_status rt3d_os_solve(rt3d_grid *grid, const double *lstar, const double *eps,
+                          const double *r, double *dJ_out, int max_sweeps, double tol,
+                          int *sweeps_out);
+
+/* One ALI iteration (Eqs. alisol, alo): S = (1-eps) J + eps B; J_FS =
+ * Lambda S; Jacobi solve (<= 50 sweeps, relative tolerance 1e-3) of
+ * [1 - Lambda*(1-eps)] dJ = J_FS - J; J += dJ. Lambda* is built on the first
+ * call after grid creation or after chi or eps change (compared by
+ * content). rel_change_out (nullable, host): max_v |dJ_v| / |J_v|. */
+rt3d_status rt3d_ali_step(rt3d_grid *grid, const double *chi, const double *eps,
+                          const double *B, const rt3d_bc *bc, double *J_inout,
+                          double *rel_change_out);
+
+/* Iterates the ALI from J_inout until the estimated relative error of J is
+ * below tol (the last change times rho/(1-rho), rho the observed contraction
+ * of the changes). In RT3D_FP32_FS_FP64_ALI mode: FP32 iterations until the
+ * change stagnates, then defect correction with FP64 formal solutions
+ * (residual r64 = J_FS64(S(J)) - J, correction from the homogeneous FP32 ALI)
+ * until the FP64 residual certifies the result. max_iter caps the ALI
+ * iterations (FP32 and FP64 counted together). Returns RT3D_ENOTCONVERGED
+ * with J_inout holding the last iterate when the cap is hit. stats: nullable. */
+rt3d_status rt3d_solve(rt3d_grid *grid, const double *chi, const double *eps, const double *B,
+                       const rt3d_bc *bc, double *J_inout, double tol, int max_iter,
+                       rt3d_solve_stats *stats);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *rt3d_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT3D_H */

@@ -46,6 +46,9 @@ def _load():
         lib.orc_fs_cart.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp,
                                     c_double, _dp, c_double, _dp, _dp, _dp, c_int]
         lib.orc_fs_cart.restype = c_int
+        lib.orc_fs_cart_angles.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp,
+                                           c_double, _dp, c_double, _dp, _dp, c_int, _ip, c_int]
+        lib.orc_fs_cart_angles.restype = c_int
         lib.orc_fs_cart_voxel.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp,
                                           c_double, _dp, c_double, _dp, c_long, c_int, c_int,
                                           _dp, _dp]
@@ -151,6 +154,24 @@ def fs_cart(chi, S, ntheta: int, nphi: int, parabolic: bool = False, bc=None,
     if err:
         raise RuntimeError(f"oracle formal solution failed ({err})")
     return (J, L) if lstar else J
+
+
+def fs_cart_angles(chi, S, ntheta: int, nphi: int, angles, parabolic: bool = False, bc=None,
+                   nthreads: int | None = None):
+    """Share of the listed solid angles in J (a bounded sample of a large solve)."""
+    lib = _load()
+    chi, S = _f64(chi), _f64(S)
+    nz, ny, nx = chi.shape
+    J = np.zeros(chi.shape)
+    ang = np.ascontiguousarray(angles, dtype=np.int32)
+    t, tf, b, bf = _bc_args(chi.shape, bc)
+    err = lib.orc_fs_cart_angles(nx, ny, nz, ntheta, nphi, int(parabolic), _ptr(chi), _ptr(S),
+                                 t, _ptr(tf), b, _ptr(bf), _ptr(J),
+                                 nthreads or default_threads(), ang.ctypes.data_as(_ip),
+                                 int(ang.size))
+    if err:
+        raise RuntimeError(f"oracle formal solution failed ({err})")
+    return J
 
 
 def fs_cart_voxel(chi, S, ntheta: int, nphi: int, v: int, parabolic: bool = False, bc=None,

@@ -280,10 +280,11 @@ static double orc_bc(int nx, double mu, int x0, int y0, double I_top, const doub
  * d = (dx+1) + 3(dy+1) + 9(dz+1). Returns 0, or < 0 on a tracing error.
  * OpenMP over solid angles with per-thread partial sums.
  * ------------------------------------------------------------------------- */
-int orc_fs_cart(int nx, int ny, int nz, int nth, int nph, int parabolic,
-                const double *chi, const double *S,
-                double I_top, const double *I_top_face, double I_bot, const double *I_bot_face,
-                double *J, double *lstar, int nthreads)
+static int orc_fs_cart_core(int nx, int ny, int nz, int nth, int nph, int parabolic,
+                            const double *chi, const double *S,
+                            double I_top, const double *I_top_face, double I_bot,
+                            const double *I_bot_face, double *J, double *lstar, int nthreads,
+                            const int *angles, int nang)
 {
     const long N = (long)nx * ny * nz;
     const int nO = nth * nph;
@@ -308,10 +309,12 @@ int orc_fs_cart(int nx, int ny, int nz, int nth, int nph, int parabolic,
         double *numL = lstar ? malloc(sizeof(double) * 27 * N) : NULL;
         Jp[tid] = Jt;
         Lp[tid] = Lt;
+        const int nloop = angles ? nang : nO;
 #ifdef _OPENMP
 #pragma omp for schedule(static)
 #endif
-        for (int o = 0; o < nO; o++) {
+        for (int io = 0; io < nloop; io++) {
+            const int o = angles ? angles[io] : io;
             const double *d = dir + 3 * o;
             int kmax = orc_kmax_cart(nx, ny, nz, d);
             int *vox = malloc(sizeof(int) * kmax);
@@ -385,6 +388,27 @@ int orc_fs_cart(int nx, int ny, int nz, int nth, int nph, int parabolic,
     for (int t = 0; t < nthreads; t++) { free(Jp[t]); free(Lp[t]); }
     free(Jp); free(Lp); free(mu); free(phi); free(dir); free(wt);
     return err;
+}
+
+int orc_fs_cart(int nx, int ny, int nz, int nth, int nph, int parabolic,
+                const double *chi, const double *S,
+                double I_top, const double *I_top_face, double I_bot, const double *I_bot_face,
+                double *J, double *lstar, int nthreads)
+{
+    return orc_fs_cart_core(nx, ny, nz, nth, nph, parabolic, chi, S, I_top, I_top_face, I_bot,
+                            I_bot_face, J, lstar, nthreads, NULL, 0);
+}
+
+/* The same sums restricted to the listed solid angles (a bounded sample of a
+ * large formal solution; J receives only their share). */
+int orc_fs_cart_angles(int nx, int ny, int nz, int nth, int nph, int parabolic,
+                       const double *chi, const double *S,
+                       double I_top, const double *I_top_face, double I_bot,
+                       const double *I_bot_face, double *J, int nthreads,
+                       const int *angles, int nang)
+{
+    return orc_fs_cart_core(nx, ny, nz, nth, nph, parabolic, chi, S, I_top, I_top_face, I_bot,
+                            I_bot_face, J, NULL, nthreads, angles, nang);
 }
 
 /* ---------------------------------------------------------------------------

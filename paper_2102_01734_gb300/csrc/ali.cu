@@ -1,0 +1,332 @@
+// Operator-splitting step (Sec. 2.2, Eq. alo) and its Jacobi solver (Sec. 4,
+// "OS iteration"), with the reductions of the convergence test.
+//
+// The OS system for the correction dJ = J_new - J_old is
+//   [1 - Lambda*(1 - eps)] dJ = r,  r = J_FS - J_old,
+// a 27-point stencil periodic in x and y. os_prep folds (1 - eps) of the
+// neighbour into the 26 off-diagonal planes a[d][v] = Lambda*[d][v] (1 -
+// eps_{v+d}) (FP64, or FP32 in the mixed mode) and stores 1/diag in FP64.
+// A sweep reads the 26 planes once (the HBM stream that bounds it), the
+// neighbours of dJ through L1/L2, and writes dJ^{m+1} with the two maxima
+// of the stop test. Sweeps are launched back to back; each reads the
+// previous sweep's maxima and returns at once after the stop test is met,
+// so a fixed launch sequence serves any sweep count.
+#include "rt3d_internal.cuh"
+
+namespace rt3d {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long dbits(double x) {
+    return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ double bitsd(unsigned long long x) {
+    return __longlong_as_double((long long)x);
+}
+
+// block-wide max of a non-negative double (NaN propagates: its bit pattern
+// is above +inf), then one atomicMax per block.
+__device__ __forceinline__ void block_max_atomic(double x, unsigned long long *dst) {
+    __shared__ unsigned long long sm[32];
+    unsigned long long b = dbits(fabs(x));
+    if (x != x) b = 0x7ff8000000000000ULL;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long o = __shfl_xor_sync(0xffffffffu, b, off);
+        b = o > b ? o : b;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sm[wid] = b;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        b = lane < nw ? sm[lane] : 0ULL;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            unsigned long long o = __shfl_xor_sync(0xffffffffu, b, off);
+            b = o > b ? o : b;
+        }
+        if (lane == 0 && b) atomicMax(dst, b);
+    }
+    __syncthreads();  // sm[] is reused by a following call
+}
+
+__global__ void pack_kernel(int n, const double *chi, double scale, const double *S, void *out,
+                            bool fp64) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const double c = chi[v] * scale, s = S[v];
+        if (fp64) static_cast<double2 *>(out)[v] = make_double2(c, s);
+        else static_cast<float2 *>(out)[v] = make_float2((float)c, (float)s);
+    }
+}
+
+// S = (1 - eps) J + eps B (or (1 - eps) J for the homogeneous problem),
+// written into the S half of the packed (chi, S) array.
+__global__ void source_kernel(int n, const double *J, const double *eps, const double *B,
+                              void *out, bool fp64, bool homogeneous) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const double e = eps[v];
+        double s = (1.0 - e) * J[v];
+        if (!homogeneous) s += e * B[v];
+        if (fp64) static_cast<double2 *>(out)[v].y = s;
+        else static_cast<float2 *>(out)[v].y = (float)s;
+    }
+}
+
+template <typename A>
+__global__ void os_prep_kernel(int nx, int ny, int nz, const double *L, const double *eps, A *a,
+                               double *inv_diag) {
+    const long long N = (long long)nx * ny * nz;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+        inv_diag[v] = 1.0 / (1.0 - L[13 * N + v] * (1.0 - eps[v]));
+        int plane = 0;
+        for (int d = 0; d < 27; ++d) {
+            if (d == 13) continue;
+            const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+            const int zz = z + dz;
+            double val = 0.0;
+            if (zz >= 0 && zz < nz) {
+                int xx = x + dx, yy = y + dy;
+                if (xx < 0) xx += nx;
+                if (xx >= nx) xx -= nx;
+                if (yy < 0) yy += ny;
+                if (yy >= ny) yy -= ny;
+                const long long u = xx + (long long)nx * (yy + (long long)ny * zz);
+                val = L[(long long)d * N + v] * (1.0 - eps[u]);
+            }
+            a[(long long)plane * N + v] = (A)val;
+            ++plane;
+        }
+    }
+}
+
+// r = Jfs - J (+ extra); dJ0 = r / diag; resets the sweep state.
+__global__ void os_init_kernel(int n, const double *Jfs, const double *J, const double *extra,
+                               const double *inv_diag, double *r, double *dJ0, OsState *st) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        st->done = 0;
+        st->count = 0;
+    }
+    if (tid < 260) {
+        st->dmax[tid] = 0ULL;
+        st->jmax[tid] = 0ULL;
+    }
+    for (int v = tid; v < n; v += gridDim.x * blockDim.x) {
+        double rv = Jfs ? Jfs[v] : 0.0;
+        if (J) rv -= J[v];
+        if (extra) rv += extra[v];
+        r[v] = rv;
+        dJ0[v] = rv * inv_diag[v];
+    }
+}
+
+template <typename A>
+__global__ void __launch_bounds__(256) os_sweep_kernel(int nx, int ny, int nz, const A *__restrict__ a,
+                                                       const double *__restrict__ inv_diag,
+                                                       const double *__restrict__ r,
+                                                       const double *__restrict__ src,
+                                                       double *__restrict__ dst, int m, double tol,
+                                                       OsState *st) {
+    if (st->done) return;
+    if (m >= 2) {
+        const double dm = bitsd(st->dmax[m - 1]), jm = bitsd(st->jmax[m - 1]);
+        if (dm <= tol * jm) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                st->done = 1;
+                st->count = m - 1;
+            }
+            return;
+        }
+    }
+    const long long N = (long long)nx * ny * nz;
+    double dmax = 0.0, jmax = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+        const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+        const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+        A acc = A(0);
+        int plane = 0;
+#pragma unroll
+        for (int d = 0; d < 27; ++d) {
+            if (d == 13) continue;
+            const int dx = d % 3, dy = (d / 3) % 3, dz = d / 9 - 1;
+            const int zz = z + dz;
+            const A coef = a[(long long)plane * N + v];
+            ++plane;
+            if (zz < 0 || zz >= nz) continue;
+            const long long u = xs[dx] + (long long)nx * (ys[dy] + (long long)ny * zz);
+            acc += coef * (A)src[u];
+        }
+        const double nv = (r[v] + (double)acc) * inv_diag[v];
+        dst[v] = nv;
+        dmax = fmax(dmax, fabs(nv - src[v]));
+        jmax = fmax(jmax, fabs(nv));
+    }
+    block_max_atomic(dmax, &st->dmax[m]);
+    block_max_atomic(jmax, &st->jmax[m]);
+}
+
+__global__ void os_finish_kernel(int max_sweeps, double tol, OsState *st) {
+    if (st->done) return;
+    st->done = 1;
+    st->count = max_sweeps;
+}
+
+// J += dJ (dJ = the final sweep buffer); rel = max |dJ| / |J_new|.
+__global__ void ali_update_kernel(int n, double *J, double *const *buf, OsState *st,
+                                  double *dJ_out) {
+    const double *dJ = buf[st->count & 1];
+    double rel = 0.0;
+    bool bad = false;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const double d = dJ[v];
+        const double jn = J[v] + d;
+        J[v] = jn;
+        if (dJ_out) dJ_out[v] = d;
+        if (d != 0.0) rel = fmax(rel, fabs(d) / fabs(jn));
+        bad |= !(fabs(jn) <= 1.79e308);
+    }
+    block_max_atomic(bad ? __longlong_as_double(0x7ff8000000000000LL) : rel, &st->rel);
+}
+
+__global__ void copy_buf_kernel(int n, double *const *buf, const OsState *st, double *dst) {
+    const double *src = buf[st->count & 1];
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        dst[v] = src[v];
+}
+
+// J += d; rel = max |d| / |J_new|; amax = max |d|.
+__global__ void axpy_rel_kernel(int n, double *J, const double *d, OsState *st) {
+    double rel = 0.0;
+    bool bad = false;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const double jn = J[v] + d[v];
+        J[v] = jn;
+        if (d[v] != 0.0) rel = fmax(rel, fabs(d[v]) / fabs(jn));
+        bad |= !(fabs(jn) <= 1.79e308);
+    }
+    block_max_atomic(bad ? __longlong_as_double(0x7ff8000000000000LL) : rel, &st->rel);
+}
+
+// r = Jfs - J; res = max |r| / |J|.
+__global__ void residual_kernel(int n, const double *Jfs, const double *J, double *r,
+                                OsState *st) {
+    double res = 0.0;
+    bool bad = false;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const double rv = Jfs[v] - J[v];
+        if (r) r[v] = rv;
+        if (rv != 0.0) res = fmax(res, fabs(rv) / fabs(J[v]));
+        bad |= !(fabs(rv) <= 1.79e308);
+    }
+    block_max_atomic(bad ? __longlong_as_double(0x7ff8000000000000LL) : res, &st->res);
+}
+
+__global__ void compare_kernel(long long n, const double *a, const double *b, OsState *st) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (__double_as_longlong(a[i]) != __double_as_longlong(b[i])) {
+            st->changed = 1;
+            return;
+        }
+    }
+}
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    const long long cap = 152LL * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_pack(int n, const double *chi, double scale, const double *S, void *chiS,
+                        bool fp64, cudaStream_t s) {
+    pack_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, chi, scale, S, chiS, fp64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source(int n, const double *J, const double *eps, const double *B, void *chiS,
+                          bool fp64, bool homogeneous, cudaStream_t s) {
+    source_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, J, eps, B, chiS, fp64, homogeneous);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_os_prep(int nx, int ny, int nz, const double *lstar, const double *eps,
+                           void *a, bool a64, double *inv_diag, cudaStream_t s) {
+    const long long N = (long long)nx * ny * nz;
+    if (a64)
+        os_prep_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(nx, ny, nz, lstar, eps,
+                                                                static_cast<double *>(a), inv_diag);
+    else
+        os_prep_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(nx, ny, nz, lstar, eps,
+                                                               static_cast<float *>(a), inv_diag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_os_init(int n, const double *Jfs, const double *J, const double *extra,
+                           const double *inv_diag, double *r, double *dJ0, OsState *st,
+                           cudaStream_t s) {
+    int g = grid_for(n, 256);
+    if (g < 2) g = 2;  // >= 260 threads to reset the sweep maxima
+    os_init_kernel<<<g, 256, 0, s>>>(n, Jfs, J, extra, inv_diag, r, dJ0, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_os_sweep(int nx, int ny, int nz, const void *a, bool a64,
+                            const double *inv_diag, const double *r, double *const *buf, int m,
+                            double tol, OsState *st, cudaStream_t s) {
+    // buf is a host array of the two device ping-pong buffers
+    const long long N = (long long)nx * ny * nz;
+    const double *src = buf[(m - 1) & 1];
+    double *dst = buf[m & 1];
+    if (a64)
+        os_sweep_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(
+            nx, ny, nz, static_cast<const double *>(a), inv_diag, r, src, dst, m, tol, st);
+    else
+        os_sweep_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(
+            nx, ny, nz, static_cast<const float *>(a), inv_diag, r, src, dst, m, tol, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_os_finish(int max_sweeps, double tol, OsState *st, cudaStream_t s) {
+    os_finish_kernel<<<1, 1, 0, s>>>(max_sweeps, tol, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ali_update(int n, double *J, double *const *buf, OsState *st, double *dJ_out,
+                              cudaStream_t s) {
+    ali_update_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, J, buf, st, dJ_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_buf(int n, double *const *buf, const OsState *st, double *dst,
+                            cudaStream_t s) {
+    copy_buf_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, buf, st, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_rel(int n, double *J, const double *d, OsState *st, cudaStream_t s) {
+    axpy_rel_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, J, d, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(int n, const double *Jfs, const double *J, double *r, OsState *st,
+                            cudaStream_t s) {
+    residual_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, Jfs, J, r, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compare(long long n, const double *a, const double *b, OsState *st,
+                           cudaStream_t s) {
+    compare_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, a, b, st);
+    return cudaGetLastError();
+}
+
+}  // namespace rt3d

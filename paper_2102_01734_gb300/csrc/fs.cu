@@ -1,0 +1,239 @@
+// Formal solution J = Lambda S (Eq. frmsol) by long characteristics on the
+// periodic Cartesian box, with the optional non-local Lambda* band (Sec. 4:
+// "computing the Lambda* operator (only in the first iteration)"), following
+// the per-slot steps of the paper's Listing 1: gather the previous and next S
+// and chi, compute dtau, compute alpha/beta/gamma, fix up at the boundary,
+// store Lambda* data, compute Delta I and exp(-dtau).
+//
+// Mapping: one thread integrates one characteristic (all nx*ny
+// characteristics of a solid angle are translates of the cached one, so the
+// threads of a warp walk neighbouring voxels of the same layer in lock step:
+// the (chi, S) gathers of a warp hit one or two 128-byte lines). Blocks are
+// (ray bundle, solid angle) with angles ordered longest first. Contributions
+// are accumulated in FP64 (red.global.add.f64), also in the FP32 mode.
+//
+// Interval functions. For the interval of optical depth u between points
+// k-1 and k, with e0 = 1 - e^-u, e1 = u - e0, e2 = u^2 - 2 e1 (Olson &
+// Kunasz 1987), the kernel works with
+//   a = e1/u, b = e2/u^2, a0 = e0 - a, d = a - b,
+// which stay O(1) or O(u) at both ends of the range. Small u: e2 = u^3 p(u)
+// with p(u) = 2 sum_m (-1)^m u^m / (m+3)!, from the Taylor series of exp,
+// then a = u (1 - b)/2, e0 = u (1 - a), E = 1 - e0. Large u: E = exp(-u),
+// a = 1 - e0/u, a0 = (1 - (1+u) E)/u, d = (2a - e0)/u.
+// Coefficients (s = u/(u+w), q = u/w, w the next interval):
+//   linear:    alpha = a0, beta = a, gamma = 0
+//   parabolic: beta + gamma = a + s d, gamma = -q s d, alpha = a0 - s d,
+// and I_k = E I_{k-1} + alpha S_{k-1} + (beta+gamma) S_k + gamma (S_{k+1} - S_k)
+// so that large |gamma| (short next interval) multiplies a difference instead
+// of cancelling between two products. The last point of a characteristic is
+// linear; the entry point has S_{-1} = S_0 and chi_{-1} l_{-1} = 0.
+#include "rt3d_internal.cuh"
+
+namespace rt3d {
+
+namespace {
+
+template <typename R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+// Taylor coefficients of p(u) = e2/u^3 = 2 sum_m (-1)^m u^m / (m+3)!.
+constexpr double fact(int n) { return n <= 1 ? 1.0 : n * fact(n - 1); }
+constexpr double pc(int m) { return (m % 2 ? -2.0 : 2.0) / fact(m + 3); }
+template <int M> struct PC { static constexpr double v = pc(M); };
+template <int M> struct PCf { static constexpr float v = (float)pc(M); };
+
+// Horner evaluation of p(u) from degree M down to 0, unrolled at compile time.
+template <int M> struct Horner {
+    __device__ __forceinline__ static double eval(double acc, double u) {
+        return Horner<M - 1>::eval(fma(acc, u, PC<M - 1>::v), u);
+    }
+};
+template <> struct Horner<0> {
+    __device__ __forceinline__ static double eval(double acc, double) { return acc; }
+};
+
+struct IntervalF {
+    float E, a0, a, d;
+};
+struct IntervalD {
+    double E, a0, a, d;
+};
+
+__device__ __forceinline__ IntervalF interval(float u) {
+    IntervalF r;
+    if (u < 1.0f) {
+        // Horner, m = 8 .. 0: truncation < 1.3e-8 relative at u = 1
+        float p = PCf<8>::v;
+        p = fmaf(p, u, PCf<7>::v);
+        p = fmaf(p, u, PCf<6>::v);
+        p = fmaf(p, u, PCf<5>::v);
+        p = fmaf(p, u, PCf<4>::v);
+        p = fmaf(p, u, PCf<3>::v);
+        p = fmaf(p, u, PCf<2>::v);
+        p = fmaf(p, u, PCf<1>::v);
+        p = fmaf(p, u, PCf<0>::v);
+        const float b = u * p;
+        const float a = 0.5f * u * (1.0f - b);
+        const float e0 = u * (1.0f - a);
+        r.E = 1.0f - e0;
+        r.a = a;
+        r.a0 = e0 - a;
+        r.d = a - b;
+    } else {
+        const float E = __expf(-u);
+        const float ru = __fdividef(1.0f, u);
+        const float e0 = 1.0f - E;
+        const float a = fmaf(-e0, ru, 1.0f);
+        r.E = E;
+        r.a = a;
+        r.a0 = fmaf(-(1.0f + u), E, 1.0f) * ru;
+        r.d = fmaf(2.0f, a, -e0) * ru;
+    }
+    return r;
+}
+
+__device__ __forceinline__ IntervalD interval(double u) {
+    IntervalD r;
+    if (u < 0.5) {
+        // Horner, m = 17 .. 0: truncation ~1e-23 relative at u = 1/2
+        const double p = Horner<17>::eval(PC<17>::v, u);
+        const double b = u * p;
+        const double a = 0.5 * u * (1.0 - b);
+        const double e0 = u * (1.0 - a);
+        r.E = 1.0 - e0;
+        r.a = a;
+        r.a0 = e0 - a;
+        r.d = a - b;
+    } else {
+        const double E = exp(-u);
+        const double ru = 1.0 / u;
+        const double e0 = 1.0 - E;
+        const double a = fma(-e0, ru, 1.0);
+        r.E = E;
+        r.a = a;
+        r.a0 = fma(-(1.0 + u), E, 1.0) * ru;
+        r.d = fma(2.0, a, -e0) * ru;
+    }
+    return r;
+}
+
+template <typename R> __device__ __forceinline__ R div_fast(R x, R y);
+template <> __device__ __forceinline__ float div_fast<float>(float x, float y) {
+    return __fdividef(x, y);
+}
+template <> __device__ __forceinline__ double div_fast<double>(double x, double y) {
+    return x / y;
+}
+
+__device__ __forceinline__ int voxel_of(uint32_t c, int x0, int y0, int nx, int ny) {
+    int x = x0 + (int)(c & 0x7ffu);
+    int y = y0 + (int)((c >> 11) & 0x7ffu);
+    if (x >= nx) x -= nx;
+    if (y >= ny) y -= ny;
+    return x + nx * (y + ny * (int)(c >> 22));
+}
+
+template <typename R, bool PARAB, bool LSTAR>
+__global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
+    using R2 = typename V2<R>::T;
+    const int nray = p.nx * p.ny;
+    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= nray) return;
+    const int o = p.order[blockIdx.y];
+    const int x0 = ray % p.nx, y0 = ray / p.nx;
+    const long long t0 = p.toff[o];
+    const int K = p.tlen[o];
+    const uint32_t *__restrict__ code = p.code + t0;
+    const R *__restrict__ len = static_cast<const R *>(p.len) + t0;
+    const R *__restrict__ cw = static_cast<const R *>(p.cw) + t0;
+    const R2 *__restrict__ chiS = static_cast<const R2 *>(p.chiS);
+    const long long N = (long long)nray * p.nz;
+
+    double I0 = 0.0;
+    if (!p.homogeneous) {
+        if (p.up[o]) I0 = p.bot_face ? p.bot_face[ray] : p.I_bot;
+        else I0 = p.top_face ? p.top_face[ray] : p.I_top;
+    }
+    R I = (R)I0;
+
+    int v = voxel_of(__ldg(code), x0, y0, p.nx, p.ny);
+    R2 cs = chiS[v];
+    R chil_c = cs.x * __ldg(len);
+    R chil_p = R(0);
+    R S_c = cs.y, S_p = cs.y;
+    R ring[kWin];
+#pragma unroll
+    for (int i = 0; i < kWin; ++i) ring[i] = R(0);
+
+    for (int k = 0; k < K; ++k) {
+        const R u = R(0.5) * (chil_p + chil_c);
+        const auto f = interval(u);
+        const bool has_next = (k + 1 < K);
+        int vn = v;
+        R chil_n = R(0), S_n = S_c;
+        if (has_next) {
+            vn = voxel_of(__ldg(code + k + 1), x0, y0, p.nx, p.ny);
+            const R2 c2 = chiS[vn];
+            chil_n = c2.x * __ldg(len + k + 1);
+            S_n = c2.y;
+        }
+        R al = f.a0, bg = f.a, ga = R(0);
+        if (PARAB && has_next) {
+            const R w = R(0.5) * (chil_c + chil_n);
+            if (w > R(0)) {
+                const R s = div_fast(u, u + w);
+                const R q = div_fast(u, w);
+                const R sd = s * f.d;
+                bg = f.a + sd;
+                ga = -q * sd;
+                al = f.a0 - sd;
+            }
+        }
+        I = f.E * I + al * S_p + bg * S_c + ga * (S_n - S_c);
+        const R c = __ldg(cw + k);
+        atomicAdd(p.J + v, (double)(c * I));
+        if (LSTAR) {
+            // ring[i] = dI_k / dS_{k-7+i}
+#pragma unroll
+            for (int i = 0; i < kWin - 1; ++i) ring[i] = f.E * ring[i + 1];
+            const R be = bg - ga;
+            if (k == 0) ring[7] += al;  // S_{-1} = S_0 at the entry point
+            else ring[6] += al;
+            ring[7] += be;
+            ring[8] = ga;
+            const uint64_t wc = __ldg(reinterpret_cast<const unsigned long long *>(p.win + t0 + k));
+#pragma unroll
+            for (int i = 0; i < kWin; ++i) {
+                const unsigned dc = (unsigned)(wc >> (5 * i)) & 31u;
+                if (dc != kWinNone) atomicAdd(p.lstar + (long long)dc * N + v, (double)(c * ring[i]));
+            }
+        }
+        chil_p = chil_c;
+        chil_c = chil_n;
+        S_p = S_c;
+        S_c = S_n;
+        v = vn;
+    }
+}
+
+template <typename R, bool PARAB, bool LSTAR>
+cudaError_t launch_t(const FsParams &p, cudaStream_t s) {
+    const int threads = 128;
+    dim3 grid((p.nx * p.ny + threads - 1) / threads, p.nangles);
+    fs_kernel<R, PARAB, LSTAR><<<grid, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fs(const FsParams &p, bool fp64, bool parabolic, bool lstar, cudaStream_t s) {
+    if (fp64) {
+        if (parabolic) return lstar ? launch_t<double, true, true>(p, s) : launch_t<double, true, false>(p, s);
+        return lstar ? launch_t<double, false, true>(p, s) : launch_t<double, false, false>(p, s);
+    }
+    if (parabolic) return lstar ? launch_t<float, true, true>(p, s) : launch_t<float, true, false>(p, s);
+    return lstar ? launch_t<float, false, true>(p, s) : launch_t<float, false, false>(p, s);
+}
+
+}  // namespace rt3d

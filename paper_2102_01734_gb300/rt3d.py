@@ -1,0 +1,291 @@
+"""Python binding of the C ABI in include/rt3d.h (argument marshalling only).
+
+Every step of the formal solution, Lambda* construction, OS solve and ALI
+iteration runs in the CUDA library librt3d.so; this module converts torch
+tensors or numpy arrays to pointers and back. There is no CPU fallback: if
+the library is missing or cannot be loaded, every call raises.
+
+Arrays are float64, C-contiguous, shape (nz, ny, nx) (x fastest) or flat
+(N,). Device tensors are passed through; host arrays are staged by the
+library. Lambda* is (27, N) offset-major: [d][v] = dJ_v/dS_{v+d},
+d = (dx+1) + 3(dy+1) + 9(dz+1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+try:  # torch is the device-memory and stream provider when present
+    import torch
+except ImportError:  # pragma: no cover
+    torch = None
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librt3d.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "rt3d.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ETIMEOUT, ENUMERIC = range(7)
+CARTESIAN_PERIODIC_XY = 0
+LINEAR, PARABOLIC = 0, 1
+FP64, FP32_FS_FP64_ALI = 0, 1
+
+_c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("geometry", _c_int), ("n", _c_int * 3), ("ntheta", _c_int), ("nphi", _c_int),
+                ("interp", _c_int), ("precision", _c_int), ("nlambda", _c_int),
+                ("cuda_stream", _vp)]
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("I_top", _c_double), ("I_bottom", _c_double), ("I_top_face", _vp),
+                ("I_bottom_face", _vp)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", _c_int), ("fs_fp32", _c_int), ("fs_fp64", _c_int),
+                ("jacobi_sweeps", _c_int), ("rel_change", _c_double),
+                ("residual64", _c_double), ("est_error", _c_double), ("seconds", _c_double),
+                ("fs32_ms", _c_double), ("fs64_ms", _c_double), ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GridInfo(ctypes.Structure):
+    _fields_ = [("nangles", _c_int), ("kmax", _c_int), ("segments", ctypes.c_longlong),
+                ("device_bytes", ctypes.c_longlong)]
+
+
+class RT3DError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rt3d status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load librt3d.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"librt3d.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    lib.rt3d_grid_create.argtypes = [P(GridDesc), P(_vp)]
+    lib.rt3d_grid_destroy.argtypes = [_vp]
+    lib.rt3d_grid_destroy.restype = None
+    lib.rt3d_grid_get_info.argtypes = [_vp, P(GridInfo)]
+    lib.rt3d_grid_template.argtypes = [_vp, _c_int, P(_c_int), _vp, _vp]
+    lib.rt3d_formal_solution.argtypes = [_vp, _vp, _vp, P(BC), _vp, _vp]
+    lib.rt3d_os_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, _c_int, _c_double, P(_c_int)]
+    lib.rt3d_ali_step.argtypes = [_vp, _vp, _vp, _vp, P(BC), _vp, P(_c_double)]
+    lib.rt3d_solve.argtypes = [_vp, _vp, _vp, _vp, P(BC), _vp, _c_double, _c_int, P(SolveStats)]
+    lib.rt3d_last_error.restype = ctypes.c_char_p
+    lib.rt3d_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in include/rt3d.h."""
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt3d_[a-z0-9_]+)\s*\(", src)))
+
+
+def last_error() -> str:
+    return load().rt3d_last_error().decode()
+
+
+def _check(status: int):
+    if status != OK:
+        raise RT3DError(status, last_error())
+
+
+# ------------------------------------------------------------ marshalling
+def _is_torch(x):
+    return torch is not None and isinstance(x, torch.Tensor)
+
+
+def _ptr(x):
+    """Pointer of a float64 contiguous tensor/array (None -> NULL)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("arrays must be contiguous float64")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("arrays must be contiguous float64")
+        return x.ctypes.data
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _empty_like(x, shape):
+    if _is_torch(x):
+        return torch.empty(shape, dtype=torch.float64, device=x.device)
+    return np.empty(shape, dtype=np.float64)
+
+
+def _bc(bc, keep):
+    """rt3d_bc from a dict {I_top: float|array, I_bottom: float|array}."""
+    if bc is None:
+        return None
+    s = BC()
+    for key, fval, fptr in (("I_top", "I_top", "I_top_face"),
+                            ("I_bottom", "I_bottom", "I_bottom_face")):
+        val = bc.get(key, 0.0)
+        if np.isscalar(val) or (_is_torch(val) and val.dim() == 0):
+            setattr(s, fval, float(val))
+            setattr(s, fptr, None)
+        else:
+            if isinstance(val, np.ndarray):
+                val = np.ascontiguousarray(val, dtype=np.float64)
+            elif _is_torch(val):
+                val = val.to(torch.float64).contiguous()
+            keep.append(val)
+            setattr(s, fval, 0.0)
+            setattr(s, fptr, _ptr(val))
+    return s
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return int(stream)
+    if torch is not None and torch.cuda.is_available():
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+# ------------------------------------------------------------- the C ABI
+def grid_create(n, ntheta: int, nphi: int, interp: int = LINEAR, precision: int = FP64,
+                stream=None, geometry: int = CARTESIAN_PERIODIC_XY):
+    lib = load()
+    if np.isscalar(n):
+        n = (int(n),) * 3
+    d = GridDesc()
+    d.geometry = geometry
+    d.n[0], d.n[1], d.n[2] = (int(v) for v in n)
+    d.ntheta, d.nphi = int(ntheta), int(nphi)
+    d.interp, d.precision, d.nlambda = int(interp), int(precision), 1
+    d.cuda_stream = _stream_handle(stream)
+    h = _vp()
+    _check(lib.rt3d_grid_create(ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def grid_destroy(h):
+    load().rt3d_grid_destroy(h)
+
+
+def grid_get_info(h) -> dict:
+    info = GridInfo()
+    _check(load().rt3d_grid_get_info(h, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def grid_template(h, angle: int):
+    """(vox int32[K], len float64[K]) of the cached characteristic of `angle`."""
+    lib = load()
+    K = _c_int(0)
+    lib.rt3d_grid_template(h, angle, ctypes.byref(K), None, None)  # query the size
+    vox = np.zeros(K.value, dtype=np.int32)
+    ln = np.zeros(K.value, dtype=np.float64)
+    _check(lib.rt3d_grid_template(h, angle, ctypes.byref(K), vox.ctypes.data, ln.ctypes.data))
+    return vox, ln
+
+
+def formal_solution(h, chi, S, bc=None, J_out=None, lstar_out=None):
+    keep = []
+    b = _bc(bc, keep)
+    _check(load().rt3d_formal_solution(h, _ptr(chi), _ptr(S), ctypes.byref(b) if b else None,
+                                       _ptr(J_out), _ptr(lstar_out)))
+    return J_out
+
+
+def os_solve(h, lstar, eps, r, dJ_out, max_sweeps: int = 50, tol: float = 1e-3) -> int:
+    m = _c_int(0)
+    _check(load().rt3d_os_solve(h, _ptr(lstar), _ptr(eps), _ptr(r), _ptr(dJ_out), max_sweeps,
+                                tol, ctypes.byref(m)))
+    return m.value
+
+
+def ali_step(h, chi, eps, B, bc, J_inout) -> float:
+    keep = []
+    b = _bc(bc, keep)
+    rel = _c_double(0.0)
+    _check(load().rt3d_ali_step(h, _ptr(chi), _ptr(eps), _ptr(B), ctypes.byref(b) if b else None,
+                                _ptr(J_inout), ctypes.byref(rel)))
+    return rel.value
+
+
+def solve(h, chi, eps, B, bc, J_inout, tol: float = 1e-8, max_iter: int = 2000,
+          raise_on_nonconv: bool = True) -> dict:
+    keep = []
+    b = _bc(bc, keep)
+    st = SolveStats()
+    status = load().rt3d_solve(h, _ptr(chi), _ptr(eps), _ptr(B), ctypes.byref(b) if b else None,
+                               _ptr(J_inout), tol, max_iter, ctypes.byref(st))
+    out = st.as_dict()
+    out["status"] = status
+    if status != OK and (raise_on_nonconv or status != ENOTCONVERGED):
+        raise RT3DError(status, last_error())
+    return out
+
+
+class Grid:
+    """Owning wrapper of an rt3d_grid handle."""
+
+    def __init__(self, n, ntheta, nphi, interp=LINEAR, precision=FP64, stream=None):
+        if np.isscalar(n):
+            n = (int(n),) * 3
+        self.n = tuple(int(v) for v in n)
+        self.shape = (self.n[2], self.n[1], self.n[0])
+        self.N = self.n[0] * self.n[1] * self.n[2]
+        self.handle = grid_create(n, ntheta, nphi, interp, precision, stream)
+
+    def close(self):
+        if self.handle:
+            grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return grid_get_info(self.handle)
+
+    def template(self, angle):
+        return grid_template(self.handle, angle)
+
+    def formal_solution(self, chi, S, bc=None, lstar=False, J_out=None, lstar_out=None):
+        J = J_out if J_out is not None else _empty_like(chi, self.shape)
+        L = None
+        if lstar:
+            L = lstar_out if lstar_out is not None else _empty_like(chi, (27, self.N))
+        formal_solution(self.handle, chi, S, bc, J, L)
+        return (J, L) if lstar else J
+
+    def os_solve(self, lstar, eps, r, max_sweeps=50, tol=1e-3):
+        dJ = _empty_like(r, r.shape)
+        m = os_solve(self.handle, lstar, eps, r, dJ, max_sweeps, tol)
+        return dJ, m
+
+    def ali_step(self, chi, eps, B, bc, J):
+        return ali_step(self.handle, chi, eps, B, bc, J)
+
+    def solve(self, chi, eps, B, bc, J, tol=1e-8, max_iter=2000, raise_on_nonconv=True):
+        return solve(self.handle, chi, eps, B, bc, J, tol, max_iter, raise_on_nonconv)

@@ -1,0 +1,49 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads,
+exports every function include/rt3d.h declares, and rejects bad descriptors
+before touching a device."""
+import ctypes
+
+import pytest
+
+from paper_2102_01734_gb300 import build, rt3d
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return rt3d.load()
+
+
+def test_header_declares_the_boundary():
+    names = rt3d.header_functions()
+    for required in ("rt3d_grid_create", "rt3d_grid_destroy", "rt3d_formal_solution",
+                     "rt3d_os_solve", "rt3d_ali_step", "rt3d_solve", "rt3d_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in rt3d.header_functions():
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("n,nth,nph,interp,prec", [
+    ((3, 8, 8), 4, 4, 0, 0),        # nx < 4
+    ((8, 8, 0), 4, 4, 0, 0),        # nz < 1
+    ((2048, 8, 8), 4, 4, 0, 0),     # nx too large
+    ((8, 8, 8), 0, 4, 0, 0),        # no angles
+    ((8, 8, 8), 4, 4, 7, 0),        # bad interpolation
+    ((8, 8, 8), 4, 4, 0, 9),        # bad precision
+])
+def test_bad_descriptor_is_einval(lib, n, nth, nph, interp, prec):
+    with pytest.raises(rt3d.RT3DError) as ei:
+        rt3d.grid_create(n, nth, nph, interp, prec, stream=0)
+    assert ei.value.status == rt3d.EINVAL
+    assert rt3d.last_error()
+
+
+def test_null_arguments_are_einval(lib):
+    assert lib.rt3d_grid_create(None, None) == rt3d.EINVAL
+    assert lib.rt3d_formal_solution(None, None, None, None, None, None) == rt3d.EINVAL
+    assert lib.rt3d_solve(None, None, None, None, None, None, 1e-8, 10, None) == rt3d.EINVAL
+    st = rt3d.SolveStats()
+    assert ctypes.sizeof(st) == 4 * 4 + 6 * 8 + 8

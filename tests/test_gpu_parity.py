@@ -1,0 +1,247 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: traced voxel indices and chords bit-exact; J and Lambda* within 1e-12
+relative in the FP64 mode and 2e-5 relative in the FP32 formal-solution mode;
+converged J within 1e-8 of the oracle's converged J.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_01734_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def rt3d():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_01734_gb300 import build, rt3d as mod
+    build.build()
+    mod.load()
+    return mod
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def dev_bc(bc):
+    return {k: (dev(v) if isinstance(v, np.ndarray) else v) for k, v in bc.items()}
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def lstar_err(Lg, Lo):
+    """Lambda* (27,N) from the GPU vs (N,27) from the oracle, relative to the
+    largest entry of each row."""
+    Lg = Lg.T
+    scale = np.max(np.abs(Lo), axis=1, keepdims=True)
+    return float(np.max(np.abs(Lg - Lo) / scale))
+
+
+# ------------------------------------------------------------ tracer (A2)
+@pytest.mark.parametrize("n,nth,nph", [((13, 11, 9), 6, 10), ((4, 4, 1), 2, 4),
+                                       ((40, 37, 23), 8, 16)])
+def test_template_bit_exact(rt3d, n, nth, nph):
+    g = rt3d.Grid(n, nth, nph)
+    mu, phi, d, w = oracle.directions(nth, nph)
+    shape = (n[2], n[1], n[0])
+    for o in range(nth * nph):
+        vox, ln = g.template(o)
+        ov, ol = oracle.trace_cart(shape, d[o], 0, 0)
+        assert np.array_equal(vox, ov), o
+        assert np.array_equal(ln.view(np.int64), ol.view(np.int64)), o
+    info = g.info()
+    assert info["nangles"] == nth * nph
+
+
+def test_template_bit_exact_box129(rt3d):
+    g = rt3d.Grid(129, 32, 64, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+    mu, phi, d, w = oracle.directions(32, 64)
+    for o in range(0, 2048, 7):
+        vox, ln = g.template(o)
+        ov, ol = oracle.trace_cart((129, 129, 129), d[o], 0, 0)
+        assert np.array_equal(vox, ov), o
+        assert np.array_equal(ln.view(np.int64), ol.view(np.int64)), o
+    assert g.info()["segments"] > 2.5e10
+
+
+# ------------------------------------------------ formal solution (A4-A7)
+CASES = [
+    # (n, ntheta, nphi, seed) -- ragged tails: nx*ny not a multiple of 128
+    ((17, 13, 11), 4, 8, 1),
+    ((9, 9, 4), 2, 5, 2),
+    ((4, 5, 1), 2, 6, 3),
+    ((33, 20, 7), 6, 6, 4),
+]
+
+
+def _case(n, seed):
+    chi, eps, B, bc = inputs.cartesian_config(n, 1e-2, seed=seed)
+    rng = np.random.default_rng(seed)
+    S = rng.uniform(0.2, 2.0, chi.shape)
+    bc = {"I_top": rng.uniform(0, 0.3, chi.shape[1:]), "I_bottom": bc["I_bottom"]}
+    return chi, S, bc
+
+
+@pytest.mark.parametrize("parabolic", [False, True])
+@pytest.mark.parametrize("n,nth,nph,seed", CASES)
+def test_fs_fp64_parity(rt3d, n, nth, nph, seed, parabolic):
+    chi, S, bc = _case(n, seed)
+    g = rt3d.Grid(n, nth, nph, int(parabolic), rt3d.FP64)
+    J, L = g.formal_solution(dev(chi), dev(S), dev_bc(bc), lstar=True)
+    Jo, Lo = oracle.fs_cart(chi, S, nth, nph, parabolic, bc, lstar=True)
+    assert relerr(J.cpu().numpy(), Jo) < TOL64
+    assert lstar_err(L.cpu().numpy(), Lo) < TOL64
+
+
+@pytest.mark.parametrize("parabolic", [False, True])
+@pytest.mark.parametrize("n,nth,nph,seed", CASES)
+def test_fs_fp32_parity(rt3d, n, nth, nph, seed, parabolic):
+    chi, S, bc = _case(n, seed)
+    g = rt3d.Grid(n, nth, nph, int(parabolic), rt3d.FP32_FS_FP64_ALI)
+    J, L = g.formal_solution(dev(chi), dev(S), dev_bc(bc), lstar=True)
+    Jo, Lo = oracle.fs_cart(chi, S, nth, nph, parabolic, bc, lstar=True)
+    assert relerr(J.cpu().numpy(), Jo) < TOL32
+    assert lstar_err(L.cpu().numpy(), Lo) < TOL32
+
+
+def test_fs_thick_thin_extremes(rt3d):
+    """Per-voxel dtau from 1e-7 to 3e3 (both series and closed-form branches,
+    vacuum-like and opaque voxels next to each other)."""
+    rng = np.random.default_rng(9)
+    n = (16, 12, 10)
+    shape = (10, 12, 16)
+    chi = 10 ** rng.uniform(-7, 3.5, shape)
+    S = rng.uniform(0.1, 3.0, shape)
+    bc = {"I_top": 0.5, "I_bottom": 1.5}
+    for parabolic in (False, True):
+        Jo = oracle.fs_cart(chi, S, 4, 8, parabolic, bc)
+        for prec, tol in ((rt3d.FP64, TOL64), (rt3d.FP32_FS_FP64_ALI, TOL32)):
+            g = rt3d.Grid(n, 4, 8, int(parabolic), prec)
+            J = g.formal_solution(dev(chi), dev(S), bc)
+            assert relerr(J.cpu().numpy(), Jo) < tol, (parabolic, prec)
+
+
+def test_fs_host_pointers_match_device(rt3d):
+    chi, S, bc = _case((17, 13, 11), 1)
+    g = rt3d.Grid((17, 13, 11), 4, 8, rt3d.PARABOLIC, rt3d.FP64)
+    Jd = g.formal_solution(dev(chi), dev(S), dev_bc(bc)).cpu().numpy()
+    Jh = g.formal_solution(chi, S, bc)
+    assert isinstance(Jh, np.ndarray)
+    assert np.max(np.abs(Jh - Jd) / Jd) < 1e-14
+
+
+def test_fs_box129_sampled(rt3d):
+    """Full-size box (129^3, 32 x 64 angles, parabolic, k^-3 lognormal field),
+    FP32 formal solution as timed by the benchmark; sampled voxels against
+    the oracle's per-voxel route."""
+    cfg = inputs.CONFIGS["box129_field"]
+    chi, eps, B, bc = inputs.cartesian_config(129, cfg["eps"], seed=cfg["seed"])
+    S = B.copy()
+    g = rt3d.Grid(129, 32, 64, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+    J = g.formal_solution(dev(chi), dev(S), dev_bc(bc)).cpu().numpy().reshape(-1)
+    rng = np.random.default_rng(0)
+    vs = [0, 129 * 129 * 64 + 65 * 129 + 3, chi.size - 1] + list(rng.integers(0, chi.size, 2))
+    for v in vs:
+        Jv = oracle.fs_cart_voxel(chi, S, 32, 64, int(v), True, bc)
+        assert abs(J[v] - Jv) / abs(Jv) < TOL32, v
+
+
+# ---------------------------------------------------------- OS solve (A8)
+def test_os_solve_parity(rt3d):
+    rng = np.random.default_rng(2)
+    n = (11, 9, 7)
+    shape = (7, 9, 11)
+    chi = 10 ** rng.uniform(-1, 1.5, shape)
+    _, Lo = oracle.fs_cart(chi, np.ones(shape), 4, 6, False, lstar=True)
+    eps = 10 ** rng.uniform(-4, -1, shape)
+    r = rng.standard_normal(shape)
+    dJo, mo = oracle.os_jacobi(Lo, eps, r, max_sweeps=50, tol=1e-6)
+    g = rt3d.Grid(n, 4, 6, rt3d.LINEAR, rt3d.FP64)
+    dJ, m = g.os_solve(dev(np.ascontiguousarray(Lo.T)), dev(eps), dev(r), max_sweeps=50, tol=1e-6)
+    assert m == mo
+    assert np.max(np.abs(dJ.cpu().numpy() - dJo)) < 1e-12 * np.max(np.abs(dJo))
+
+
+def test_ali_step_parity(rt3d):
+    chi, eps, B, bc = inputs.cartesian_config((13, 11, 9), 1e-3, seed=7)
+    J0 = np.full(chi.shape, 0.5)
+    # oracle: one iteration of Eq. alo
+    S = (1 - eps) * J0 + eps * B
+    Jfs, Lo = oracle.fs_cart(chi, S, 4, 8, True, bc, lstar=True)
+    dJo, _ = oracle.os_jacobi(Lo, eps, Jfs - J0, 50, 1e-3)
+    Jo = J0 + dJo
+    g = rt3d.Grid((13, 11, 9), 4, 8, rt3d.PARABOLIC, rt3d.FP64)
+    J = dev(J0)
+    rel = g.ali_step(dev(chi), dev(eps), dev(B), dev_bc(bc), J)
+    assert relerr(J.cpu().numpy(), Jo) < 1e-11
+    assert abs(rel - np.max(np.abs(dJo) / np.abs(Jo))) < 1e-9 * rel
+
+
+# ------------------------------------------------- converged solve (A8-A10)
+def _golden33():
+    vals = [float(l) for l in open(os.path.join(HERE, "golden", "box33_fp64_J.txt"))
+            if not l.startswith("#")]
+    return np.array(vals)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_box33_matches_golden(rt3d, precision):
+    chi, eps, B, bc = inputs.cartesian_config(33, 1e-2)
+    prec = rt3d.FP64 if precision == "fp64" else rt3d.FP32_FS_FP64_ALI
+    g = rt3d.Grid(33, 8, 16, rt3d.LINEAR, prec)
+    J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
+    st = g.solve(dev(chi), dev(eps), dev(B), dev_bc(bc), J, tol=1e-9, max_iter=3000)
+    ref = _golden33()[:, None, None]
+    err = np.max(np.abs(J.cpu().numpy() - ref) / ref)
+    assert err < 1e-8, (err, st)
+    assert st["residual64"] < 1e-8
+
+
+@pytest.mark.parametrize("parabolic", [False, True])
+def test_solve_field_matches_oracle(rt3d, parabolic):
+    n = (14, 12, 11)
+    chi, eps, B, bc = inputs.cartesian_config(n, 1e-4, seed=3)
+    Jo, it, _, _ = oracle.ali_solve(chi, eps, B, 4, 8, parabolic, bc, tol=1e-13, max_iter=3000)
+    assert it > 0
+    for prec in (rt3d.FP64, rt3d.FP32_FS_FP64_ALI):
+        g = rt3d.Grid(n, 4, 8, int(parabolic), prec)
+        J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
+        st = g.solve(dev(chi), dev(eps), dev(B), dev_bc(bc), J, tol=1e-9, max_iter=3000)
+        err = relerr(J.cpu().numpy(), Jo)
+        assert err < 1e-8, (prec, err, st)
+
+
+# ----------------------------------------------------------- error paths
+def test_iteration_cap_is_enotconverged(rt3d):
+    chi, eps, B, bc = inputs.cartesian_config(8, 1e-4)
+    g = rt3d.Grid(8, 2, 4, rt3d.LINEAR, rt3d.FP64)
+    J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
+    st = g.solve(dev(chi), dev(eps), dev(B), dev_bc(bc), J, tol=1e-12, max_iter=2,
+                 raise_on_nonconv=False)
+    assert st["status"] == rt3d.ENOTCONVERGED
+    assert st["iterations"] == 2
+    assert torch.isfinite(J).all()
+
+
+def test_nan_input_is_enumeric(rt3d):
+    chi, eps, B, bc = inputs.cartesian_config(8, 1e-2)
+    B = B.copy()
+    B[3, 2, 1] = np.nan
+    g = rt3d.Grid(8, 2, 4, rt3d.LINEAR, rt3d.FP64)
+    J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(rt3d.RT3DError) as ei:
+        g.solve(dev(chi), dev(eps), dev(B), dev_bc(bc), J, tol=1e-8, max_iter=20)
+    assert ei.value.status == rt3d.ENUMERIC
