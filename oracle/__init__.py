@@ -42,6 +42,8 @@ def _load():
         lib.orc_kmax_cart.restype = c_int
         lib.orc_e012.argtypes = [c_double, _dp, _dp, _dp]
         lib.orc_coef.argtypes = [c_int, c_double, c_double, _dp, _dp, _dp, _dp]
+        lib.orc_parab_weight.argtypes = [c_double, c_double]
+        lib.orc_parab_weight.restype = c_double
         lib.orc_ray_fs.argtypes = [c_int, _dp, _dp, c_double, c_int, _dp, _dp, _dp, _dp, _dp]
         lib.orc_fs_cart.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp,
                                     c_double, _dp, c_double, _dp, _dp, _dp, c_int]
@@ -116,6 +118,11 @@ def coef(parabolic: bool, u: float, w: float):
     out = [ctypes.c_double() for _ in range(4)]
     lib.orc_coef(int(parabolic), float(u), float(w), *[ctypes.byref(o) for o in out])
     return tuple(o.value for o in out)
+
+
+def parab_weight(u: float, w: float) -> float:
+    """Weight f of the parabolic against the linear coefficients."""
+    return _load().orc_parab_weight(float(u), float(w))
 
 
 def ray_fs(chil, S, I0: float, parabolic: bool):
@@ -219,7 +226,7 @@ def ali_solve(chi, eps, B, ntheta: int, nphi: int, parabolic: bool = False, bc=N
                            max_sweeps, sweep_tol, nthreads or default_threads(), _ptr(L),
                            _ptr(hist))
     if it <= -1000:
-        raise RuntimeError(f"oracle ALI failed ({it})")
+        raise RuntimeError(f"oracle ALI failed ({it}): non-finite J or tracing error")
     return J, it, hist[:abs(it)], L
 
 

@@ -164,11 +164,33 @@ void orc_e012(double u, double *e0, double *e1, double *e2)
     }
 }
 
+/* Weight of the parabolic coefficients against the linear ones:
+ * f = clamp(2 - 2u, 0, 1) * clamp(2 - q/2, 0, 1), q = u/w, i.e. the full
+ * parabola for u <= 1/2 and u/w <= 2, the linear form for u >= 1 or
+ * u/w >= 4, linear ramps in between. (Reading: with voxel-constant S the
+ * plain parabola gives the downstream voxel a negative weight in optically
+ * thick intervals and overshoots next to short intervals; then the OS
+ * matrix 1 - Lambda*(1-eps) loses diagonal dominance at small eps and the
+ * Jacobi/Gauss-Seidel solvers of Sec. 4 diverge.) */
+double orc_parab_weight(double u, double w)
+{
+    if (!(w > 0.0)) return 0.0;
+    double fu = 2.0 - 2.0 * u;
+    if (fu > 1.0) fu = 1.0;
+    if (fu < 0.0) fu = 0.0;
+    double fq = 2.0 - 0.5 * (u / w);
+    if (fq > 1.0) fq = 1.0;
+    if (fq < 0.0) fq = 0.0;
+    return fu * fq;
+}
+
 /* Interpolation coefficients of the interval (k-1 -> k) with optical depth u,
  * the next interval (k -> k+1) having w. E = exp(-u). Linear (parabolic == 0
  * or w <= 0): alpha = e0 - e1/u, beta = e1/u, gamma = 0. Parabolic: the
- * Lagrange parabola through the three points integrated over the interval.
- * u <= 0 (vacuum) gives E = 1 and zero coefficients. */
+ * Lagrange parabola through the three points integrated over the interval,
+ * blended with the linear coefficients by the weight f above:
+ * c = c_lin + f (c_par - c_lin). u <= 0 (vacuum) gives E = 1 and zero
+ * coefficients. */
 void orc_coef(int parabolic, double u, double w, double *E, double *al, double *be, double *ga)
 {
     if (!(u > 0.0)) {
@@ -179,14 +201,19 @@ void orc_coef(int parabolic, double u, double w, double *E, double *al, double *
     double e0, e1, e2;
     orc_e012(u, &e0, &e1, &e2);
     *E = exp(-u);
-    if (!parabolic || !(w > 0.0)) {
-        *al = e0 - e1 / u;
-        *be = e1 / u;
+    double al_l = e0 - e1 / u, be_l = e1 / u;
+    double f = parabolic ? orc_parab_weight(u, w) : 0.0;
+    if (f == 0.0) {
+        *al = al_l;
+        *be = be_l;
         *ga = 0.0;
     } else {
-        *al = e0 + (e2 - (w + 2.0 * u) * e1) / (u * (u + w));
-        *be = ((u + w) * e1 - e2) / (u * w);
-        *ga = (e2 - u * e1) / (w * (u + w));
+        double al_p = e0 + (e2 - (w + 2.0 * u) * e1) / (u * (u + w));
+        double be_p = ((u + w) * e1 - e2) / (u * w);
+        double ga_p = (e2 - u * e1) / (w * (u + w));
+        *al = al_l + f * (al_p - al_l);
+        *be = be_l + f * (be_p - be_l);
+        *ga = f * ga_p;
     }
 }
 
@@ -577,12 +604,16 @@ int orc_ali_solve(int nx, int ny, int nz, int nth, int nph, int parabolic,
         for (long v = 0; v < N; v++) r[v] = Jfs[v] - J[v];
         orc_os_jacobi(nx, ny, nz, L, eps, r, dJ, max_sweeps, sweep_tol);
         double rel = 0.0;
+        int bad = 0;
         for (long v = 0; v < N; v++) {
             J[v] += dJ[v];
+            if (!isfinite(J[v])) bad = 1;
+            if (dJ[v] == 0.0) continue;
             double q = fabs(dJ[v]) / fabs(J[v]);
             if (q > rel) rel = q;
         }
-        if (history) history[it] = rel;
+        if (history) history[it] = bad ? NAN : rel;
+        if (bad) { err = -100; break; }
         if (rel < tol) { it++; conv = 1; break; }
     }
     free(S); free(Jfs); free(r); free(dJ);

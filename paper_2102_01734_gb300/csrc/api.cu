@@ -587,10 +587,14 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     const int max_sweeps = 50;
     const double sweep_tol = 1e-3;
 
-    // Phase 1: ALI iterations in the grid's FS precision.
-    double rel = 1.0, rel_prev = 0.0, est = 1.0;
+    // Phase 1: ALI iterations in the grid's FS precision. The FP32 formal
+    // solution carries rounding noise that the OS correction amplifies by up
+    // to 1/(1 - Lambda*_vv (1-eps)); the changes then stop falling. Phase 1
+    // ends when the estimated error is below tol or the changes stagnate (no
+    // halving of the smallest change within 8 iterations).
+    double rel = 1.0, rel_prev = 0.0, est = 1.0, rel_min = 1e300;
+    int since_min = 0;
     bool conv = false;
-    const double switch_at = g->fs64 ? 0.0 : 1e-6;  // FP32 accuracy floor
     int it = 0;
     while (it < max_iter) {
         TRY(ali_iteration(g, fp, g->fs64, max_sweeps, sweep_tol, &rel));
@@ -602,24 +606,32 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
         rho = std::min(std::max(rho, 0.0), 0.999);
         est = rel * rho / (1.0 - rho);
         rel_prev = rel;
-        if (g->fs64) {
-            if (est <= tol && it >= 2) {
-                conv = true;
-                break;
-            }
-        } else if (rel <= switch_at || est <= tol) {
+        if (rel < 0.5 * rel_min) {
+            rel_min = rel;
+            since_min = 0;
+        } else if (++since_min >= 8) {
+            break;  // stagnated
+        }
+        if (est <= tol && it >= 2) {
+            conv = g->fs64;
             break;
         }
     }
     s.rel_change = rel;
 
-    // Phase 2 (mixed precision): defect correction with FP64 residuals.
+    // Phase 2 (mixed precision): defect correction with FP64 residuals,
+    // r64 = J_FS64(S(J)) - J, and corrections delta from the homogeneous
+    // problem (1 - Lambda(1-eps)) delta = r64 iterated with the FP32 formal
+    // solution. The error after J += delta is about |delta| times the relative
+    // accuracy of delta; rounds repeat until that estimate is below tol, and
+    // a last FP64 formal solution certifies the returned J.
     FsParams fp64p;
     TRY(fs_params(g, bc, true, false, &fp64p));
     FsParams fphom;
     TRY(fs_params(g, nullptr, false, true, &fphom));
-    if (!g->fs64 && it < max_iter) {
-        for (int round = 0; round < 6 && it < max_iter; ++round) {
+    const bool mixed = !g->fs64;
+    if ((mixed || !conv) && it < max_iter) {
+        for (int round = 0; round < 8 && it < max_iter; ++round) {
             // r64 = J_FS64(S(J)) - J
             CKL(launch_source(n, g->J, g->eps, g->B, g->chiS64, true, false, g->stream));
             TRY(run_fs(g, fp64p, true, false));
@@ -631,18 +643,20 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
             s.residual64 = res;
             if (!(res == res)) return fail(RT3D_ENUMERIC, "NaN in the FP64 residual");
             if (conv) break;  // that was the certification of the corrected J
-            // delta: ALI on (1 - Lambda(1-eps)) delta = r64 with the homogeneous
-            // FP32 formal solution; delta_0 = M^-1 r64.
+            // delta_0 = M^-1 r64, then ALI on delta with the homogeneous FS
             TRY(os_solve_dev(g, nullptr, nullptr, g->r64, max_sweeps, sweep_tol));
             CKL(launch_copy_buf(n, g->dJ_dev, g->st, g->delta, g->stream));
-            double drel = 1.0, dprev = 0.0, dest = 1.0;
-            for (int inner = 0; inner < 200 && it < max_iter; ++inner) {
-                // J' = Lambda_hom((1-eps) delta) + r64 ; Jacobi on J' - delta
-                CKL(launch_source(n, g->delta, g->eps, nullptr, g->chiS32, false, true, g->stream));
-                TRY(run_fs(g, fphom, false, false));
-                ++s.fs_fp32;
+            double drel = 1.0, dprev = 0.0, dmin = 1e300, dacc = 1.0;
+            int dsince = 0;
+            const bool fs32 = mixed;
+            for (int inner = 0; inner < 400 && it < max_iter; ++inner) {
+                CKL(launch_source(n, g->delta, g->eps, nullptr, fs32 ? g->chiS32 : g->chiS64, !fs32,
+                                  true, g->stream));
+                TRY(run_fs(g, fphom, !fs32, false));
+                if (fs32) ++s.fs_fp32;
+                else ++s.fs_fp64;
                 ++it;
-                // r = Jfs + r64 - delta
+                // r = Lambda_hom((1-eps) delta) + r64 - delta
                 TRY(os_solve_dev(g, g->Jfs, g->delta, g->r64, max_sweeps, sweep_tol));
                 TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));
                 CKL(launch_ali_update(n, g->delta, g->dJ_dev, g->st, nullptr, g->stream));
@@ -650,20 +664,27 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
                 if (!(drel == drel)) return fail(RT3D_ENUMERIC, "NaN in the defect correction");
                 double rho = dprev > 0.0 ? drel / dprev : 0.9;
                 rho = std::min(std::max(rho, 0.0), 0.999);
-                dest = drel * rho / (1.0 - rho);
+                dacc = std::max(drel * rho / (1.0 - rho), drel);
                 dprev = drel;
-                if (dest <= 1e-3 || drel <= 1e-5) break;
+                if (dacc <= 1e-4) break;
+                if (drel < 0.5 * dmin) {
+                    dmin = drel;
+                    dsince = 0;
+                } else if (++dsince >= 8) {
+                    dacc = std::max(dacc, 10.0 * dmin);  // stagnated at the FP32 floor
+                    break;
+                }
             }
             // J += delta; size of the correction relative to J
             TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));
             CKL(launch_axpy_rel(n, g->J, g->delta, g->st, g->stream));
             double crel = 0.0;
             TRY(read_scalar_d(g, offsetof(OsState, rel), &crel));
-            est = crel * std::max(dest, 1e-5) + 1e-12;
+            est = crel * dacc;
             s.rel_change = crel;
             if (est <= tol) conv = true;
         }
-    } else if (g->fs64) {
+    } else if (conv) {
         // certification residual of the returned J
         CKL(launch_source(n, g->J, g->eps, g->B, g->chiS64, true, false, g->stream));
         TRY(run_fs(g, fp64p, true, false));

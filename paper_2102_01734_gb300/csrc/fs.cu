@@ -22,7 +22,11 @@
 // a = 1 - e0/u, a0 = (1 - (1+u) E)/u, d = (2a - e0)/u.
 // Coefficients (s = u/(u+w), q = u/w, w the next interval):
 //   linear:    alpha = a0, beta = a, gamma = 0
-//   parabolic: beta + gamma = a + s d, gamma = -q s d, alpha = a0 - s d,
+//   parabolic: beta + gamma = a + f s d, gamma = -f q s d, alpha = a0 - f s d,
+// where f = clamp(2 - 2u, 0, 1) clamp(2 - q/2, 0, 1) blends the Olson-Kunasz
+// parabola (f = 1: u <= 1/2 and q <= 2) continuously into the linear form
+// (f = 0: u >= 1 or q >= 4), which keeps every weight of an optically thick
+// interval non-negative (the OS matrix stays diagonally dominant),
 // and I_k = E I_{k-1} + alpha S_{k-1} + (beta+gamma) S_k + gamma (S_{k+1} - S_k)
 // so that large |gamma| (short next interval) multiplies a difference instead
 // of cancelling between two products. The last point of a characteristic is
@@ -126,6 +130,10 @@ template <> __device__ __forceinline__ double div_fast<double>(double x, double 
     return x / y;
 }
 
+template <typename R> __device__ __forceinline__ R clamp01(R x) {
+    return x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
+}
+
 __device__ __forceinline__ int voxel_of(uint32_t c, int x0, int y0, int nx, int ny) {
     int x = x0 + (int)(c & 0x7ffu);
     int y = y0 + (int)((c >> 11) & 0x7ffu);
@@ -182,12 +190,14 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
         if (PARAB && has_next) {
             const R w = R(0.5) * (chil_c + chil_n);
             if (w > R(0)) {
-                const R s = div_fast(u, u + w);
                 const R q = div_fast(u, w);
-                const R sd = s * f.d;
-                bg = f.a + sd;
-                ga = -q * sd;
-                al = f.a0 - sd;
+                const R fw = clamp01(R(2) - R(2) * u) * clamp01(R(2) - R(0.5) * q);
+                if (fw > R(0)) {
+                    const R sd = fw * div_fast(u, u + w) * f.d;
+                    bg = f.a + sd;
+                    ga = -q * sd;
+                    al = f.a0 - sd;
+                }
             }
         }
         I = f.E * I + al * S_p + bg * S_c + ga * (S_n - S_c);

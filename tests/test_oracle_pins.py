@@ -63,9 +63,11 @@ def _lagrange_integrals(u, w):
     return a, b, g
 
 
-@pytest.mark.parametrize("u,w", [(1e-5, 2e-5), (0.01, 0.03), (0.3, 0.1), (0.9, 4.0), (2.0, 1.5),
-                                 (30.0, 45.0), (300.0, 100.0)])
+@pytest.mark.parametrize("u,w", [(1e-5, 2e-5), (0.01, 0.03), (0.3, 0.2), (0.45, 4.0),
+                                 (0.5, 0.25), (0.2, 0.1)])
 def test_parabolic_coefficients_integrate_the_parabola(u, w):
+    """Optically thin intervals with spacing ratio u/w <= 2: the full
+    Olson-Kunasz parabola."""
     E, a, b, g = oracle.coef(True, u, w)
     ra, rb, rg = _lagrange_integrals(u, w)
     scale = float(-mpmath.expm1(-u))  # e0: the size of the sum alpha+beta+gamma
@@ -73,6 +75,45 @@ def test_parabolic_coefficients_integrate_the_parabola(u, w):
     for x, r in ((a, ra), (b, rb), (g, rg)):
         assert abs(x - float(r)) <= 1e-13 * scale, (u, w, x, float(r))
     assert abs(a + b + g - scale) <= 1e-14 * scale
+    assert g < 0.0
+
+
+def _linear_integrals(u):
+    um = mpmath.mpf(u)
+    ra = mpmath.quad(lambda t: (1 - t / um) * mpmath.exp(-(um - t)), [0, um])
+    rb = mpmath.quad(lambda t: (t / um) * mpmath.exp(-(um - t)), [0, um])
+    return ra, rb
+
+
+@pytest.mark.parametrize("u,w", [(1.0, 1.0), (2.0, 1.5), (30.0, 45.0), (300.0, 100.0),
+                                 (0.3, 0.05), (0.1, 0.02)])
+def test_thick_or_skewed_intervals_use_the_linear_weights(u, w):
+    """u >= 1 or u/w >= 4: the parabola is switched off, every weight of the
+    interval is non-negative."""
+    E, a, b, g = oracle.coef(True, u, w)
+    ra, rb = _linear_integrals(u)
+    scale = float(-mpmath.expm1(-u))
+    assert g == 0.0
+    assert abs(a - float(ra)) <= 1e-13 * scale and abs(b - float(rb)) <= 1e-13 * scale
+    assert a >= 0.0 and b >= 0.0
+
+
+def test_parabolic_weight_ramps_are_continuous():
+    """No jump in the coefficients across the blend ramps (u = 1/2, 1 and
+    u/w = 2, 4), and alpha+beta+gamma = e0 everywhere."""
+    for u0, w0 in ((0.5, 1.0), (1.0, 1.0), (0.4, 0.2), (0.4, 0.1)):
+        for du in (1e-9, -1e-9):
+            c1 = np.array(oracle.coef(True, u0 + du, w0))
+            c0 = np.array(oracle.coef(True, u0, w0))
+            assert np.max(np.abs(c1 - c0)) < 1e-7
+    rng = np.random.default_rng(1)
+    for u, w in 10 ** rng.uniform(-4, 2, (200, 2)):
+        E, a, b, g = oracle.coef(True, u, w)
+        e0 = -math.expm1(-u)
+        assert abs(a + b + g - e0) <= 1e-14 * e0
+        f = oracle.parab_weight(u, w)
+        assert 0.0 <= f <= 1.0
+        assert (f == 0.0) == (g == 0.0)
 
 
 @pytest.mark.parametrize("u", [1e-9, 0.02, 0.6, 7.0, 800.0])
@@ -104,7 +145,9 @@ def _analytic_I(tau, I_start, k0, k1, Sfun):
 def test_P9_polynomial_source_is_integrated_exactly(parabolic):
     rng = np.random.default_rng(7)
     K = 14
-    chil = 10.0 ** rng.uniform(-3, 1.3, K)  # chi*l per point: dtau from 1e-3 to ~20
+    # chi*l per point; the parabolic case stays where the full parabola applies
+    # (intervals <= 1/2, neighbouring intervals within a factor 2)
+    chil = rng.uniform(0.16, 0.3, K) if parabolic else 10.0 ** rng.uniform(-3, 1.3, K)
     # point optical depths: tau_k = sum_{i<k} chil_i + chil_k / 2 (entry at 0)
     tau = np.concatenate([[0.0], np.cumsum(chil)[:-1]]) + 0.5 * chil
     tau_m = [mpmath.mpf(0)]
