@@ -53,6 +53,12 @@ typedef enum {
 enum { RT3D_CARTESIAN_PERIODIC_XY = 0 };
 enum { RT3D_LINEAR = 0, RT3D_PARABOLIC = 1 };
 enum {
+    RT3D_ACCEL_NONE = 0,  /* ALI: J += [1 - Lambda*(1-eps)]^-1 (J_FS - J) */
+    RT3D_ACCEL_KRYLOV = 1 /* FGMRES on (1 - Lambda(1-eps)) J = Lambda(eps B) + J_bc,
+                             right-preconditioned by [1 - Lambda*(1-eps)]^-1 (the
+                             same OS operator; same fixed point as the ALI) */
+};
+enum {
     RT3D_FP64 = 0,            /* formal solution and ALI in FP64 */
     RT3D_FP32_FS_FP64_ALI = 1 /* FP32 formal solution, FP64 ALI/residual, FP64 refinement */
 };
@@ -66,6 +72,8 @@ typedef struct {
     int precision;    /* RT3D_FP64 or RT3D_FP32_FS_FP64_ALI */
     int nlambda;      /* reserved: must be 0 or 1 */
     void *cuda_stream;/* cudaStream_t to run on, or NULL for the legacy stream */
+    int accel;        /* rt3d_solve iteration: RT3D_ACCEL_NONE (plain ALI, Eq. alo
+                         with Jacobi OS solves) or RT3D_ACCEL_KRYLOV */
 } rt3d_grid_desc;
 
 /* Boundary intensities (Sec. 3.1: I = 0 incoming at the outer boundary; the

@@ -94,6 +94,14 @@ struct rt3d_grid {
     OsState *st = nullptr;
     bool lstar_valid = false;
 
+    // Krylov workspace (allocated on first use): basis V[0..m], preconditioned
+    // directions Z[0..m-1], their device pointer arrays, small scalars
+    static constexpr int kKrylov = 100;
+    bool krylov_ready = false;
+    double *V[kKrylov + 1] = {}, *Z[kKrylov] = {};
+    double **dV = nullptr, **dZ = nullptr, **dOne = nullptr;
+    double *dots = nullptr, *coef = nullptr;
+
     // instrumentation: formal-solution kernel time (CUDA events on the
     // grid's stream) and kernels launched
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -247,6 +255,8 @@ rt3d_status validate_desc(const rt3d_grid_desc *d) {
     if (d->precision != RT3D_FP64 && d->precision != RT3D_FP32_FS_FP64_ALI)
         return fail(RT3D_EINVAL, "bad precision %d", d->precision);
     if (d->nlambda > 1) return fail(RT3D_EINVAL, "nlambda > 1 is not supported by this call");
+    if (d->accel != RT3D_ACCEL_NONE && d->accel != RT3D_ACCEL_KRYLOV)
+        return fail(RT3D_EINVAL, "bad accel %d", d->accel);
     return RT3D_OK;
 }
 
@@ -393,6 +403,34 @@ rt3d_status grid_build(rt3d_grid *g) {
     return RT3D_OK;
 }
 
+// Convergence monitor of an iteration from its max relative changes:
+// contraction rho from the last `kWindow` changes, error estimate
+// rel * rho / (1 - rho), stagnation when the window shows no decrease.
+struct Progress {
+    static constexpr int kWindow = 10;
+    std::vector<double> h;
+    void add(double r) { h.push_back(r); }
+    double rho() const {
+        const int n = (int)h.size();
+        if (n < 2) return 0.9;
+        const int m = std::min(n - 1, kWindow);
+        const double a = h[n - 1 - m], b = h[n - 1];
+        if (!(a > 0.0) || !(b > 0.0)) return 0.0;
+        return std::min(std::pow(b / a, 1.0 / m), 0.999);
+    }
+    double error_estimate() const {
+        if (h.empty()) return 1.0;
+        const double r = rho();
+        return h.back() * r / (1.0 - r);
+    }
+    // no decrease over two windows: the changes sit at the rounding floor
+    bool stagnated() const {
+        const int n = (int)h.size();
+        if (n < 2 * kWindow + 1) return false;
+        return h[n - 1] > 0.7 * h[n - 1 - 2 * kWindow] && h.back() < 1e-2;
+    }
+};
+
 // Copies a device result to a caller array (device or host).
 rt3d_status deliver(rt3d_grid *g, double *dst, const double *src, size_t n) {
     if (!dst || dst == src) return RT3D_OK;
@@ -443,6 +481,203 @@ rt3d_status ali_iteration(rt3d_grid *g, const FsParams &fp, bool fp64, int max_s
     TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));
     CKL(launch_ali_update(N, g->J, g->dJ_dev, g->st, nullptr, g->stream));
     TRY(read_scalar_d(g, offsetof(OsState, rel), rel));
+    return RT3D_OK;
+}
+
+rt3d_status krylov_setup(rt3d_grid *g) {
+    if (g->krylov_ready) return RT3D_OK;
+    const size_t N = (size_t)g->N;
+    const int m = rt3d_grid::kKrylov;
+    for (int i = 0; i <= m; ++i) TRY(g->alloc(&g->V[i], N));
+    for (int i = 0; i < m; ++i) TRY(g->alloc(&g->Z[i], N));
+    TRY(g->alloc(&g->dV, m + 1));
+    TRY(g->alloc(&g->dZ, m));
+    TRY(g->alloc(&g->dOne, 1));
+    TRY(g->alloc(&g->dots, m + 1));
+    TRY(g->alloc(&g->coef, m + 1));
+    CK(cudaMemcpyAsync(g->dV, g->V, sizeof(double *) * (m + 1), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemcpyAsync(g->dZ, g->Z, sizeof(double *) * m, cudaMemcpyHostToDevice, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->krylov_ready = true;
+    return RT3D_OK;
+}
+
+// <V[i], w> for i < k (V = g->dV) into host out[k]
+rt3d_status kdots(rt3d_grid *g, double *const *Vdev, int k, const double *w, double *out) {
+    CK(cudaMemsetAsync(g->dots, 0, sizeof(double) * k, g->stream));
+    CKL(launch_multi_dot((int)g->N, Vdev, k, w, g->dots, g->stream));
+    CK(cudaMemcpyAsync(out, g->dots, sizeof(double) * k, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return RT3D_OK;
+}
+
+rt3d_status knorm(rt3d_grid *g, const double *w, double *out) {
+    CK(cudaMemcpyAsync(g->dOne, &w, sizeof(double *), cudaMemcpyHostToDevice, g->stream));
+    double d = 0.0;
+    TRY(kdots(g, g->dOne, 1, w, &d));
+    *out = std::sqrt(std::max(d, 0.0));
+    return RT3D_OK;
+}
+
+// w -= sum_i c[i] Vdev[i]
+rt3d_status kaxpy(rt3d_grid *g, double *w, double *const *Vdev, const double *c, int k) {
+    CK(cudaMemcpyAsync(g->coef, c, sizeof(double) * k, cudaMemcpyHostToDevice, g->stream));
+    CKL(launch_multi_axpy((int)g->N, w, Vdev, g->coef, k, g->stream));
+    CK(cudaStreamSynchronize(g->stream));  // c is host memory owned by the caller
+    return RT3D_OK;
+}
+
+// out = A v = v - Lambda_hom((1 - eps) v), formal solution in FP32 or FP64
+rt3d_status apply_A(rt3d_grid *g, const FsParams &fphom, bool fp64, const double *v, double *out) {
+    const int n = (int)g->N;
+    CKL(launch_source(n, v, g->eps, nullptr, fp64 ? g->chiS64 : g->chiS32, fp64, true, g->stream));
+    TRY(run_fs(g, fphom, fp64, false));
+    CKL(launch_sub(n, v, g->Jfs, out, g->stream));
+    return RT3D_OK;
+}
+
+// z = M^-1 v by Jacobi sweeps (the OS solve of Eq. alo)
+rt3d_status precond(rt3d_grid *g, const double *v, double *z) {
+    TRY(os_solve_dev(g, nullptr, nullptr, v, 50, 1e-3));
+    CKL(launch_copy_buf((int)g->N, g->dJ_dev, g->st, z, g->stream));
+    return RT3D_OK;
+}
+
+// One FGMRES cycle (right preconditioning, classical Gram-Schmidt applied
+// twice) for A x = r from x = 0. Stops when the residual estimate falls to
+// eta |r| or after kKrylov steps. Returns the achieved reduction and the
+// number of operator applications.
+rt3d_status fgmres(rt3d_grid *g, const FsParams &fphom, bool fp64, const double *r, double *x,
+                   double eta, int max_steps, double *achieved, int *steps) {
+    const int n = (int)g->N;
+    const int m = std::min(rt3d_grid::kKrylov, std::max(1, max_steps));
+    TRY(krylov_setup(g));
+    double beta = 0.0;
+    TRY(knorm(g, r, &beta));
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, g->stream));
+    *steps = 0;
+    *achieved = 0.0;
+    if (!(beta > 0.0)) return RT3D_OK;
+    if (!std::isfinite(beta)) return fail(RT3D_ENUMERIC, "non-finite residual norm");
+    CKL(launch_scale_copy(n, r, 1.0 / beta, g->V[0], g->stream));
+    std::vector<double> H((m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), gv(m + 1, 0.0), h(m + 1),
+        h2(m + 1);
+    gv[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+        TRY(precond(g, g->V[j], g->Z[j]));
+        TRY(apply_A(g, fphom, fp64, g->Z[j], g->V[j + 1]));
+        TRY(kdots(g, g->dV, j + 1, g->V[j + 1], h.data()));
+        TRY(kaxpy(g, g->V[j + 1], g->dV, h.data(), j + 1));
+        TRY(kdots(g, g->dV, j + 1, g->V[j + 1], h2.data()));
+        TRY(kaxpy(g, g->V[j + 1], g->dV, h2.data(), j + 1));
+        for (int i = 0; i <= j; ++i) h[i] += h2[i];
+        double hn = 0.0;
+        TRY(knorm(g, g->V[j + 1], &hn));
+        if (!std::isfinite(hn)) return fail(RT3D_ENUMERIC, "non-finite Krylov vector");
+        if (hn > 0.0) CKL(launch_scale_copy(n, g->V[j + 1], 1.0 / hn, g->V[j + 1], g->stream));
+        // Givens rotations on column j
+        for (int i = 0; i < j; ++i) {
+            const double a = h[i], b = h[i + 1];
+            h[i] = cs[i] * a + sn[i] * b;
+            h[i + 1] = -sn[i] * a + cs[i] * b;
+        }
+        const double a = h[j], b = hn;
+        const double den = std::hypot(a, b);
+        cs[j] = den > 0.0 ? a / den : 1.0;
+        sn[j] = den > 0.0 ? b / den : 0.0;
+        h[j] = den;
+        gv[j + 1] = -sn[j] * gv[j];
+        gv[j] = cs[j] * gv[j];
+        for (int i = 0; i <= j; ++i) H[i * m + j] = h[i];
+        k = j + 1;
+        if (std::fabs(gv[j + 1]) <= eta * beta || !(hn > 0.0)) break;
+    }
+    // back substitution H y = g, then x = sum y_i Z_i
+    std::vector<double> y(k, 0.0);
+    for (int i = k - 1; i >= 0; --i) {
+        double t = gv[i];
+        for (int l = i + 1; l < k; ++l) t -= H[i * m + l] * y[l];
+        y[i] = H[i * m + i] != 0.0 ? t / H[i * m + i] : 0.0;
+    }
+    for (int i = 0; i < k; ++i) y[i] = -y[i];
+    TRY(kaxpy(g, x, g->dZ, y.data(), k));
+    *achieved = std::fabs(gv[k]) / beta;
+    *steps = k;
+    return RT3D_OK;
+}
+
+// Krylov-accelerated solve with FP64 iterative refinement. Rounds: residual
+// r = J_FS(S(J)) - J (FP32 before the first converged cycle in the mixed
+// mode, FP64 afterwards), FGMRES cycle on A delta = r (A in the grid's FS
+// precision), J += delta. The error after a round is estimated as
+// gain * (next FP64 residual), gain = |delta|/|r| of the previous round;
+// the FP64 residual that meets tol is the certification.
+rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p,
+                         const FsParams &fphom, double tol, int max_iter, rt3d_solve_stats &s,
+                         bool *conv_out) {
+    const int n = (int)g->N;
+    const bool mixed = !g->fs64;
+    bool res64 = !mixed;
+    bool conv = false;
+    double gain = -1.0, est = 1.0, res = 0.0;
+    int it = 0, rounds32 = 0;
+    // Reduction asked of one FGMRES cycle: with an FP32 operator the basis
+    // carries rounding noise, so cycles stop at 1e-3 and the FP64 residual
+    // of the next round drives the refinement.
+    const double eta = mixed ? 1e-3 : 1e-4;
+    for (int round = 0; round < 60 && it < max_iter; ++round) {
+        // residual of the current J (the first one also builds Lambda*)
+        const bool fs64 = res64;
+        const bool build = !g->lstar_valid;
+        CKL(launch_source(n, g->J, g->eps, g->B, fs64 ? g->chiS64 : g->chiS32, fs64, false,
+                          g->stream));
+        TRY(run_fs(g, fs64 ? fp64p : fp, fs64, build));
+        if (fs64) ++s.fs_fp64;
+        else ++s.fs_fp32;
+        if (build) {
+            CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag,
+                               g->stream));
+            CK(cudaMemcpyAsync(g->chi_ref, g->chi, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                               g->stream));
+            CK(cudaMemcpyAsync(g->eps_ref, g->eps, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                               g->stream));
+            g->lstar_valid = true;
+        }
+        TRY(reset_scalar(g, offsetof(OsState, res), sizeof(unsigned long long)));
+        CKL(launch_residual(n, g->Jfs, g->J, g->r64, g->st, g->stream));
+        TRY(read_scalar_d(g, offsetof(OsState, res), &res));
+        if (!(res == res)) return fail(RT3D_ENUMERIC, "NaN in the residual");
+        if (fs64) s.residual64 = res;
+        // gain < 0: unknown (first round, or a residual relative to J = 0)
+        if (fs64 && gain >= 0.0) {
+            est = gain * res;
+            if (est <= tol) {
+                conv = true;
+                break;
+            }
+        }
+        double achieved = 0.0;
+        int steps = 0;
+        TRY(fgmres(g, fphom, g->fs64, g->r64, g->delta, eta, max_iter - it, &achieved, &steps));
+        it += steps;
+        if (g->fs64) s.fs_fp64 += steps;
+        else s.fs_fp32 += steps;
+        TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));
+        CKL(launch_axpy_rel(n, g->J, g->delta, g->st, g->stream));
+        double crel = 0.0;
+        TRY(read_scalar_d(g, offsetof(OsState, rel), &crel));
+        if (!(crel == crel)) return fail(RT3D_ENUMERIC, "NaN in the Krylov correction");
+        s.rel_change = crel;
+        gain = (res > 0.0 && std::isfinite(res)) ? crel / res : -1.0;
+        if (!res64) {
+            ++rounds32;
+            if (achieved <= eta || rounds32 >= 3) res64 = true;
+        }
+    }
+    s.iterations = it;
+    s.est_error = est;
+    *conv_out = conv;
     return RT3D_OK;
 }
 
@@ -586,36 +821,49 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     TRY(fs_params(g, bc, g->fs64, false, &fp));
     const int max_sweeps = 50;
     const double sweep_tol = 1e-3;
+    if (g->desc.accel == RT3D_ACCEL_KRYLOV) {
+        FsParams fp64k, fphomk;
+        TRY(fs_params(g, bc, true, false, &fp64k));
+        TRY(fs_params(g, nullptr, !g->fs64 ? false : true, true, &fphomk));
+        bool kconv = false;
+        TRY(krylov_solve(g, fp, fp64k, fphomk, tol, max_iter, s, &kconv));
+        TRY(deliver(g, J_inout, g->J, N));
+        CK(cudaStreamSynchronize(g->stream));
+        TRY(collect_events(g));
+        s.fs32_ms = g->fs_ms[0];
+        s.fs64_ms = g->fs_ms[1];
+        s.launches = g->launches;
+        s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        if (stats) *stats = s;
+        if (!kconv)
+            return fail(RT3D_ENOTCONVERGED, "not converged after %d iterations (est %.3g)",
+                        s.iterations, s.est_error);
+        return RT3D_OK;
+    }
 
     // Phase 1: ALI iterations in the grid's FS precision. The FP32 formal
     // solution carries rounding noise that the OS correction amplifies by up
     // to 1/(1 - Lambda*_vv (1-eps)); the changes then stop falling. Phase 1
-    // ends when the estimated error is below tol or the changes stagnate (no
-    // halving of the smallest change within 8 iterations).
-    double rel = 1.0, rel_prev = 0.0, est = 1.0, rel_min = 1e300;
-    int since_min = 0;
+    // ends when the estimated error is below tol (FP64), below the switch
+    // level (FP32), or when the changes stagnate.
+    double rel = 1.0, est = 1.0;
     bool conv = false;
     int it = 0;
+    Progress prog;
+    const double switch_at = g->fs64 ? tol : std::max(tol, 1e-6);
     while (it < max_iter) {
         TRY(ali_iteration(g, fp, g->fs64, max_sweeps, sweep_tol, &rel));
         ++it;
         if (g->fs64) ++s.fs_fp64;
         else ++s.fs_fp32;
         if (!(rel == rel)) return fail(RT3D_ENUMERIC, "NaN in the ALI change at iteration %d", it);
-        double rho = rel_prev > 0.0 ? rel / rel_prev : 0.9;
-        rho = std::min(std::max(rho, 0.0), 0.999);
-        est = rel * rho / (1.0 - rho);
-        rel_prev = rel;
-        if (rel < 0.5 * rel_min) {
-            rel_min = rel;
-            since_min = 0;
-        } else if (++since_min >= 8) {
-            break;  // stagnated
-        }
-        if (est <= tol && it >= 2) {
+        prog.add(rel);
+        est = prog.error_estimate();
+        if (est <= switch_at && it >= 2) {
             conv = g->fs64;
             break;
         }
+        if (prog.stagnated()) break;
     }
     s.rel_change = rel;
 
@@ -646,10 +894,10 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
             // delta_0 = M^-1 r64, then ALI on delta with the homogeneous FS
             TRY(os_solve_dev(g, nullptr, nullptr, g->r64, max_sweeps, sweep_tol));
             CKL(launch_copy_buf(n, g->dJ_dev, g->st, g->delta, g->stream));
-            double drel = 1.0, dprev = 0.0, dmin = 1e300, dacc = 1.0;
-            int dsince = 0;
+            double drel = 1.0, dacc = 1.0;
+            Progress dprog;
             const bool fs32 = mixed;
-            for (int inner = 0; inner < 400 && it < max_iter; ++inner) {
+            for (int inner = 0; inner < 1000 && it < max_iter; ++inner) {
                 CKL(launch_source(n, g->delta, g->eps, nullptr, fs32 ? g->chiS32 : g->chiS64, !fs32,
                                   true, g->stream));
                 TRY(run_fs(g, fphom, !fs32, false));
@@ -662,18 +910,10 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
                 CKL(launch_ali_update(n, g->delta, g->dJ_dev, g->st, nullptr, g->stream));
                 TRY(read_scalar_d(g, offsetof(OsState, rel), &drel));
                 if (!(drel == drel)) return fail(RT3D_ENUMERIC, "NaN in the defect correction");
-                double rho = dprev > 0.0 ? drel / dprev : 0.9;
-                rho = std::min(std::max(rho, 0.0), 0.999);
-                dacc = std::max(drel * rho / (1.0 - rho), drel);
-                dprev = drel;
+                dprog.add(drel);
+                dacc = std::max(dprog.error_estimate(), drel);
                 if (dacc <= 1e-4) break;
-                if (drel < 0.5 * dmin) {
-                    dmin = drel;
-                    dsince = 0;
-                } else if (++dsince >= 8) {
-                    dacc = std::max(dacc, 10.0 * dmin);  // stagnated at the FP32 floor
-                    break;
-                }
+                if (dprog.stagnated()) break;
             }
             // J += delta; size of the correction relative to J
             TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));

@@ -118,4 +118,12 @@ cudaError_t launch_compare(long long n, const double *a, const double *b, OsStat
 cudaError_t launch_copy_buf(int n, double *const *buf, const OsState *st, double *dst,
                             cudaStream_t s);
 
+// ---- Krylov vector kernels (krylov.cu) ----
+cudaError_t launch_multi_dot(int n, const double *const *V, int k, const double *w, double *out,
+                             cudaStream_t s);
+cudaError_t launch_multi_axpy(int n, double *w, const double *const *V, const double *coef, int k,
+                              cudaStream_t s);
+cudaError_t launch_scale_copy(int n, const double *src, double alpha, double *dst, cudaStream_t s);
+cudaError_t launch_sub(int n, const double *a, const double *b, double *out, cudaStream_t s);
+
 }  // namespace rt3d

@@ -31,6 +31,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ETIMEOUT, ENUMERIC = range(7)
 CARTESIAN_PERIODIC_XY = 0
 LINEAR, PARABOLIC = 0, 1
 FP64, FP32_FS_FP64_ALI = 0, 1
+ACCEL_NONE, ACCEL_KRYLOV = 0, 1
 
 _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 
@@ -38,7 +39,7 @@ _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 class GridDesc(ctypes.Structure):
     _fields_ = [("geometry", _c_int), ("n", _c_int * 3), ("ntheta", _c_int), ("nphi", _c_int),
                 ("interp", _c_int), ("precision", _c_int), ("nlambda", _c_int),
-                ("cuda_stream", _vp)]
+                ("cuda_stream", _vp), ("accel", _c_int)]
 
 
 class BC(ctypes.Structure):
@@ -169,7 +170,7 @@ def _stream_handle(stream):
 
 # ------------------------------------------------------------- the C ABI
 def grid_create(n, ntheta: int, nphi: int, interp: int = LINEAR, precision: int = FP64,
-                stream=None, geometry: int = CARTESIAN_PERIODIC_XY):
+                stream=None, geometry: int = CARTESIAN_PERIODIC_XY, accel: int = ACCEL_KRYLOV):
     lib = load()
     if np.isscalar(n):
         n = (int(n),) * 3
@@ -179,6 +180,7 @@ def grid_create(n, ntheta: int, nphi: int, interp: int = LINEAR, precision: int 
     d.ntheta, d.nphi = int(ntheta), int(nphi)
     d.interp, d.precision, d.nlambda = int(interp), int(precision), 1
     d.cuda_stream = _stream_handle(stream)
+    d.accel = int(accel)
     h = _vp()
     _check(lib.rt3d_grid_create(ctypes.byref(d), ctypes.byref(h)))
     return h
@@ -246,13 +248,14 @@ def solve(h, chi, eps, B, bc, J_inout, tol: float = 1e-8, max_iter: int = 2000,
 class Grid:
     """Owning wrapper of an rt3d_grid handle."""
 
-    def __init__(self, n, ntheta, nphi, interp=LINEAR, precision=FP64, stream=None):
+    def __init__(self, n, ntheta, nphi, interp=LINEAR, precision=FP64, stream=None,
+                 accel=ACCEL_KRYLOV):
         if np.isscalar(n):
             n = (int(n),) * 3
         self.n = tuple(int(v) for v in n)
         self.shape = (self.n[2], self.n[1], self.n[0])
         self.N = self.n[0] * self.n[1] * self.n[2]
-        self.handle = grid_create(n, ntheta, nphi, interp, precision, stream)
+        self.handle = grid_create(n, ntheta, nphi, interp, precision, stream, accel=accel)
 
     def close(self):
         if self.handle:

@@ -197,11 +197,13 @@ def _golden33():
     return np.array(vals)
 
 
+@pytest.mark.parametrize("accel", ["ali", "krylov"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_solve_box33_matches_golden(rt3d, precision):
+def test_solve_box33_matches_golden(rt3d, precision, accel):
     chi, eps, B, bc = inputs.cartesian_config(33, 1e-2)
     prec = rt3d.FP64 if precision == "fp64" else rt3d.FP32_FS_FP64_ALI
-    g = rt3d.Grid(33, 8, 16, rt3d.LINEAR, prec)
+    acc = rt3d.ACCEL_NONE if accel == "ali" else rt3d.ACCEL_KRYLOV
+    g = rt3d.Grid(33, 8, 16, rt3d.LINEAR, prec, accel=acc)
     J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
     st = g.solve(dev(chi), dev(eps), dev(B), dev_bc(bc), J, tol=1e-9, max_iter=3000)
     ref = _golden33()[:, None, None]
@@ -210,14 +212,16 @@ def test_solve_box33_matches_golden(rt3d, precision):
     assert st["residual64"] < 1e-8
 
 
+@pytest.mark.parametrize("accel", ["ali", "krylov"])
 @pytest.mark.parametrize("parabolic", [False, True])
-def test_solve_field_matches_oracle(rt3d, parabolic):
+def test_solve_field_matches_oracle(rt3d, parabolic, accel):
     n = (14, 12, 11)
     chi, eps, B, bc = inputs.cartesian_config(n, 1e-4, seed=3)
     Jo, it, _, _ = oracle.ali_solve(chi, eps, B, 4, 8, parabolic, bc, tol=1e-13, max_iter=3000)
     assert it > 0
+    acc = rt3d.ACCEL_NONE if accel == "ali" else rt3d.ACCEL_KRYLOV
     for prec in (rt3d.FP64, rt3d.FP32_FS_FP64_ALI):
-        g = rt3d.Grid(n, 4, 8, int(parabolic), prec)
+        g = rt3d.Grid(n, 4, 8, int(parabolic), prec, accel=acc)
         J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
         st = g.solve(dev(chi), dev(eps), dev(B), dev_bc(bc), J, tol=1e-9, max_iter=3000)
         err = relerr(J.cpu().numpy(), Jo)
