@@ -306,6 +306,34 @@ def run_ours(args):
     return 0
 
 
+def run_kernels(args):
+    """Profiling workload (no timing): the workload's grid, two FP32 formal
+    solutions, one with Lambda*, one FP64 formal solution (if --fp64-fs), and
+    a short OS solve. Used under ncu for per-kernel counters."""
+    import torch
+
+    from paper_2102_01734_gb300 import build, inputs, rt3d
+
+    build.build()
+    cfg = inputs.CONFIGS[WORKLOAD]
+    chi, eps, B, bc = inputs.cartesian_config(cfg["n"], cfg["eps"], seed=cfg["seed"])
+    dev = torch.device("cuda")
+    tchi, teps, tB = (torch.from_numpy(a).to(dev) for a in (chi, eps, B))
+    tbc = {"I_top": 0.0, "I_bottom": torch.from_numpy(bc["I_bottom"]).to(dev)}
+    g = rt3d.Grid(cfg["n"], cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+    J = g.formal_solution(tchi, tB, tbc)
+    J = g.formal_solution(tchi, tB, tbc)
+    J, L = g.formal_solution(tchi, tB, tbc, lstar=True)
+    r = J - tB
+    g.os_solve(L, teps, r, max_sweeps=4, tol=0.0)
+    if args.fp64_fs:
+        g64 = rt3d.Grid(cfg["n"], cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, rt3d.FP64)
+        g64.formal_solution(tchi, tB, tbc)
+    torch.cuda.synchronize()
+    print("kernels done")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,7 +345,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-angles", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels", action="store_true",
+                    help="run the profiling workload (for ncu) instead of the benchmark")
+    ap.add_argument("--fp64-fs", action="store_true", help="with --kernels: add an FP64 FS")
     args = ap.parse_args()
+    if args.kernels:
+        return run_kernels(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
