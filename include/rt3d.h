@@ -176,6 +176,33 @@ rt3d_status rt3d_solve(rt3d_grid *grid, const double *chi, const double *eps, co
                        const rt3d_bc *bc, double *J_inout, double tol, int max_iter,
                        rt3d_solve_stats *stats);
 
+/* Allocation-free Jacobi OS solve. No counterpart in the paper: this is a
+ * library service for callers that cannot allocate device memory, such as a
+ * host application whose device memory is entirely pre-reserved by its own
+ * pool allocator, or a time-critical loop that must not call cudaMalloc or
+ * cudaFree (both synchronise the device).
+ *
+ * Computes the same result as rt3d_os_solve on an RT3D_FP64 grid
+ * ([1 - Lambda*(1-eps)] dJ = r by Jacobi sweeps from dJ^0 = r/diag, stop when
+ * max|dJ^{m+1} - dJ^m| <= tol max|dJ^{m+1}| or after max_sweeps, 1..256)
+ * without a grid and without allocating: the caller passes device arrays
+ * lstar double[27][N] (layout of rt3d_formal_solution), eps, r and dJ_out
+ * double[N], N = nx*ny*nz <= RT3D_NOALLOC_MAX_VOXELS (host pointers, larger
+ * grids or nx, ny < 4 return RT3D_EINVAL). The only scratch is a fixed
+ * file-scope device array of 2 * RT3D_NOALLOC_MAX_VOXELS doubles (1 MiB,
+ * held by every GPU that loads the library until the process exits).
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture. All calls share the array: calls whose work
+ * overlaps on the GPU race and must be serialised. Work runs on cuda_stream
+ * (NULL: legacy stream); the call returns after it completes. sweeps_out
+ * (nullable, host) receives the number of sweeps. */
+#define RT3D_NOALLOC_MAX_VOXELS 65536
+rt3d_status rt3d_os_solve_noalloc(int nx, int ny, int nz, const double *lstar,
+                                  const double *eps, const double *r, double *dJ_out,
+                                  int max_sweeps, double tol, int *sweeps_out,
+                                  void *cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *rt3d_last_error(void);
 

@@ -683,6 +683,8 @@ rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p
 
 }  // namespace
 
+void rt3d::set_last_error(const char *msg) { g_err = msg; }
+
 extern "C" {
 
 const char *rt3d_last_error(void) { return g_err.c_str(); }

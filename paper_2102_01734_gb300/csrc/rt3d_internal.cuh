@@ -118,6 +118,9 @@ cudaError_t launch_compare(long long n, const double *a, const double *b, OsStat
 cudaError_t launch_copy_buf(int n, double *const *buf, const OsState *st, double *dst,
                             cudaStream_t s);
 
+// Sets the message returned by rt3d_last_error() on this thread.
+void set_last_error(const char *msg);
+
 // ---- Krylov vector kernels (krylov.cu) ----
 cudaError_t launch_multi_dot(int n, const double *const *V, int k, const double *w, double *out,
                              cudaStream_t s);

@@ -90,6 +90,8 @@ def load(path: str | None = None):
     lib.rt3d_os_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, _c_int, _c_double, P(_c_int)]
     lib.rt3d_ali_step.argtypes = [_vp, _vp, _vp, _vp, P(BC), _vp, P(_c_double)]
     lib.rt3d_solve.argtypes = [_vp, _vp, _vp, _vp, P(BC), _vp, _c_double, _c_int, P(SolveStats)]
+    lib.rt3d_os_solve_noalloc.argtypes = [_c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _c_int,
+                                          _c_double, P(_c_int), _vp]
     lib.rt3d_last_error.restype = ctypes.c_char_p
     lib.rt3d_last_error.argtypes = []
     _lib = lib
@@ -219,6 +221,21 @@ def os_solve(h, lstar, eps, r, dJ_out, max_sweeps: int = 50, tol: float = 1e-3) 
     m = _c_int(0)
     _check(load().rt3d_os_solve(h, _ptr(lstar), _ptr(eps), _ptr(r), _ptr(dJ_out), max_sweeps,
                                 tol, ctypes.byref(m)))
+    return m.value
+
+
+NOALLOC_MAX_VOXELS = 65536
+
+
+def os_solve_noalloc(n, lstar, eps, r, dJ_out, max_sweeps: int = 50, tol: float = 1e-3,
+                     stream=None) -> int:
+    """Allocation-free Jacobi OS solve (device arrays only, N <= 65536):
+    for callers that cannot allocate device memory. Returns the sweeps."""
+    nx, ny, nz = (int(v) for v in n)
+    m = _c_int(0)
+    _check(load().rt3d_os_solve_noalloc(nx, ny, nz, _ptr(lstar), _ptr(eps), _ptr(r),
+                                        _ptr(dJ_out), max_sweeps, tol, ctypes.byref(m),
+                                        _stream_handle(stream)))
     return m.value
 
 
