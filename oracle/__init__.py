@@ -61,6 +61,17 @@ def _load():
                                       c_double, _dp, c_double, _dp, _dp, c_double, c_int, c_int,
                                       c_double, c_int, _dp, _dp]
         lib.orc_ali_solve.restype = c_int
+        lib.orc_sph_trace_voxel.argtypes = [c_int, c_int, c_int, c_double, c_double, _dp, c_int,
+                                            c_int, _ip, _dp, _ip, _dp]
+        lib.orc_sph_trace_voxel.restype = c_int
+        lib.orc_sph_kcap.argtypes = [c_int, c_int, c_int]
+        lib.orc_sph_kcap.restype = c_int
+        lib.orc_sph_rays.argtypes = [c_int, c_int, c_int, c_double, c_double, c_int, c_int, c_int,
+                                     _ip]
+        lib.orc_sph_rays.restype = c_int
+        lib.orc_fs_sph.argtypes = [c_int, c_int, c_int, c_double, c_double, c_int, c_int, c_int,
+                                   _dp, _dp, _dp, c_double, c_double, _dp, _dp]
+        lib.orc_fs_sph.restype = c_int
         _lib = lib
     return _lib
 
@@ -254,3 +265,49 @@ def direct_solve(chi, eps, B, ntheta: int, nphi: int, parabolic: bool = False, b
     rhs = M @ (eps_f * B_f) + Jbc
     A = np.eye(chi.size) - M * (1.0 - eps_f)[None, :]
     return np.linalg.solve(A, rhs).reshape(chi.shape)
+
+
+# ------------------------------------------------------------ spherical grid
+def sph_trace(n, d, v, r_in=1.0, r_out=1.3):
+    """Cells, chords, entry-through-core flag and entry point of the ray that
+    voxel v launches in direction d on the (nr, nt, np) spherical grid."""
+    lib = _load()
+    nr, nt, np_ = n
+    cap = lib.orc_sph_kcap(nr, nt, np_)
+    vox = np.zeros(cap, dtype=np.int32)
+    ln = np.zeros(cap)
+    ec = ctypes.c_int()
+    pin = np.zeros(3)
+    d = _f64(d)
+    K = lib.orc_sph_trace_voxel(nr, nt, np_, r_in, r_out, _ptr(d), int(v), cap,
+                                vox.ctypes.data_as(_ip), _ptr(ln), ctypes.byref(ec), _ptr(pin))
+    if K < 0:
+        raise RuntimeError("spherical trace failed")
+    return vox[:K].copy(), ln[:K].copy(), bool(ec.value), pin
+
+
+def sph_rays(n, ntheta, nphi, o, r_in=1.0, r_out=1.3):
+    """Launching voxels of the ray set of solid angle o."""
+    lib = _load()
+    nr, nt, np_ = n
+    launch = np.zeros(nr * nt * np_, dtype=np.int32)
+    k = lib.orc_sph_rays(nr, nt, np_, r_in, r_out, ntheta, nphi, int(o), launch.ctypes.data_as(_ip))
+    if k < 0:
+        raise RuntimeError("spherical ray set failed")
+    return launch[:k].copy()
+
+
+def fs_sph(chi, S, B, ntheta, nphi, parabolic=False, I_out=0.0, I_irr=0.0, lstar=False,
+           r_in=1.0, r_out=1.3):
+    """Formal solution on the spherical grid; arrays shaped (np, nt, nr)
+    (r fastest: v = ir + nr (it + nt ip))."""
+    lib = _load()
+    chi, S, B = _f64(chi), _f64(S), _f64(B)
+    np_, nt, nr = chi.shape
+    J = np.zeros(chi.shape)
+    L = np.zeros((chi.size, 27)) if lstar else None
+    err = lib.orc_fs_sph(nr, nt, np_, r_in, r_out, ntheta, nphi, int(parabolic), _ptr(chi),
+                         _ptr(S), _ptr(B), float(I_out), float(I_irr), _ptr(J), _ptr(L))
+    if err:
+        raise RuntimeError(f"spherical formal solution failed ({err})")
+    return (J, L) if lstar else J
