@@ -334,6 +334,106 @@ def run_kernels(args):
     return 0
 
 
+def run_warmstart(args):
+    """Learned warm start (spec pattern, not in the paper): training data
+    are converged solutions the method produces on 32 x 32 x nz boxes (the
+    vertical structure of the evaluation box), eps = 1e-6 and eps from the
+    batched generator; evaluation: a held-out nz^3 box, eps = 1e-6, solve from
+    J = B against solve from the network's prediction (FP32 formal solutions
+    and wall time to the same certified tolerance)."""
+    import torch
+
+    from paper_2102_01734_gb300 import build, inputs, rt3d, warmstart
+
+    build.build()
+    nz = args.ws_n
+    nth, nph = args.ws_angles
+    t0 = time.perf_counter()
+    gtrain = rt3d.Grid((32, 32, nz), nth // 2, nph // 2, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+    eps_l, _ = inputs.batched_wavelengths(args.ws_fields, seed=3)
+    seeds = list(range(1000, 1000 + args.ws_fields))
+    eps_of = lambda s: 1e-6 if s % 2 == 0 else max(float(eps_l[s - 1000]), 1e-6)
+    data = warmstart.solve_fields(gtrain, (nz, 32, 32), seeds, eps_of, tol=1e-8)
+    t_data = time.perf_counter() - t0
+    net = warmstart.UNet(seed=0)
+    t0 = time.perf_counter()
+    hist = warmstart.train(net, data, args.ws_steps, log_every=max(1, args.ws_steps // 10))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del gtrain
+    # evaluation on a held-out box
+    chi, eps, B, bc = inputs.cartesian_config(nz, 1e-6, seed=9000)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    tchi, teps, tB = d(chi), d(eps), d(B)
+    tbc = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}
+    g = rt3d.Grid(nz, nth, nph, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+    res = {}
+    for name in ("B", "net"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if name == "B":
+            J = tB.clone()
+        else:
+            J = net.predict(tchi[None], teps[None], tB[None], tB[None])[0].contiguous()
+        J0 = J.clone()
+        st = g.solve(tchi, teps, tB, tbc, J, tol=args.tol, max_iter=args.max_iter)
+        torch.cuda.synchronize()
+        res[name] = {"seconds": time.perf_counter() - t0, "fs_fp32": st["fs_fp32"],
+                     "fs_fp64": st["fs_fp64"], "iterations": st["iterations"],
+                     "start_error_max": float(torch.max(torch.abs(torch.log(J0 / J)))),
+                     "residual64": st["residual64"]}
+    Jn, JB = None, None
+    out = {"mode": "warmstart", "eval_grid": [nz, nz, nz], "angles": [nth, nph],
+           "train": {"fields": len(data), "box": [32, 32, nz], "angles": [nth // 2, nph // 2],
+                     "steps": args.ws_steps, "seconds_data": t_data, "seconds_train": t_train,
+                     "params": net.n_params(), "loss_history": hist},
+           "solve_from_B": res["B"], "solve_from_net": res["net"],
+           "speedup_solves_per_s": res["B"]["seconds"] / res["net"]["seconds"]}
+    print(json.dumps(out))
+    return 0
+
+
+def run_batched(args):
+    """Batched wavelengths (97^3 box of the k^-3 field, seed 1, 16 x 32 angles,
+    parabolic; per wavelength eps log-uniform in [1e-8, 1e-1] and opacity scale
+    10^U(-3, 3), seed 3): one rt3d_solve_batched call (FP32 batched ALI under a
+    replayed CUDA graph with device-side retirement, then FP64 refinement and
+    certification per wavelength)."""
+    import torch
+
+    from paper_2102_01734_gb300 import build, inputs, rt3d
+
+    build.build()
+    n = args.batch_n
+    nl = args.batch_lambdas
+    chi, _, B, bc = inputs.cartesian_config(n, 1e-2, seed=1)
+    eps_l, scale_l = inputs.batched_wavelengths(nl, seed=3)
+    dv = torch.device("cuda")
+    tchi = torch.from_numpy(chi).to(dv)
+    chis = torch.stack([float(s) * tchi for s in scale_l]).contiguous()
+    epss = torch.stack([torch.full_like(tchi, float(e)) for e in eps_l]).contiguous()
+    tB = torch.from_numpy(B).to(dv)
+    Bs = tB.expand(nl, *tB.shape).contiguous()
+    bots = torch.from_numpy(bc["I_bottom"]).to(dv).expand(nl, n, n).contiguous()
+    g = rt3d.Grid(n, 16, 32, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+    seg = g.info()["segments"]
+    J = Bs.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = g.solve_batched(chis, epss, Bs, {"I_top": 0.0, "I_bottom": bots}, J, tol=args.tol,
+                         max_iter=args.max_iter, raise_on_nonconv=False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    per = st.pop("per_lambda")
+    out = {"mode": "batched", "grid": [n, n, n], "angles": [16, 32], "nlambda": nl,
+           "seconds": dt, "lambda_solves_per_s": int(st["converged"]) / dt,
+           "batched_phase_segments_per_s": (st["fs_lambda32"] - nl) * seg / (st["batch_ms"] / 1e3)
+           if st["batch_ms"] > 0 else None,
+           "stats": st, "not_converged": int(np.sum(per != 0))}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,9 +448,22 @@ def main():
     ap.add_argument("--kernels", action="store_true",
                     help="run the profiling workload (for ncu) instead of the benchmark")
     ap.add_argument("--fp64-fs", action="store_true", help="with --kernels: add an FP64 FS")
+    ap.add_argument("--batched", action="store_true", help="batched-wavelength measurement")
+    ap.add_argument("--batch-n", type=int, default=97)
+    ap.add_argument("--batch-lambdas", type=int, default=32)
+    ap.add_argument("--warmstart", action="store_true",
+                    help="train the learned warm start and evaluate it")
+    ap.add_argument("--ws-n", type=int, default=193)
+    ap.add_argument("--ws-angles", type=int, nargs=2, default=[32, 64])
+    ap.add_argument("--ws-fields", type=int, default=24)
+    ap.add_argument("--ws-steps", type=int, default=600)
     args = ap.parse_args()
     if args.kernels:
         return run_kernels(args)
+    if args.warmstart:
+        return run_warmstart(args)
+    if args.batched:
+        return run_batched(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -50,7 +50,12 @@ typedef enum {
     RT3D_ENUMERIC = 6        /* NaN/Inf met in a residual or change */
 } rt3d_status;
 
-enum { RT3D_CARTESIAN_PERIODIC_XY = 0 };
+enum {
+    RT3D_CARTESIAN_PERIODIC_XY = 0, /* n = (nx, ny, nz) unit voxels, periodic in x, y */
+    RT3D_SPHERICAL = 1              /* n = (nr, ntheta, nphi) cells between r_in and r_out
+                                       (log-spaced in r, uniform in theta and phi,
+                                       periodic in phi); voxel v = ir + nr (it + nt ip) */
+};
 enum { RT3D_LINEAR = 0, RT3D_PARABOLIC = 1 };
 enum {
     RT3D_ACCEL_NONE = 0,  /* ALI: J += [1 - Lambda*(1-eps)]^-1 (J_FS - J) */
@@ -65,7 +70,8 @@ enum {
 
 typedef struct {
     int geometry;     /* RT3D_CARTESIAN_PERIODIC_XY */
-    int n[3];         /* nx, ny, nz: 4 <= nx, ny <= 2047, 1 <= nz <= 1023 */
+    int n[3];         /* nx, ny, nz: 4 <= nx, ny <= 2047, 1 <= nz <= 1023,
+                         4 nx ny nz < 2^31 */
     int ntheta, nphi; /* direction set: mu_i = -1 + (2i+1)/ntheta,
                          phi_j = (2j+1) pi / nphi, weight 1/(ntheta nphi) */
     int interp;       /* RT3D_LINEAR or RT3D_PARABOLIC source interpolation */
@@ -74,6 +80,7 @@ typedef struct {
     void *cuda_stream;/* cudaStream_t to run on, or NULL for the legacy stream */
     int accel;        /* rt3d_solve iteration: RT3D_ACCEL_NONE (plain ALI, Eq. alo
                          with Jacobi OS solves) or RT3D_ACCEL_KRYLOV */
+    double r_in, r_out; /* RT3D_SPHERICAL: core and outer radius (0 < r_in < r_out) */
 } rt3d_grid_desc;
 
 /* Boundary intensities (Sec. 3.1: I = 0 incoming at the outer boundary; the
@@ -86,7 +93,13 @@ typedef struct {
     double I_bottom;
     const double *I_top_face;
     const double *I_bottom_face;
+    double I_irr;     /* RT3D_SPHERICAL: irradiation entering the outer sphere at
+                         points with x > 0 along directions with d_x < 0 */
 } rt3d_bc;
+/* On a spherical grid I_top (or I_top_face, unused) is the intensity entering
+ * the outer sphere outside the irradiated part, I_bottom / I_bottom_face
+ * ([nphi][ntheta], index it + nt ip) the intensity leaving the core into the
+ * first cell of a characteristic. */
 
 typedef struct {
     int iterations;     /* ALI iterations of the main loop */
@@ -133,6 +146,14 @@ rt3d_status rt3d_grid_get_info(const rt3d_grid *grid, rt3d_grid_info *info);
 rt3d_status rt3d_grid_template(const rt3d_grid *grid, int angle, int *K, int32_t *vox,
                                double *len);
 
+/* One characteristic of the spherical grid's cache: ray `index` (0-based) of
+ * solid angle `angle`: points K (in/out capacity), cells vox[K], FP64 chords
+ * len[K], the voxel that launched it, and its boundary kind (0 outer sphere,
+ * 1 outer sphere irradiated, 2 core). Host memory. Returns RT3D_EINVAL past
+ * the last ray of the angle. */
+rt3d_status rt3d_grid_sph_ray(const rt3d_grid *grid, int angle, int index, int *K, int32_t *vox,
+                              double *len, int *launch, int *kind);
+
 /* Formal solution J = Lambda S (Eq. frmsol) over all solid angles, in the
  * grid's precision (FP64, or FP32 for RT3D_FP32_FS_FP64_ALI; results are
  * returned as double either way):
@@ -175,6 +196,38 @@ rt3d_status rt3d_ali_step(rt3d_grid *grid, const double *chi, const double *eps,
 rt3d_status rt3d_solve(rt3d_grid *grid, const double *chi, const double *eps, const double *B,
                        const rt3d_bc *bc, double *J_inout, double tol, int max_iter,
                        rt3d_solve_stats *stats);
+
+typedef struct {
+    int nlambda;            /* wavelengths in the batch */
+    int converged;          /* wavelengths certified converged */
+    int iterations;         /* batched ALI iterations (graph replays) */
+    int graph_replays;      /* replays of the captured iteration graph */
+    long long fs_lambda32;  /* single-wavelength FP32 formal solutions done */
+    long long fs_lambda64;  /* single-wavelength FP64 formal solutions done */
+    double max_est_error;   /* largest estimated relative error of a returned J */
+    double max_residual64;  /* largest certifying FP64 residual */
+    double batch_ms;        /* device time of the batched iterations */
+    double fs32_ms, fs64_ms;
+    double seconds;
+    long long launches;
+} rt3d_batch_stats;
+
+/* Batched wavelengths (Sec. 4.1: the geometry is the same for all wavelength
+ * points): n_lambda independent problems on the grid's geometry. chi, eps, B
+ * and J_inout are double[n_lambda][N] (wavelength-major); face arrays of bc,
+ * when given, are double[n_lambda][ny][nx]. Phase 1 iterates the ALI of all
+ * wavelengths together in FP32 (one captured CUDA graph per iteration,
+ * replayed; a wavelength retires on the device when its estimated error is
+ * below max(tol, 1e-6) or its changes stagnate); phase 2 refines and certifies
+ * every wavelength with the FP64 residual of rt3d_solve's Krylov scheme.
+ * status_out (nullable, host int[n_lambda]) receives RT3D_OK,
+ * RT3D_ENOTCONVERGED or RT3D_ENUMERIC per wavelength. Returns
+ * RT3D_ENOTCONVERGED if any wavelength is not certified. Device memory grows
+ * by about (8 * 8 + 4 * 26 + 4 * 16) n_lambda N bytes on first use. */
+rt3d_status rt3d_solve_batched(rt3d_grid *grid, int nlambda, const double *chi,
+                               const double *eps, const double *B, const rt3d_bc *bc,
+                               double *J_inout, double tol, int max_iter, int *status_out,
+                               rt3d_batch_stats *stats);
 
 /* Allocation-free Jacobi OS solve. No counterpart in the paper: this is a
  * library service for callers that cannot allocate device memory, such as a

@@ -236,7 +236,7 @@ def ali_solve(chi, eps, B, ntheta: int, nphi: int, parabolic: bool = False, bc=N
                            _ptr(B), t, _ptr(tf), b, _ptr(bf), _ptr(J), tol, max_iter,
                            max_sweeps, sweep_tol, nthreads or default_threads(), _ptr(L),
                            _ptr(hist))
-    if it <= -1000:
+    if it <= -1000000:
         raise RuntimeError(f"oracle ALI failed ({it}): non-finite J or tracing error")
     return J, it, hist[:abs(it)], L
 

@@ -618,6 +618,6 @@ int orc_ali_solve(int nx, int ny, int nz, int nth, int nph, int parabolic,
     }
     free(S); free(Jfs); free(r); free(dJ);
     if (!lstar_out) free(L);
-    if (err) return -1000 + err;
+    if (err) return -1000000 + err;
     return conv ? it : -it;
 }

@@ -46,8 +46,8 @@ def _stale(sources, headers) -> bool:
 
 def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
     sources = sorted(glob.glob(os.path.join(SRC_DIR, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(SRC_DIR, "*.cuh"))) + [
-        os.path.join(INC_DIR, "rt3d.h")]
+    headers = sorted(glob.glob(os.path.join(SRC_DIR, "*.cuh"))) + sorted(
+        glob.glob(os.path.join(INC_DIR, "*.h")))
     if not force and not _stale(sources, headers):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)

@@ -51,31 +51,66 @@ __device__ __forceinline__ void block_max_atomic(double x, unsigned long long *d
     __syncthreads();  // sm[] is reused by a following call
 }
 
-__global__ void pack_kernel(int n, const double *chi, double scale, const double *S, void *out,
-                            bool fp64) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const double c = chi[v] * scale, s = S[v];
-        if (fp64) static_cast<double2 *>(out)[v] = make_double2(c, s);
-        else static_cast<float2 *>(out)[v] = make_float2((float)c, (float)s);
+// Packed (chi, S) written to the four replicas of every voxel.
+__global__ void pack_kernel(int nx, int ny, int nz, const double *chi, double scale,
+                            const double *S, void *out, bool fp64) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+        const double c = chi[v] * scale, sv = S[v];
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                const long long r = rep_index(x + a * nx, y + b * ny, z, nx, ny);
+                if (fp64) static_cast<double2 *>(out)[r] = make_double2(c, sv);
+                else static_cast<float2 *>(out)[r] = make_float2((float)c, (float)sv);
+            }
     }
 }
 
 // S = (1 - eps) J + eps B (or (1 - eps) J for the homogeneous problem),
-// written into the S half of the packed (chi, S) array.
-__global__ void source_kernel(int n, const double *J, const double *eps, const double *B,
-                              void *out, bool fp64, bool homogeneous) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+// written into the S half of the four replicas of the packed (chi, S).
+__global__ void source_kernel(int nx, int ny, int nz, const double *J, const double *eps,
+                              const double *B, void *out, bool fp64, bool homogeneous) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
         const double e = eps[v];
-        double s = (1.0 - e) * J[v];
-        if (!homogeneous) s += e * B[v];
-        if (fp64) static_cast<double2 *>(out)[v].y = s;
-        else static_cast<float2 *>(out)[v].y = (float)s;
+        double sv = (1.0 - e) * J[v];
+        if (!homogeneous) sv += e * B[v];
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                const long long r = rep_index(x + a * nx, y + b * ny, z, nx, ny);
+                if (fp64) static_cast<double2 *>(out)[r].y = sv;
+                else static_cast<float2 *>(out)[r].y = (float)sv;
+            }
     }
+}
+
+// neighbour index of (x, y, z) + (dx, dy, dz) with the periodic axes wrapped;
+// -1 outside a non-periodic axis
+__device__ __forceinline__ long long nb_index(int x, int y, int z, int dx, int dy, int dz, int nx,
+                                              int ny, int nz, Periodic per) {
+    int xx = x + dx, yy = y + dy, zz = z + dz;
+    if (xx < 0 || xx >= nx) {
+        if (!per.x) return -1;
+        xx += xx < 0 ? nx : -nx;
+    }
+    if (yy < 0 || yy >= ny) {
+        if (!per.y) return -1;
+        yy += yy < 0 ? ny : -ny;
+    }
+    if (zz < 0 || zz >= nz) {
+        if (!per.z) return -1;
+        zz += zz < 0 ? nz : -nz;
+    }
+    return xx + (long long)nx * (yy + (long long)ny * zz);
 }
 
 template <typename A>
 __global__ void os_prep_kernel(int nx, int ny, int nz, const double *L, const double *eps, A *a,
-                               double *inv_diag) {
+                               double *inv_diag, Periodic per) {
     const long long N = (long long)nx * ny * nz;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
          v += (long long)gridDim.x * blockDim.x) {
@@ -84,18 +119,9 @@ __global__ void os_prep_kernel(int nx, int ny, int nz, const double *L, const do
         int plane = 0;
         for (int d = 0; d < 27; ++d) {
             if (d == 13) continue;
-            const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-            const int zz = z + dz;
+            const long long u = nb_index(x, y, z, d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1, nx, ny, nz, per);
             double val = 0.0;
-            if (zz >= 0 && zz < nz) {
-                int xx = x + dx, yy = y + dy;
-                if (xx < 0) xx += nx;
-                if (xx >= nx) xx -= nx;
-                if (yy < 0) yy += ny;
-                if (yy >= ny) yy -= ny;
-                const long long u = xx + (long long)nx * (yy + (long long)ny * zz);
-                val = L[(long long)d * N + v] * (1.0 - eps[u]);
-            }
+            if (u >= 0) val = L[(long long)d * N + v] * (1.0 - eps[u]);
             a[(long long)plane * N + v] = (A)val;
             ++plane;
         }
@@ -129,7 +155,7 @@ __global__ void __launch_bounds__(256) os_sweep_kernel(int nx, int ny, int nz, c
                                                        const double *__restrict__ r,
                                                        const double *__restrict__ src,
                                                        double *__restrict__ dst, int m, double tol,
-                                                       OsState *st) {
+                                                       OsState *st, Periodic per) {
     if (st->done) return;
     if (m >= 2) {
         const double dm = bitsd(st->dmax[m - 1]), jm = bitsd(st->jmax[m - 1]);
@@ -146,19 +172,15 @@ __global__ void __launch_bounds__(256) os_sweep_kernel(int nx, int ny, int nz, c
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
          v += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
-        const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-        const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
         A acc = A(0);
         int plane = 0;
 #pragma unroll
         for (int d = 0; d < 27; ++d) {
             if (d == 13) continue;
-            const int dx = d % 3, dy = (d / 3) % 3, dz = d / 9 - 1;
-            const int zz = z + dz;
             const A coef = a[(long long)plane * N + v];
             ++plane;
-            if (zz < 0 || zz >= nz) continue;
-            const long long u = xs[dx] + (long long)nx * (ys[dy] + (long long)ny * zz);
+            const long long u = nb_index(x, y, z, d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1, nx, ny, nz, per);
+            if (u < 0) continue;
             acc += coef * (A)src[u];
         }
         const double nv = (r[v] + (double)acc) * inv_diag[v];
@@ -246,27 +268,30 @@ int grid_for(long long n, int threads) {
 
 }  // namespace
 
-cudaError_t launch_pack(int n, const double *chi, double scale, const double *S, void *chiS,
-                        bool fp64, cudaStream_t s) {
-    pack_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, chi, scale, S, chiS, fp64);
+cudaError_t launch_pack(int nx, int ny, int nz, const double *chi, double scale, const double *S,
+                        void *chiS, bool fp64, cudaStream_t s) {
+    const long long n = (long long)nx * ny * nz;
+    pack_kernel<<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, chi, scale, S, chiS, fp64);
     return cudaGetLastError();
 }
 
-cudaError_t launch_source(int n, const double *J, const double *eps, const double *B, void *chiS,
-                          bool fp64, bool homogeneous, cudaStream_t s) {
-    source_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, J, eps, B, chiS, fp64, homogeneous);
+cudaError_t launch_source(int nx, int ny, int nz, const double *J, const double *eps,
+                          const double *B, void *chiS, bool fp64, bool homogeneous,
+                          cudaStream_t s) {
+    const long long n = (long long)nx * ny * nz;
+    source_kernel<<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, J, eps, B, chiS, fp64, homogeneous);
     return cudaGetLastError();
 }
 
 cudaError_t launch_os_prep(int nx, int ny, int nz, const double *lstar, const double *eps,
-                           void *a, bool a64, double *inv_diag, cudaStream_t s) {
+                           void *a, bool a64, double *inv_diag, cudaStream_t s, Periodic per) {
     const long long N = (long long)nx * ny * nz;
     if (a64)
         os_prep_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(nx, ny, nz, lstar, eps,
-                                                                static_cast<double *>(a), inv_diag);
+                                                                static_cast<double *>(a), inv_diag, per);
     else
         os_prep_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(nx, ny, nz, lstar, eps,
-                                                               static_cast<float *>(a), inv_diag);
+                                                               static_cast<float *>(a), inv_diag, per);
     return cudaGetLastError();
 }
 
@@ -281,17 +306,17 @@ cudaError_t launch_os_init(int n, const double *Jfs, const double *J, const doub
 
 cudaError_t launch_os_sweep(int nx, int ny, int nz, const void *a, bool a64,
                             const double *inv_diag, const double *r, double *const *buf, int m,
-                            double tol, OsState *st, cudaStream_t s) {
+                            double tol, OsState *st, cudaStream_t s, Periodic per) {
     // buf is a host array of the two device ping-pong buffers
     const long long N = (long long)nx * ny * nz;
     const double *src = buf[(m - 1) & 1];
     double *dst = buf[m & 1];
     if (a64)
         os_sweep_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(
-            nx, ny, nz, static_cast<const double *>(a), inv_diag, r, src, dst, m, tol, st);
+            nx, ny, nz, static_cast<const double *>(a), inv_diag, r, src, dst, m, tol, st, per);
     else
         os_sweep_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(
-            nx, ny, nz, static_cast<const float *>(a), inv_diag, r, src, dst, m, tol, st);
+            nx, ny, nz, static_cast<const float *>(a), inv_diag, r, src, dst, m, tol, st, per);
     return cudaGetLastError();
 }
 

@@ -88,7 +88,8 @@ struct rt3d_grid {
     double *top = nullptr, *bot = nullptr, *tmp = nullptr, *delta = nullptr, *r64 = nullptr;
     double *chi_ref = nullptr, *eps_ref = nullptr;
     double **dJ_dev = nullptr;  // device copy of {dJ[0], dJ[1]}
-    void *chiS32 = nullptr, *chiS64 = nullptr;
+    void *chiS32 = nullptr, *chiS64 = nullptr;  // [4N] replicated 2 x 2 in x, y
+    double *Jrep = nullptr;                      // [4N] fast-path accumulation
     void *a = nullptr;  // [26][N] OS off-diagonals (f64 in FP64 mode, f32 otherwise)
     bool a64 = true;
     OsState *st = nullptr;
@@ -101,6 +102,33 @@ struct rt3d_grid {
     double *V[kKrylov + 1] = {}, *Z[kKrylov] = {};
     double **dV = nullptr, **dZ = nullptr, **dOne = nullptr;
     double *dots = nullptr, *coef = nullptr;
+
+    // spherical grid: trig tables and the ray cache
+    bool sph = false;
+    Periodic per{true, true, false};
+    double *s_re2 = nullptr, *s_ct = nullptr, *s_ctk = nullptr, *s_cpe = nullptr, *s_spe = nullptr;
+    double *s_rc = nullptr, *s_stc = nullptr, *s_ctc = nullptr, *s_cpc = nullptr, *s_spc = nullptr;
+    long long s_nrays = 0, s_nseg = 0;
+    std::vector<long long> s_ray_base;
+    std::vector<int> s_nrays_angle;
+    long long *s_ray_off = nullptr;
+    int *s_ray_len = nullptr, *s_ray_angle = nullptr, *s_ray_launch = nullptr;
+    int *s_ray_kind = nullptr, *s_ray_face = nullptr, *s_cell = nullptr, *s_crep = nullptr;
+    double *s_len64 = nullptr, *s_cw64 = nullptr;
+    float *s_len32 = nullptr, *s_cw32 = nullptr;
+    uint64_t *s_win = nullptr;
+
+    // batched-wavelength workspace (allocated for the largest n_lambda seen)
+    int bl_cap = 0;
+    double *bchi = nullptr, *beps = nullptr, *bB = nullptr, *bJ = nullptr, *br = nullptr;
+    double *bbuf0 = nullptr, *bbuf1 = nullptr, *binv = nullptr, *bJrep = nullptr;
+    double *btop = nullptr, *bbot = nullptr;
+    float2 *bchiS = nullptr;
+    float *ba = nullptr;
+    BatchState bsh{};             // host copy of the device pointers
+    BatchState *bsd = nullptr;    // device copy
+    cudaStream_t bstream = nullptr;
+    cudaEvent_t bev0 = nullptr, bev1 = nullptr;
 
     // instrumentation: formal-solution kernel time (CUDA events on the
     // grid's stream) and kernels launched
@@ -124,6 +152,9 @@ struct rt3d_grid {
         return RT3D_OK;
     }
     ~rt3d_grid() {
+        if (bstream) cudaStreamDestroy(bstream);
+        if (bev0) cudaEventDestroy(bev0);
+        if (bev1) cudaEventDestroy(bev1);
         for (void *p : allocs) cudaFree(p);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
@@ -162,15 +193,19 @@ rt3d_status fs_params(rt3d_grid *g, const rt3d_bc *bc, bool fp64, bool homogeneo
     q.len = fp64 ? (const void *)g->tpl.len64 : (const void *)g->tpl.len32;
     q.cw = fp64 ? (const void *)g->tpl.cw64 : (const void *)g->tpl.cw32;
     q.win = g->tpl.win;
+    q.rec32 = g->tpl.rec32;
+    q.Jrep = g->Jrep;
     q.chiS = fp64 ? g->chiS64 : g->chiS32;
     q.homogeneous = homogeneous ? 1 : 0;
     if (bc && !homogeneous) {
         q.I_top = bc->I_top;
         q.I_bot = bc->I_bottom;
+        q.I_irr = bc->I_irr;
         const double *tf = nullptr, *bf = nullptr;
         const size_t nf = (size_t)g->nx * g->ny;
-        TRY(stage_in(g, bc->I_top_face, nf, g->top, &tf));
-        TRY(stage_in(g, bc->I_bottom_face, nf, g->bot, &bf));
+        const size_t nfb = g->sph ? (size_t)g->ny * g->nz : nf;  // spherical core face
+        if (!g->sph) TRY(stage_in(g, bc->I_top_face, nf, g->top, &tf));
+        TRY(stage_in(g, bc->I_bottom_face, nfb, g->bot, &bf));
         q.top_face = tf;
         q.bot_face = bf;
     }
@@ -198,14 +233,52 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
     p.cw = fp64 ? (const void *)g->tpl.cw64 : (const void *)g->tpl.cw32;
     p.J = g->Jfs;
     p.lstar = with_lstar ? g->lstar : nullptr;
-    CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
+    if (g->sph) {
+        SphFsParams sp{};
+        sp.nrays = g->s_nrays;
+        sp.N = (int)g->N;
+        sp.ray_off = g->s_ray_off;
+        sp.ray_len = g->s_ray_len;
+        sp.ray_kind = g->s_ray_kind;
+        sp.ray_face = g->s_ray_face;
+        sp.cell = g->s_cell;
+        sp.crep = g->s_crep;
+        sp.len = fp64 ? (const void *)g->s_len64 : (const void *)g->s_len32;
+        sp.cw = fp64 ? (const void *)g->s_cw64 : (const void *)g->s_cw32;
+        sp.win = g->s_win;
+        sp.chiS = p.chiS;
+        sp.J = g->Jfs;
+        sp.lstar = p.lstar;
+        sp.core_face = base.bot_face;
+        sp.I_core = base.I_bot;
+        sp.I_out = base.I_top;
+        sp.I_irr = base.I_irr;
+        sp.homogeneous = base.homogeneous;
+        CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
+        if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
+        TRY(collect_events(g));
+        CK(cudaEventRecord(g->ev0, g->stream));
+        CK(launch_sph_fs(sp, fp64, g->parab, with_lstar, g->stream));
+        CK(cudaEventRecord(g->ev1, g->stream));
+        g->ev_pending = fp64 ? 1 : 0;
+        ++g->launches;
+        return RT3D_OK;
+    }
+    const bool fast = !fp64 && !with_lstar;
+    if (fast) CK(cudaMemsetAsync(g->Jrep, 0, sizeof(double) * 4 * g->N, g->stream));
+    else CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
     if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
     TRY(collect_events(g));
     CK(cudaEventRecord(g->ev0, g->stream));
-    CK(launch_fs(p, fp64, g->parab, with_lstar, g->stream));
+    if (fast) CK(launch_fs_fast(p, g->parab, g->stream));
+    else CK(launch_fs(p, fp64, g->parab, with_lstar, g->stream));
     CK(cudaEventRecord(g->ev1, g->stream));
     g->ev_pending = fp64 ? 1 : 0;
     ++g->launches;
+    if (fast) {
+        CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
+        ++g->launches;
+    }
     return RT3D_OK;
 }
 
@@ -234,20 +307,227 @@ rt3d_status os_solve_dev(rt3d_grid *g, const double *Jfs, const double *J, const
     CK(launch_os_init((int)g->N, Jfs, J, extra, g->inv_diag, g->r, g->dJ[0], g->st, g->stream));
     for (int m = 1; m <= max_sweeps; ++m)
         CK(launch_os_sweep(g->nx, g->ny, g->nz, g->a, g->a64, g->inv_diag, g->r, g->dJ, m, tol,
-                           g->st, g->stream));
+                           g->st, g->stream, g->per));
     CK(launch_os_finish(max_sweeps, tol, g->st, g->stream));
     g->launches += max_sweeps + 2;
     return RT3D_OK;
 }
 
+// Work buffers of the formal solution and the solvers.
+rt3d_status alloc_work(rt3d_grid *g) {
+    cudaStream_t s = g->stream;
+    // work buffers
+    const size_t N = (size_t)g->N;
+    const size_t nf = g->sph ? (size_t)g->ny * g->nz : (size_t)g->nx * g->ny;
+    TRY(g->alloc(&g->chi, N));
+    TRY(g->alloc(&g->eps, N));
+    TRY(g->alloc(&g->B, N));
+    TRY(g->alloc(&g->S, N));
+    TRY(g->alloc(&g->J, N));
+    TRY(g->alloc(&g->Jfs, N));
+    TRY(g->alloc(&g->r, N));
+    TRY(g->alloc(&g->dJ[0], N));
+    TRY(g->alloc(&g->dJ[1], N));
+    TRY(g->alloc(&g->inv_diag, N));
+    TRY(g->alloc(&g->tmp, N));
+    TRY(g->alloc(&g->delta, N));
+    TRY(g->alloc(&g->r64, N));
+    TRY(g->alloc(&g->chi_ref, N));
+    TRY(g->alloc(&g->eps_ref, N));
+    TRY(g->alloc(&g->lstar, 27 * N));
+    TRY(g->alloc(&g->top, nf));
+    TRY(g->alloc(&g->bot, nf));
+    TRY(g->alloc(&g->dJ_dev, 2));
+    TRY(g->alloc(reinterpret_cast<double2 **>(&g->chiS64), 4 * N));
+    TRY(g->alloc(reinterpret_cast<float2 **>(&g->chiS32), 4 * N));
+    TRY(g->alloc(&g->Jrep, 4 * N));
+    if (g->a64) TRY(g->alloc(reinterpret_cast<double **>(&g->a), 26 * N));
+    else TRY(g->alloc(reinterpret_cast<float **>(&g->a), 26 * N));
+    TRY(g->alloc(&g->st, 1));
+    CK(cudaMemcpyAsync(g->dJ_dev, g->dJ, sizeof(double *) * 2, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(g->st, 0, sizeof(OsState), s));
+    CK(cudaEventCreate(&g->ev0));
+    CK(cudaEventCreate(&g->ev1));
+    CK(cudaStreamSynchronize(s));
+    return RT3D_OK;
+}
+
+// Spherical geometry cache: trig tables on the host (plain IEEE arithmetic
+// and libm), the ray set of every solid angle built on the device in angle
+// chunks (pass 1 counts rays and segments, pass 2 fills the tables).
+rt3d_status sph_build(rt3d_grid *g) {
+    const rt3d_grid_desc &d = g->desc;
+    const int nr = g->nx, nt = g->ny, np = g->nz, nO = g->nO;
+    const long long N = g->N;
+    std::vector<double> re(nr + 1), re2(nr + 1), ct(nt + 1), ctk(nt + 1), cpe(np), spe(np), rc(nr),
+        stc(nt), ctc(nt), cpc(np), spc(np);
+    for (int i = 0; i <= nr; ++i) re[i] = d.r_in * std::pow(d.r_out / d.r_in, (double)i / (double)nr);
+    re[0] = d.r_in;
+    re[nr] = d.r_out;
+    for (int i = 0; i <= nr; ++i) re2[i] = re[i] * re[i];
+    for (int j = 0; j <= nt; ++j) {
+        double c = std::cos((double)j * M_PI / (double)nt);
+        if (2 * j == nt) c = 0.0;
+        if (j == 0) c = 1.0;
+        if (j == nt) c = -1.0;
+        ct[j] = c;
+        ctk[j] = c * std::fabs(c);
+    }
+    for (int k = 0; k < np; ++k) {
+        const double ph = 2.0 * M_PI * (double)k / (double)np;
+        cpe[k] = std::cos(ph);
+        spe[k] = std::sin(ph);
+        const double pc = 2.0 * M_PI * ((double)k + 0.5) / (double)np;
+        cpc[k] = std::cos(pc);
+        spc[k] = std::sin(pc);
+    }
+    for (int i = 0; i < nr; ++i) rc[i] = std::sqrt(re[i] * re[i + 1]);
+    for (int j = 0; j < nt; ++j) {
+        const double t = ((double)j + 0.5) * M_PI / (double)nt;
+        stc[j] = std::sin(t);
+        ctc[j] = std::cos(t);
+    }
+    cudaStream_t s = g->stream;
+    auto up = [&](double **dst, const std::vector<double> &v) -> rt3d_status {
+        TRY(g->alloc(dst, v.size()));
+        CK(cudaMemcpyAsync(*dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, s));
+        return RT3D_OK;
+    };
+    TRY(up(&g->s_re2, re2));
+    TRY(up(&g->s_ct, ct));
+    TRY(up(&g->s_ctk, ctk));
+    TRY(up(&g->s_cpe, cpe));
+    TRY(up(&g->s_spe, spe));
+    TRY(up(&g->s_rc, rc));
+    TRY(up(&g->s_stc, stc));
+    TRY(up(&g->s_ctc, ctc));
+    TRY(up(&g->s_cpc, cpc));
+    TRY(up(&g->s_spc, spc));
+    double *d_dir = nullptr, *d_wt = nullptr;
+    TRY(up(&d_dir, g->dir));
+    TRY(up(&d_wt, g->wt));
+    SphBuildParams bp{};
+    bp.T = SphTables{nr, nt, np, g->s_re2, g->s_ct, g->s_ctk, g->s_cpe, g->s_spe,
+                     g->s_rc, g->s_stc, g->s_ctc, g->s_cpc, g->s_spc};
+    bp.nangles = nO;
+    bp.ncap = 2 * (nr + 1) + 2 * (nt + 1) + np + 8;
+    bp.dir = d_dir;
+    bp.wt = d_wt;
+    // chunk of angles built at once: scratch N/8 + 8 N + 8 ncap bytes per angle
+    const long long per_angle = N / 8 + 8 * N + 8LL * bp.ncap + 64;
+    int chunk = (int)std::max(1LL, std::min<long long>(nO, (2LL << 30) / per_angle));
+    const int words = (int)((N + 31) / 32);
+    unsigned *hit = nullptr;
+    double *tbuf = nullptr, *den = nullptr;
+    int *d_nrays = nullptr, *d_err = nullptr;
+    long long *d_nseg = nullptr;
+    TRY(g->alloc(&hit, (size_t)chunk * words));
+    TRY(g->alloc(&tbuf, (size_t)chunk * bp.ncap));
+    TRY(g->alloc(&den, (size_t)chunk * N));
+    TRY(g->alloc(&d_nrays, nO));
+    TRY(g->alloc(&d_nseg, nO));
+    TRY(g->alloc(&d_err, 1));
+    CK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    bp.hit = hit;
+    bp.tbuf = tbuf;
+    bp.den = den;
+    bp.nrays = d_nrays;
+    bp.nseg = d_nseg;
+    bp.err = d_err;
+    bp.pass = 1;
+    for (int o0 = 0; o0 < nO; o0 += chunk) {
+        bp.o0 = o0;
+        bp.nchunk = std::min(chunk, nO - o0);
+        CK(launch_sph_build(bp, s));
+    }
+    std::vector<int> nrays(nO);
+    std::vector<long long> nseg(nO);
+    int herr = 0;
+    CK(cudaMemcpyAsync(nrays.data(), d_nrays, sizeof(int) * nO, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(nseg.data(), d_nseg, sizeof(long long) * nO, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr) return fail(RT3D_EINVAL, "spherical tracer error %d", herr);
+    std::vector<long long> rbase(nO), sbase(nO);
+    long long tr = 0, tsg = 0;
+    for (int o = 0; o < nO; ++o) {
+        rbase[o] = tr;
+        sbase[o] = tsg;
+        tr += nrays[o];
+        tsg += nseg[o];
+    }
+    if (tsg >= (1LL << 40)) return fail(RT3D_EINVAL, "spherical cache too large");
+    g->s_nrays = tr;
+    g->s_nseg = tsg;
+    g->s_ray_base = rbase;
+    g->s_nrays_angle = nrays;
+    long long *d_rbase = nullptr, *d_sbase = nullptr;
+    TRY(g->alloc(&d_rbase, nO));
+    TRY(g->alloc(&d_sbase, nO));
+    CK(cudaMemcpyAsync(d_rbase, rbase.data(), sizeof(long long) * nO, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_sbase, sbase.data(), sizeof(long long) * nO, cudaMemcpyHostToDevice, s));
+    TRY(g->alloc(&g->s_ray_off, tr));
+    TRY(g->alloc(&g->s_ray_len, tr));
+    TRY(g->alloc(&g->s_ray_angle, tr));
+    TRY(g->alloc(&g->s_ray_launch, tr));
+    TRY(g->alloc(&g->s_ray_kind, tr));
+    TRY(g->alloc(&g->s_ray_face, tr));
+    TRY(g->alloc(&g->s_cell, tsg));
+    TRY(g->alloc(&g->s_crep, tsg));
+    TRY(g->alloc(&g->s_len64, tsg));
+    TRY(g->alloc(&g->s_cw64, tsg));
+    TRY(g->alloc(&g->s_len32, tsg));
+    TRY(g->alloc(&g->s_cw32, tsg));
+    TRY(g->alloc(&g->s_win, tsg));
+    bp.pass = 2;
+    bp.ray_base = d_rbase;
+    bp.seg_base = d_sbase;
+    bp.ray_off = g->s_ray_off;
+    bp.ray_len = g->s_ray_len;
+    bp.ray_angle = g->s_ray_angle;
+    bp.ray_launch = g->s_ray_launch;
+    bp.ray_kind = g->s_ray_kind;
+    bp.ray_face = g->s_ray_face;
+    bp.cell = g->s_cell;
+    bp.crep = g->s_crep;
+    bp.len64 = g->s_len64;
+    bp.cw64 = g->s_cw64;
+    bp.len32 = g->s_len32;
+    bp.cw32 = g->s_cw32;
+    bp.win = g->s_win;
+    for (int o0 = 0; o0 < nO; o0 += chunk) {
+        bp.o0 = o0;
+        bp.nchunk = std::min(chunk, nO - o0);
+        CK(launch_sph_build(bp, s));
+    }
+    CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr == 3) return fail(RT3D_EINVAL, "a Lambda* window exceeds 9 points");
+    if (herr == 5) return fail(RT3D_EINVAL, "a cell is not crossed by some solid angle");
+    if (herr) return fail(RT3D_EINVAL, "spherical tracer error %d", herr);
+    g->segments = tsg;
+    g->tpl.kmax = bp.ncap;
+    return alloc_work(g);
+}
+
 rt3d_status validate_desc(const rt3d_grid_desc *d) {
     if (!d) return fail(RT3D_EINVAL, "desc is NULL");
-    if (d->geometry != RT3D_CARTESIAN_PERIODIC_XY)
+    if (d->geometry != RT3D_CARTESIAN_PERIODIC_XY && d->geometry != RT3D_SPHERICAL)
         return fail(RT3D_EINVAL, "geometry %d is not supported", d->geometry);
-    if (d->n[0] < 4 || d->n[0] > 2047 || d->n[1] < 4 || d->n[1] > 2047 || d->n[2] < 1 ||
-        d->n[2] > 1023)
+    if (d->geometry == RT3D_SPHERICAL) {
+        if (d->n[0] < 1 || d->n[1] < 2 || d->n[2] < 4 || d->n[0] > 4096 || d->n[1] > 4096 ||
+            d->n[2] > 4096)
+            return fail(RT3D_EINVAL, "spherical grid %d x %d x %d: need nr >= 1, ntheta >= 2, "
+                                     "nphi >= 4", d->n[0], d->n[1], d->n[2]);
+        if (!(d->r_in > 0.0) || !(d->r_out > d->r_in))
+            return fail(RT3D_EINVAL, "spherical grid needs 0 < r_in < r_out");
+    } else if (d->n[0] < 4 || d->n[0] > 2047 || d->n[1] < 4 || d->n[1] > 2047 || d->n[2] < 1 ||
+               d->n[2] > 1023) {
         return fail(RT3D_EINVAL, "grid %d x %d x %d outside 4..2047 x 4..2047 x 1..1023",
                     d->n[0], d->n[1], d->n[2]);
+    }
+    if (4LL * d->n[0] * d->n[1] * d->n[2] >= (1LL << 31))
+        return fail(RT3D_EINVAL, "grid too large: 4 nx ny nz must stay below 2^31");
     if (d->ntheta < 1 || d->nphi < 1 || (long long)d->ntheta * d->nphi > 65535)
         return fail(RT3D_EINVAL, "bad angle grid %d x %d", d->ntheta, d->nphi);
     if (d->interp != RT3D_LINEAR && d->interp != RT3D_PARABOLIC)
@@ -271,6 +551,8 @@ rt3d_status grid_build(rt3d_grid *g) {
     g->fs64 = d.precision == RT3D_FP64;
     g->parab = d.interp == RT3D_PARABOLIC;
     g->a64 = g->fs64;
+    g->sph = d.geometry == RT3D_SPHERICAL;
+    if (g->sph) g->per = Periodic{false, false, true};
 
     // A1: direction set in FP64 on the host (midpoints in mu and phi).
     const int nO = g->nO;
@@ -288,9 +570,11 @@ rt3d_status grid_build(rt3d_grid *g) {
             g->dir[3 * o + 0] = st * std::cos(ph);
             g->dir[3 * o + 1] = st * std::sin(ph);
             g->dir[3 * o + 2] = m;
-            if (!(std::fabs(m) > 0.0)) return fail(RT3D_EINVAL, "direction %d has mu = 0", o);
+            if (!g->sph && !(std::fabs(m) > 0.0))
+                return fail(RT3D_EINVAL, "direction %d has mu = 0 (use an even ntheta)", o);
         }
     }
+    if (g->sph) return sph_build(g);
     // Capacity per angle: nz z-steps plus at most |d_x| nz/|mu| + 1 x-steps and
     // likewise in y.
     std::vector<int> cap(nO);
@@ -317,6 +601,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     TRY(g->alloc(&t.cw64, total));
     TRY(g->alloc(&t.cw32, total));
     TRY(g->alloc(&t.win, total));
+    TRY(g->alloc(&t.rec32, total));
     double *d_dir = nullptr, *d_wt = nullptr, *d_ls = nullptr;
     int *d_cap = nullptr, *d_err = nullptr;
     TRY(g->alloc(&d_dir, 3 * nO));
@@ -349,6 +634,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     tp.cw64 = t.cw64;
     tp.cw32 = t.cw32;
     tp.win = t.win;
+    tp.rec32 = t.rec32;
     tp.layer_sum = d_ls;
     tp.err = d_err;
     CK(launch_trace(tp, s));
@@ -369,38 +655,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     g->segments = 0;
     for (int o = 0; o < nO; ++o) g->segments += (long long)g->K[o] * g->nx * g->ny;
 
-    // work buffers
-    const size_t N = (size_t)g->N, nf = (size_t)g->nx * g->ny;
-    TRY(g->alloc(&g->chi, N));
-    TRY(g->alloc(&g->eps, N));
-    TRY(g->alloc(&g->B, N));
-    TRY(g->alloc(&g->S, N));
-    TRY(g->alloc(&g->J, N));
-    TRY(g->alloc(&g->Jfs, N));
-    TRY(g->alloc(&g->r, N));
-    TRY(g->alloc(&g->dJ[0], N));
-    TRY(g->alloc(&g->dJ[1], N));
-    TRY(g->alloc(&g->inv_diag, N));
-    TRY(g->alloc(&g->tmp, N));
-    TRY(g->alloc(&g->delta, N));
-    TRY(g->alloc(&g->r64, N));
-    TRY(g->alloc(&g->chi_ref, N));
-    TRY(g->alloc(&g->eps_ref, N));
-    TRY(g->alloc(&g->lstar, 27 * N));
-    TRY(g->alloc(&g->top, nf));
-    TRY(g->alloc(&g->bot, nf));
-    TRY(g->alloc(&g->dJ_dev, 2));
-    TRY(g->alloc(reinterpret_cast<double2 **>(&g->chiS64), N));
-    TRY(g->alloc(reinterpret_cast<float2 **>(&g->chiS32), N));
-    if (g->a64) TRY(g->alloc(reinterpret_cast<double **>(&g->a), 26 * N));
-    else TRY(g->alloc(reinterpret_cast<float **>(&g->a), 26 * N));
-    TRY(g->alloc(&g->st, 1));
-    CK(cudaMemcpyAsync(g->dJ_dev, g->dJ, sizeof(double *) * 2, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(g->st, 0, sizeof(OsState), s));
-    CK(cudaEventCreate(&g->ev0));
-    CK(cudaEventCreate(&g->ev1));
-    CK(cudaStreamSynchronize(s));
-    return RT3D_OK;
+    return alloc_work(g);
 }
 
 // Convergence monitor of an iteration from its max relative changes:
@@ -455,8 +710,8 @@ rt3d_status load_problem(rt3d_grid *g, const double *chi, const double *eps, con
         CK(cudaStreamSynchronize(g->stream));
         if (changed) g->lstar_valid = false;
     }
-    CKL(launch_pack((int)N, g->chi, 1.0, g->chi /*S placeholder*/, g->chiS32, false, g->stream));
-    CKL(launch_pack((int)N, g->chi, 1.0, g->chi, g->chiS64, true, g->stream));
+    CKL(launch_pack(g->nx, g->ny, g->nz, g->chi, 1.0, g->chi /*S placeholder*/, g->chiS32, false, g->stream));
+    CKL(launch_pack(g->nx, g->ny, g->nz, g->chi, 1.0, g->chi, g->chiS64, true, g->stream));
     return RT3D_OK;
 }
 
@@ -465,12 +720,12 @@ rt3d_status load_problem(rt3d_grid *g, const double *chi, const double *eps, con
 rt3d_status ali_iteration(rt3d_grid *g, const FsParams &fp, bool fp64, int max_sweeps,
                           double sweep_tol, double *rel) {
     const int N = (int)g->N;
-    CKL(launch_source(N, g->J, g->eps, g->B, fp64 ? g->chiS64 : g->chiS32, fp64, false, g->stream));
+    CKL(launch_source(g->nx, g->ny, g->nz, g->J, g->eps, g->B, fp64 ? g->chiS64 : g->chiS32, fp64, false, g->stream));
     const bool build = !g->lstar_valid;
     TRY(run_fs(g, fp, fp64, build));
     if (build) {
         CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag,
-                          g->stream));
+                          g->stream, g->per));
         CK(cudaMemcpyAsync(g->chi_ref, g->chi, sizeof(double) * N, cudaMemcpyDeviceToDevice,
                            g->stream));
         CK(cudaMemcpyAsync(g->eps_ref, g->eps, sizeof(double) * N, cudaMemcpyDeviceToDevice,
@@ -530,7 +785,7 @@ rt3d_status kaxpy(rt3d_grid *g, double *w, double *const *Vdev, const double *c,
 // out = A v = v - Lambda_hom((1 - eps) v), formal solution in FP32 or FP64
 rt3d_status apply_A(rt3d_grid *g, const FsParams &fphom, bool fp64, const double *v, double *out) {
     const int n = (int)g->N;
-    CKL(launch_source(n, v, g->eps, nullptr, fp64 ? g->chiS64 : g->chiS32, fp64, true, g->stream));
+    CKL(launch_source(g->nx, g->ny, g->nz, v, g->eps, nullptr, fp64 ? g->chiS64 : g->chiS32, fp64, true, g->stream));
     TRY(run_fs(g, fphom, fp64, false));
     CKL(launch_sub(n, v, g->Jfs, out, g->stream));
     return RT3D_OK;
@@ -622,22 +877,23 @@ rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p
     bool conv = false;
     double gain = -1.0, est = 1.0, res = 0.0;
     int it = 0, rounds32 = 0;
-    // Reduction asked of one FGMRES cycle: with an FP32 operator the basis
-    // carries rounding noise, so cycles stop at 1e-3 and the FP64 residual
-    // of the next round drives the refinement.
-    const double eta = mixed ? 1e-3 : 1e-4;
+    // Reduction asked of one FGMRES cycle. An FP64 formal solution costs
+    // about 60 FP32 ones on this GPU, so every cycle is driven down to 1e-5
+    // (the FP32 operator's rounding still allows that) to keep the number of
+    // FP64 residuals of the refinement at two or three.
+    const double eta = 1e-5;
     for (int round = 0; round < 60 && it < max_iter; ++round) {
         // residual of the current J (the first one also builds Lambda*)
         const bool fs64 = res64;
         const bool build = !g->lstar_valid;
-        CKL(launch_source(n, g->J, g->eps, g->B, fs64 ? g->chiS64 : g->chiS32, fs64, false,
+        CKL(launch_source(g->nx, g->ny, g->nz, g->J, g->eps, g->B, fs64 ? g->chiS64 : g->chiS32, fs64, false,
                           g->stream));
         TRY(run_fs(g, fs64 ? fp64p : fp, fs64, build));
         if (fs64) ++s.fs_fp64;
         else ++s.fs_fp32;
         if (build) {
             CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag,
-                               g->stream));
+                               g->stream, g->per));
             CK(cudaMemcpyAsync(g->chi_ref, g->chi, sizeof(double) * n, cudaMemcpyDeviceToDevice,
                                g->stream));
             CK(cudaMemcpyAsync(g->eps_ref, g->eps, sizeof(double) * n, cudaMemcpyDeviceToDevice,
@@ -678,6 +934,45 @@ rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p
     s.iterations = it;
     s.est_error = est;
     *conv_out = conv;
+    return RT3D_OK;
+}
+
+// Batched workspace for nl wavelengths (grows; never shrinks).
+rt3d_status batch_setup(rt3d_grid *g, int nl) {
+    if (g->bl_cap >= nl) return RT3D_OK;
+    const size_t N = (size_t)g->N, nf = (size_t)g->nx * g->ny, L = (size_t)nl;
+    TRY(g->alloc(&g->bchi, L * N));
+    TRY(g->alloc(&g->beps, L * N));
+    TRY(g->alloc(&g->bB, L * N));
+    TRY(g->alloc(&g->bJ, L * N));
+    TRY(g->alloc(&g->br, L * N));
+    TRY(g->alloc(&g->bbuf0, L * N));
+    TRY(g->alloc(&g->bbuf1, L * N));
+    TRY(g->alloc(&g->binv, L * N));
+    TRY(g->alloc(&g->bJrep, 4 * L * N));
+    TRY(g->alloc(&g->bchiS, 4 * L * N));
+    TRY(g->alloc(&g->ba, 26 * L * N));
+    TRY(g->alloc(&g->btop, L * nf));
+    TRY(g->alloc(&g->bbot, L * nf));
+    BatchState &b = g->bsh;
+    TRY(g->alloc(&b.active, L));
+    TRY(g->alloc(&b.state, L));
+    TRY(g->alloc(&b.done, L));
+    TRY(g->alloc(&b.count, L));
+    TRY(g->alloc(&b.iters, L));
+    TRY(g->alloc(&b.dmax, L * (kBatchSweeps + 1)));
+    TRY(g->alloc(&b.jmax, L * (kBatchSweeps + 1)));
+    TRY(g->alloc(&b.rel, L));
+    TRY(g->alloc(&b.hist, L * kHist));
+    TRY(g->alloc(&b.est, L));
+    b.nactive = 0;
+    TRY(g->alloc(&g->bsd, 1));
+    if (!g->bstream) {
+        CK(cudaStreamCreateWithFlags(&g->bstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&g->bev0, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&g->bev1, cudaEventDisableTiming));
+    }
+    g->bl_cap = nl;
     return RT3D_OK;
 }
 
@@ -722,10 +1017,40 @@ rt3d_status rt3d_grid_get_info(const rt3d_grid *g, rt3d_grid_info *info) {
     return RT3D_OK;
 }
 
+rt3d_status rt3d_grid_sph_ray(const rt3d_grid *gc, int angle, int index, int *K, int32_t *vox,
+                              double *len, int *launch, int *kind) {
+    rt3d_grid *g = const_cast<rt3d_grid *>(gc);
+    if (!g || !K) return fail(RT3D_EINVAL, "NULL argument");
+    if (!g->sph) return fail(RT3D_EINVAL, "not a spherical grid");
+    if (angle < 0 || angle >= g->nO) return fail(RT3D_EINVAL, "angle %d out of range", angle);
+    if (index < 0 || index >= g->s_nrays_angle[angle])
+        return fail(RT3D_EINVAL, "ray %d out of range", index);
+    const long long r = g->s_ray_base[angle] + index;
+    long long off = 0;
+    int k = 0, ln = 0, kd = 0;
+    CK(cudaMemcpyAsync(&off, g->s_ray_off + r, sizeof off, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(&k, g->s_ray_len + r, sizeof k, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(&ln, g->s_ray_launch + r, sizeof ln, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(&kd, g->s_ray_kind + r, sizeof kd, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (*K < k) {
+        *K = k;
+        return fail(RT3D_EINVAL, "capacity below %d points", k);
+    }
+    *K = k;
+    if (vox) CK(cudaMemcpyAsync(vox, g->s_cell + off, sizeof(int) * k, cudaMemcpyDeviceToHost, g->stream));
+    if (len) CK(cudaMemcpyAsync(len, g->s_len64 + off, sizeof(double) * k, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (launch) *launch = ln;
+    if (kind) *kind = kd;
+    return RT3D_OK;
+}
+
 rt3d_status rt3d_grid_template(const rt3d_grid *gc, int angle, int *K, int32_t *vox,
                                double *len) {
     rt3d_grid *g = const_cast<rt3d_grid *>(gc);
     if (!g || !K) return fail(RT3D_EINVAL, "NULL argument");
+    if (g->sph) return fail(RT3D_EINVAL, "spherical grids have no per-angle template");
     if (angle < 0 || angle >= g->nO) return fail(RT3D_EINVAL, "angle %d out of range", angle);
     const int k = g->K[angle];
     if (*K < k) {
@@ -759,7 +1084,7 @@ rt3d_status rt3d_formal_solution(rt3d_grid *g, const double *chi, const double *
     const double *dchi = nullptr, *dS = nullptr;
     TRY(stage_in(g, chi, N, g->chi, &dchi));
     TRY(stage_in(g, S, N, g->S, &dS));
-    CKL(launch_pack((int)N, dchi, 1.0, dS, g->fs64 ? g->chiS64 : g->chiS32, g->fs64, g->stream));
+    CKL(launch_pack(g->nx, g->ny, g->nz, dchi, 1.0, dS, g->fs64 ? g->chiS64 : g->chiS32, g->fs64, g->stream));
     FsParams fp;
     TRY(fs_params(g, bc, g->fs64, false, &fp));
     TRY(run_fs(g, fp, g->fs64, lstar_out != nullptr));
@@ -778,7 +1103,7 @@ rt3d_status rt3d_os_solve(rt3d_grid *g, const double *lstar, const double *eps, 
     CK(cudaMemcpyAsync(g->eps, eps, N * sizeof(double), cudaMemcpyDefault, g->stream));
     CK(cudaMemcpyAsync(g->tmp, r, N * sizeof(double), cudaMemcpyDefault, g->stream));
     g->lstar_valid = false;  // the grid's Lambda* now holds the caller's band
-    CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag, g->stream));
+    CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag, g->stream, g->per));
     TRY(os_solve_dev(g, nullptr, nullptr, g->tmp, max_sweeps, tol));
     CKL(launch_copy_buf((int)N, g->dJ_dev, g->st, g->delta, g->stream));
     TRY(deliver(g, dJ_out, g->delta, N));
@@ -883,7 +1208,7 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     if ((mixed || !conv) && it < max_iter) {
         for (int round = 0; round < 8 && it < max_iter; ++round) {
             // r64 = J_FS64(S(J)) - J
-            CKL(launch_source(n, g->J, g->eps, g->B, g->chiS64, true, false, g->stream));
+            CKL(launch_source(g->nx, g->ny, g->nz, g->J, g->eps, g->B, g->chiS64, true, false, g->stream));
             TRY(run_fs(g, fp64p, true, false));
             ++s.fs_fp64;
             TRY(reset_scalar(g, offsetof(OsState, res), sizeof(unsigned long long)));
@@ -900,7 +1225,7 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
             Progress dprog;
             const bool fs32 = mixed;
             for (int inner = 0; inner < 1000 && it < max_iter; ++inner) {
-                CKL(launch_source(n, g->delta, g->eps, nullptr, fs32 ? g->chiS32 : g->chiS64, !fs32,
+                CKL(launch_source(g->nx, g->ny, g->nz, g->delta, g->eps, nullptr, fs32 ? g->chiS32 : g->chiS64, !fs32,
                                   true, g->stream));
                 TRY(run_fs(g, fphom, !fs32, false));
                 if (fs32) ++s.fs_fp32;
@@ -928,7 +1253,7 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
         }
     } else if (conv) {
         // certification residual of the returned J
-        CKL(launch_source(n, g->J, g->eps, g->B, g->chiS64, true, false, g->stream));
+        CKL(launch_source(g->nx, g->ny, g->nz, g->J, g->eps, g->B, g->chiS64, true, false, g->stream));
         TRY(run_fs(g, fp64p, true, false));
         ++s.fs_fp64;
         TRY(reset_scalar(g, offsetof(OsState, res), sizeof(unsigned long long)));
@@ -946,6 +1271,198 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = s;
     if (!conv) return fail(RT3D_ENOTCONVERGED, "not converged after %d iterations (est %.3g)", it, est);
+    return RT3D_OK;
+}
+
+
+rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const double *eps,
+                               const double *B, const rt3d_bc *bc, double *J_inout, double tol,
+                               int max_iter, int *status_out, rt3d_batch_stats *stats) {
+    const auto t_start = std::chrono::steady_clock::now();
+    if (!g || !chi || !eps || !B || !J_inout) return fail(RT3D_EINVAL, "NULL argument");
+    if (nl < 1 || nl > 65535) return fail(RT3D_EINVAL, "n_lambda %d outside 1..65535", nl);
+    if (g->sph) return fail(RT3D_EINVAL, "batched wavelengths need a Cartesian grid");
+    if (!(tol > 0.0) || max_iter < 1) return fail(RT3D_EINVAL, "bad tol or max_iter");
+    const size_t N = (size_t)g->N, nf = (size_t)g->nx * g->ny, L = (size_t)nl;
+    rt3d_batch_stats bs{};
+    bs.nlambda = nl;
+    g->fs_ms[0] = g->fs_ms[1] = 0.0;
+    g->launches = 0;
+    TRY(batch_setup(g, nl));
+    cudaStream_t s = g->stream;
+    CK(cudaMemcpyAsync(g->bchi, chi, L * N * sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(g->beps, eps, L * N * sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(g->bB, B, L * N * sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(g->bJ, J_inout, L * N * sizeof(double), cudaMemcpyDefault, s));
+    const bool tf = bc && bc->I_top_face, bf = bc && bc->I_bottom_face;
+    if (tf) CK(cudaMemcpyAsync(g->btop, bc->I_top_face, L * nf * sizeof(double), cudaMemcpyDefault, s));
+    if (bf) CK(cudaMemcpyAsync(g->bbot, bc->I_bottom_face, L * nf * sizeof(double), cudaMemcpyDefault, s));
+
+    // Lambda* of every wavelength (FP32 formal solution with Lambda*, once),
+    // folded into its OS coefficients.
+    for (int l = 0; l < nl; ++l) {
+        float2 *cl = g->bchiS + 4 * (size_t)l * N;
+        CKL(launch_pack(g->nx, g->ny, g->nz, g->bchi + l * N, 1.0, g->bB + l * N, cl, false, s));
+        FsParams p{};
+        p.nx = g->nx;
+        p.ny = g->ny;
+        p.nz = g->nz;
+        p.nangles = g->nO;
+        p.order = g->tpl.order;
+        p.toff = g->tpl.toff;
+        p.tlen = g->tpl.tlen;
+        p.up = g->tpl.up;
+        p.code = g->tpl.code;
+        p.len = g->tpl.len32;
+        p.cw = g->tpl.cw32;
+        p.win = g->tpl.win;
+        p.rec32 = g->tpl.rec32;
+        p.chiS = cl;
+        p.J = g->Jfs;
+        p.lstar = g->lstar;
+        p.homogeneous = 1;
+        CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * N, s));
+        CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * N, s));
+        CKL(launch_fs(p, false, g->parab, true, s));
+        CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->beps + l * N, g->ba + 26 * l * N,
+                           false, g->binv + l * N, s, g->per));
+        ++bs.fs_lambda32;
+    }
+    g->lstar_valid = false;  // the grid's single-wavelength Lambda* was overwritten
+
+    // device state
+    std::vector<int> ones(L, 1);
+    BatchState &h = g->bsh;
+    CK(cudaMemcpyAsync(h.active, ones.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(h.state, 0, L * sizeof(int), s));
+    CK(cudaMemsetAsync(h.iters, 0, L * sizeof(int), s));
+    CK(cudaMemsetAsync(g->bJrep, 0, 4 * L * N * sizeof(double), s));
+    h.nactive = nl;
+    CK(cudaMemcpyAsync(g->bsd, &h, sizeof(BatchState), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+
+    BatchFsParams bp{};
+    bp.nx = g->nx;
+    bp.ny = g->ny;
+    bp.nz = g->nz;
+    bp.nangles = g->nO;
+    bp.order = g->tpl.order;
+    bp.toff = g->tpl.toff;
+    bp.tlen = g->tpl.tlen;
+    bp.up = g->tpl.up;
+    bp.rec32 = g->tpl.rec32;
+    bp.chiS = g->bchiS;
+    bp.Jrep = g->bJrep;
+    bp.top_face = tf ? g->btop : nullptr;
+    bp.bot_face = bf ? g->bbot : nullptr;
+    bp.I_top = bc ? bc->I_top : 0.0;
+    bp.I_bot = bc ? bc->I_bottom : 0.0;
+    bp.bs = g->bsd;
+
+    // capture one iteration into a CUDA graph on the batch stream
+    const int iter_cap = max_iter;
+    const double switch_tol = g->fs64 ? tol : std::max(tol, 1e-6);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaStreamBeginCapture(g->bstream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = launch_batch_iteration(bp, nl, g->bJ, g->beps, g->bB, g->ba, g->binv, g->br,
+                                            g->bbuf0, g->bbuf1, kBatchSweeps, 1e-3, switch_tol,
+                                            iter_cap, g->parab, g->bstream);
+    cudaError_t ce = cudaStreamEndCapture(g->bstream, &graph);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(RT3D_ECUDA, "batch graph capture failed: %s",
+                    cudaGetErrorString(le != cudaSuccess ? le : ce));
+    }
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    const long long per_iter = 7 + kBatchSweeps;
+    CK(cudaEventRecord(g->bev0, s));
+    CK(cudaStreamWaitEvent(g->bstream, g->bev0, 0));
+    float fs_ms_total = 0.0f;
+    cudaEvent_t t0, t1;
+    CK(cudaEventCreate(&t0));
+    CK(cudaEventCreate(&t1));
+    CK(cudaEventRecord(t0, g->bstream));
+    int replays = 0, nactive = nl;
+    while (nactive > 0 && replays < iter_cap) {
+        const int burst = std::min(4, iter_cap - replays);
+        for (int i = 0; i < burst; ++i) CK(cudaGraphLaunch(exec, g->bstream));
+        replays += burst;
+        CK(cudaMemcpyAsync(&nactive, &g->bsd->nactive, sizeof(int), cudaMemcpyDeviceToHost,
+                           g->bstream));
+        CK(cudaStreamSynchronize(g->bstream));
+    }
+    CK(cudaEventRecord(t1, g->bstream));
+    CK(cudaEventSynchronize(t1));
+    CK(cudaEventElapsedTime(&fs_ms_total, t0, t1));
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    g->launches += per_iter * replays;
+    bs.graph_replays = replays;
+    bs.batch_ms = fs_ms_total;
+    CK(cudaEventRecord(g->bev1, g->bstream));
+    CK(cudaStreamWaitEvent(s, g->bev1, 0));
+
+    std::vector<int> iters(L), state(L);
+    CK(cudaMemcpyAsync(iters.data(), h.iters, L * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(state.data(), h.state, L * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int l = 0; l < nl; ++l) bs.fs_lambda32 += iters[l];
+    bs.iterations = replays;
+
+    // FP64 refinement and certification of every wavelength with the
+    // single-wavelength Krylov solver, started from the batched J.
+    int nconv = 0;
+    double max_est = 0.0, max_res = 0.0;
+    for (int l = 0; l < nl; ++l) {
+        int st_l = state[l];
+        if (st_l == 3) {
+            if (status_out) status_out[l] = RT3D_ENUMERIC;
+            continue;
+        }
+        CK(cudaMemcpyAsync(g->chi, g->bchi + l * N, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(g->eps, g->beps + l * N, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(g->B, g->bB + l * N, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(g->J, g->bJ + l * N, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CKL(launch_pack(g->nx, g->ny, g->nz, g->chi, 1.0, g->chi, g->chiS32, false, s));
+        CKL(launch_pack(g->nx, g->ny, g->nz, g->chi, 1.0, g->chi, g->chiS64, true, s));
+        g->lstar_valid = false;
+        rt3d_bc bl{};
+        bl.I_top = bc ? bc->I_top : 0.0;
+        bl.I_bottom = bc ? bc->I_bottom : 0.0;
+        bl.I_top_face = tf ? g->btop + l * nf : nullptr;
+        bl.I_bottom_face = bf ? g->bbot + l * nf : nullptr;
+        FsParams fp, fp64k, fphomk;
+        TRY(fs_params(g, &bl, g->fs64, false, &fp));
+        TRY(fs_params(g, &bl, true, false, &fp64k));
+        TRY(fs_params(g, nullptr, g->fs64, true, &fphomk));
+        rt3d_solve_stats sl{};
+        bool kconv = false;
+        TRY(krylov_solve(g, fp, fp64k, fphomk, tol, max_iter, sl, &kconv));
+        CK(cudaMemcpyAsync(g->bJ + l * N, g->J, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        bs.fs_lambda32 += sl.fs_fp32;
+        bs.fs_lambda64 += sl.fs_fp64;
+        max_est = std::max(max_est, sl.est_error);
+        max_res = std::max(max_res, sl.residual64);
+        if (kconv) ++nconv;
+        if (status_out) status_out[l] = kconv ? RT3D_OK : RT3D_ENOTCONVERGED;
+    }
+    g->lstar_valid = false;
+    CK(cudaMemcpyAsync(J_inout, g->bJ, L * N * sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    TRY(collect_events(g));
+    bs.converged = nconv;
+    bs.max_est_error = max_est;
+    bs.max_residual64 = max_res;
+    bs.fs32_ms = g->fs_ms[0] + bs.batch_ms;
+    bs.fs64_ms = g->fs_ms[1];
+    bs.launches = g->launches;
+    bs.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (stats) *stats = bs;
+    if (nconv < nl)
+        return fail(RT3D_ENOTCONVERGED, "%d of %d wavelengths not converged", nl - nconv, nl);
     return RT3D_OK;
 }
 

@@ -1,0 +1,346 @@
+// Batched wavelengths: n_lambda independent ALI solves (Eq. alo) that share
+// the geometry cache (Sec. 4.1: "the geometry and thus, the set of tracks ...
+// remain the same for all wavelength points"). Every kernel takes the
+// wavelength from blockIdx.y (or .z) and returns at once for a retired one,
+// so one captured sequence of launches (a CUDA graph) serves every
+// iteration whatever the number of wavelengths still active. A wavelength
+// retires on the device when the estimated error of its J (last change
+// times rho/(1-rho), rho from the last kHist changes) is below tol, or when
+// its changes stagnate (the FP32 floor), which hands it to the FP64
+// refinement.
+#include "rt3d_internal.cuh"
+
+namespace rt3d {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long dbits(double x) {
+    return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ double bitsd(unsigned long long x) {
+    return __longlong_as_double((long long)x);
+}
+
+__device__ __forceinline__ void bmax_atomic(double x, unsigned long long *dst) {
+    __shared__ unsigned long long sm[32];
+    unsigned long long b = dbits(fabs(x));
+    if (x != x) b = 0x7ff8000000000000ULL;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, b, off);
+        b = o > b ? o : b;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sm[wid] = b;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        b = lane < nw ? sm[lane] : 0ULL;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, b, off);
+            b = o > b ? o : b;
+        }
+        if (lane == 0 && b) atomicMax(dst, b);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ float clamp01f(float x) { return x < 0.f ? 0.f : (x > 1.f ? 1.f : x); }
+
+// Interval functions (same construction as the unbatched FP32 path).
+struct IntF {
+    float E, a0, a, d;
+};
+__device__ __forceinline__ IntF interval_f(float u) {
+    IntF r;
+    if (u < 1.0f) {
+        constexpr float c0 = 2.0f / 6.0f, c1 = -2.0f / 24.0f, c2 = 2.0f / 120.0f,
+                        c3 = -2.0f / 720.0f, c4 = 2.0f / 5040.0f, c5 = -2.0f / 40320.0f,
+                        c6 = 2.0f / 362880.0f, c7 = -2.0f / 3628800.0f, c8 = 2.0f / 39916800.0f;
+        float p = fmaf(c8, u, c7);
+        p = fmaf(p, u, c6);
+        p = fmaf(p, u, c5);
+        p = fmaf(p, u, c4);
+        p = fmaf(p, u, c3);
+        p = fmaf(p, u, c2);
+        p = fmaf(p, u, c1);
+        p = fmaf(p, u, c0);
+        const float b = u * p;
+        const float a = 0.5f * u * (1.0f - b);
+        const float e0 = u * (1.0f - a);
+        r.E = 1.0f - e0;
+        r.a = a;
+        r.a0 = e0 - a;
+        r.d = a - b;
+    } else {
+        const float E = __expf(-u);
+        const float ru = __fdividef(1.0f, u);
+        const float e0 = 1.0f - E;
+        const float a = fmaf(-e0, ru, 1.0f);
+        r.E = E;
+        r.a = a;
+        r.a0 = fmaf(-(1.0f + u), E, 1.0f) * ru;
+        r.d = fmaf(2.0f, a, -e0) * ru;
+    }
+    return r;
+}
+
+// S = (1 - eps) J + eps B into the four replicas of the packed (chi, S) of
+// every active wavelength (blockIdx.y).
+__global__ void b_source(int nx, int ny, int nz, const double *J, const double *eps,
+                         const double *B, float2 *chiS, const BatchState *bs) {
+    const int l = blockIdx.y;
+    if (!bs->active[l]) return;
+    const long long n = (long long)nx * ny * nz;
+    const double *Jl = J + l * n, *el = eps + l * n, *Bl = B + l * n;
+    float2 *cl = chiS + 4 * l * n;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+        const float s = (float)((1.0 - el[v]) * Jl[v] + el[v] * Bl[v]);
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) cl[rep_index(x + a * nx, y + b * ny, z, nx, ny)].y = s;
+    }
+}
+
+// FP32 formal solution (no Lambda*) of wavelength blockIdx.z into its
+// replicated FP64 J; the per-point arithmetic is that of the unbatched fast
+// kernel.
+template <bool PARAB>
+__global__ void __launch_bounds__(128) b_fs(BatchFsParams p) {
+    const int l = blockIdx.z;
+    if (!p.bs->active[l]) return;
+    const int nray = p.nx * p.ny;
+    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= nray) return;
+    const long long n4 = 4LL * nray * p.nz;
+    const int o = p.order[blockIdx.y];
+    const int x0 = ray % p.nx, y0 = ray / p.nx;
+    const int base = x0 + 2 * p.nx * y0;
+    const int K = p.tlen[o];
+    const float4 *__restrict__ rec = p.rec32 + p.toff[o];
+    const float2 *__restrict__ chiS = p.chiS + l * n4;
+    double *__restrict__ J = p.Jrep + l * n4;
+    double I0;
+    if (p.up[o]) I0 = p.bot_face ? p.bot_face[(long long)l * nray + ray] : p.I_bot;
+    else I0 = p.top_face ? p.top_face[(long long)l * nray + ray] : p.I_top;
+    float I = (float)I0;
+    float4 r = __ldg(rec);
+    int vc = base + __float_as_int(r.x);
+    float2 cs = chiS[vc];
+    float hc = cs.x * r.y;
+    float cwc = r.z;
+    float hp = 0.0f, Sc = cs.y, Sp = cs.y;
+    for (int k = 1; k < K; ++k) {
+        const float4 rn = __ldg(rec + k);
+        const int vn = base + __float_as_int(rn.x);
+        const float2 cn = chiS[vn];
+        const float hn = cn.x * rn.y;
+        const float Sn = cn.y;
+        const float u = hp + hc;
+        const IntF f = interval_f(u);
+        float al = f.a0, bg = f.a, ga = 0.0f;
+        if (PARAB) {
+            const float w = hc + hn;
+            const float q = __fdividef(u, w);
+            const float fw = clamp01f(2.0f - 2.0f * u) * clamp01f(2.0f - 0.5f * q);
+            if (fw > 0.0f) {
+                const float sd = fw * __fdividef(u, u + w) * f.d;
+                bg = f.a + sd;
+                ga = -q * sd;
+                al = f.a0 - sd;
+            }
+        }
+        I = f.E * I + al * Sp + bg * Sc + ga * (Sn - Sc);
+        atomicAdd(J + vc, (double)(cwc * I));
+        hp = hc;
+        hc = hn;
+        Sp = Sc;
+        Sc = Sn;
+        vc = vn;
+        cwc = rn.z;
+    }
+    const IntF f = interval_f(hp + hc);
+    I = f.E * I + f.a0 * Sp + f.a * Sc;
+    atomicAdd(J + vc, (double)(cwc * I));
+}
+
+// Jfs = fold(Jrep); r = Jfs - J; dJ0 = r / diag; Jrep zeroed for the next
+// formal solution; per-wavelength sweep state reset.
+__global__ void b_fold_init(int nx, int ny, int nz, double *Jrep, const double *J,
+                            const double *inv_diag, double *r, double *dJ0, BatchState *bs) {
+    const int l = blockIdx.y;
+    if (!bs->active[l]) return;
+    const long long n = (long long)nx * ny * nz;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        bs->done[l] = 0;
+        bs->count[l] = 0;
+        bs->rel[l] = 0ULL;
+    }
+    if (tid <= kBatchSweeps) {
+        bs->dmax[l * (kBatchSweeps + 1) + tid] = 0ULL;
+        bs->jmax[l * (kBatchSweeps + 1) + tid] = 0ULL;
+    }
+    double *Jr = Jrep + 4 * l * n;
+    for (long long v = tid; v < n; v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+        const long long i0 = rep_index(x, y, z, nx, ny), i1 = rep_index(x + nx, y, z, nx, ny);
+        const long long i2 = rep_index(x, y + ny, z, nx, ny), i3 = rep_index(x + nx, y + ny, z, nx, ny);
+        const double jfs = (Jr[i0] + Jr[i1]) + (Jr[i2] + Jr[i3]);
+        Jr[i0] = 0.0;
+        Jr[i1] = 0.0;
+        Jr[i2] = 0.0;
+        Jr[i3] = 0.0;
+        const double rv = jfs - J[l * n + v];
+        r[l * n + v] = rv;
+        dJ0[l * n + v] = rv * inv_diag[l * n + v];
+    }
+}
+
+// Jacobi sweep m of every active wavelength (FP32 products of the stored
+// FP32 coefficients, FP64 state), with the stop test of the unbatched solve.
+__global__ void __launch_bounds__(256) b_sweep(int nx, int ny, int nz, const float *__restrict__ a,
+                                               const double *__restrict__ inv_diag,
+                                               const double *__restrict__ r, double *buf0,
+                                               double *buf1, int m, double tol, BatchState *bs) {
+    const int l = blockIdx.y;
+    if (!bs->active[l] || bs->done[l]) return;
+    unsigned long long *dmx = bs->dmax + l * (kBatchSweeps + 1);
+    unsigned long long *jmx = bs->jmax + l * (kBatchSweeps + 1);
+    if (m >= 2) {
+        if (bitsd(dmx[m - 1]) <= tol * bitsd(jmx[m - 1])) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                bs->done[l] = 1;
+                bs->count[l] = m - 1;
+            }
+            return;
+        }
+    }
+    const long long n = (long long)nx * ny * nz;
+    const double *src = ((m - 1) & 1 ? buf1 : buf0) + l * n;
+    double *dst = (m & 1 ? buf1 : buf0) + l * n;
+    const float *al = a + 26 * l * n;
+    const double *il = inv_diag + l * n, *rl = r + l * n;
+    double dmax = 0.0, jmax = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+        const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+        const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+        float acc = 0.0f;
+        int plane = 0;
+#pragma unroll
+        for (int d = 0; d < 27; ++d) {
+            if (d == 13) continue;
+            const int zz = z + d / 9 - 1;
+            const float coef = al[(long long)plane * n + v];
+            ++plane;
+            if (zz < 0 || zz >= nz) continue;
+            const long long u = xs[d % 3] + (long long)nx * (ys[(d / 3) % 3] + (long long)ny * zz);
+            acc = fmaf(coef, (float)src[u], acc);
+        }
+        const double nv = (rl[v] + (double)acc) * il[v];
+        dst[v] = nv;
+        dmax = fmax(dmax, fabs(nv - src[v]));
+        jmax = fmax(jmax, fabs(nv));
+    }
+    bmax_atomic(dmax, &dmx[m]);
+    bmax_atomic(jmax, &jmx[m]);
+}
+
+// J += dJ (final sweep buffer); rel = max |dJ| / |J| per wavelength.
+__global__ void b_update(int n, double *J, const double *buf0, const double *buf1,
+                         int max_sweeps, BatchState *bs) {
+    const int l = blockIdx.y;
+    if (!bs->active[l]) return;
+    const int cnt = bs->done[l] ? bs->count[l] : max_sweeps;
+    const double *dJ = (cnt & 1 ? buf1 : buf0) + (long long)l * n;
+    double *Jl = J + (long long)l * n;
+    double rel = 0.0;
+    bool bad = false;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const double d = dJ[v];
+        const double jn = Jl[v] + d;
+        Jl[v] = jn;
+        if (d != 0.0) rel = fmax(rel, fabs(d) / fabs(jn));
+        bad |= !(fabs(jn) <= 1.79e308);
+    }
+    bmax_atomic(bad ? __longlong_as_double(0x7ff8000000000000LL) : rel, &bs->rel[l]);
+}
+
+// Per wavelength: record the change, estimate the error from the last kHist
+// changes, retire when converged (state 1), stagnated at the rounding floor
+// of the formal solution (state 2), failed (state 3: NaN) or out of
+// iterations (state 4).
+__global__ void b_retire(int nl, double tol, int max_iter, BatchState *bs) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl || !bs->active[l]) return;
+    const double rel = bitsd(bs->rel[l]);
+    const int it = ++bs->iters[l];
+    double *h = bs->hist + l * kHist;
+    h[(it - 1) % kHist] = rel;
+    if (!(rel == rel)) {
+        bs->active[l] = 0;
+        bs->state[l] = 3;
+        return;
+    }
+    double rho = 0.9;
+    if (it >= 2) {
+        const int m = it - 1 < kHist - 1 ? it - 1 : kHist - 1;
+        const double a = h[(it - 1 - m) % kHist];
+        rho = (a > 0.0 && rel > 0.0) ? pow(rel / a, 1.0 / m) : 0.0;
+        rho = rho > 0.999 ? 0.999 : rho;
+    }
+    const double est = rel * rho / (1.0 - rho);
+    bs->est[l] = est;
+    if (it >= 2 && est <= tol) {
+        bs->active[l] = 0;
+        bs->state[l] = 1;
+    } else if (it >= kHist && rel > 0.7 * h[it % kHist] && rel < 1e-2) {
+        bs->active[l] = 0;  // no decrease over the window: rounding floor
+        bs->state[l] = 2;
+    } else if (it >= max_iter) {
+        bs->active[l] = 0;
+        bs->state[l] = 4;
+    }
+}
+
+__global__ void b_count_active(int nl, BatchState *bs) {
+    int c = 0;
+    for (int l = threadIdx.x; l < nl; l += 32) c += bs->active[l];
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if (threadIdx.x == 0) bs->nactive = c;
+}
+
+int grid_x(long long n, int threads, int cap) {
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, double *J, const double *eps,
+                                   const double *B, const float *a, const double *inv_diag,
+                                   double *r, double *buf0, double *buf1, int max_sweeps,
+                                   double sweep_tol, double tol, int max_iter, bool parabolic,
+                                   cudaStream_t s) {
+    const long long n = (long long)p.nx * p.ny * p.nz;
+    const int gx = grid_x(n, 256, 152 * 2);
+    b_source<<<dim3(gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, J, eps, B, p.chiS, p.bs);
+    dim3 gfs((p.nx * p.ny + 127) / 128, p.nangles, nl);
+    if (parabolic) b_fs<true><<<gfs, 128, 0, s>>>(p);
+    else b_fs<false><<<gfs, 128, 0, s>>>(p);
+    b_fold_init<<<dim3(gx < 2 ? 2 : gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, p.Jrep, J, inv_diag,
+                                                          r, buf0, p.bs);
+    for (int m = 1; m <= max_sweeps; ++m)
+        b_sweep<<<dim3(gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, a, inv_diag, r, buf0, buf1, m,
+                                            sweep_tol, p.bs);
+    b_update<<<dim3(gx, nl), 256, 0, s>>>((int)n, J, buf0, buf1, max_sweeps, p.bs);
+    b_retire<<<(nl + 127) / 128, 128, 0, s>>>(nl, tol, max_iter, p.bs);
+    b_count_active<<<1, 32, 0, s>>>(nl, p.bs);
+    return cudaGetLastError();
+}
+
+}  // namespace rt3d

@@ -142,6 +142,12 @@ __device__ __forceinline__ int voxel_of(uint32_t c, int x0, int y0, int nx, int 
     return x + nx * (y + ny * (int)(c >> 22));
 }
 
+// index of the same point in the 2 x 2-replicated packed (chi, S) array
+__device__ __forceinline__ int rep_of(uint32_t c, int x0, int y0, int nx, int ny) {
+    return (int)rep_index(x0 + (int)(c & 0x7ffu), y0 + (int)((c >> 11) & 0x7ffu), (int)(c >> 22),
+                          nx, ny);
+}
+
 template <typename R, bool PARAB, bool LSTAR>
 __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
     using R2 = typename V2<R>::T;
@@ -166,7 +172,7 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
     R I = (R)I0;
 
     int v = voxel_of(__ldg(code), x0, y0, p.nx, p.ny);
-    R2 cs = chiS[v];
+    R2 cs = chiS[rep_of(__ldg(code), x0, y0, p.nx, p.ny)];
     R chil_c = cs.x * __ldg(len);
     R chil_p = R(0);
     R S_c = cs.y, S_p = cs.y;
@@ -181,8 +187,9 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
         int vn = v;
         R chil_n = R(0), S_n = S_c;
         if (has_next) {
-            vn = voxel_of(__ldg(code + k + 1), x0, y0, p.nx, p.ny);
-            const R2 c2 = chiS[vn];
+            const uint32_t cn = __ldg(code + k + 1);
+            vn = voxel_of(cn, x0, y0, p.nx, p.ny);
+            const R2 c2 = chiS[rep_of(cn, x0, y0, p.nx, p.ny)];
             chil_n = c2.x * __ldg(len + k + 1);
             S_n = c2.y;
         }
@@ -227,6 +234,82 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
     }
 }
 
+// FP32 formal solution without Lambda* (every iteration after the first).
+// Per point: one 16-byte broadcast load of the step record (replicated
+// offset, l/2, J weight), one integer add for the replicated address, one
+// 8-byte (chi, S) gather, the interval arithmetic, and one FP64 reduction
+// into the replicated J (folded afterwards). The last point (linear form)
+// is peeled off the loop.
+template <bool PARAB>
+__global__ void __launch_bounds__(128) fs_fast_kernel(FsParams p) {
+    const int nray = p.nx * p.ny;
+    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= nray) return;
+    const int o = p.order[blockIdx.y];
+    const int x0 = ray % p.nx, y0 = ray / p.nx;
+    const int base = x0 + 2 * p.nx * y0;
+    const int K = p.tlen[o];
+    const float4 *__restrict__ rec = p.rec32 + p.toff[o];
+    const float2 *__restrict__ chiS = static_cast<const float2 *>(p.chiS);
+    double *__restrict__ J = p.Jrep;
+
+    double I0 = 0.0;
+    if (!p.homogeneous) {
+        if (p.up[o]) I0 = p.bot_face ? p.bot_face[ray] : p.I_bot;
+        else I0 = p.top_face ? p.top_face[ray] : p.I_top;
+    }
+    float I = (float)I0;
+    float4 r = __ldg(rec);
+    int vc = base + __float_as_int(r.x);
+    float2 cs = chiS[vc];
+    float hc = cs.x * r.y;  // half the optical depth of the chord of the point
+    float cwc = r.z;
+    float hp = 0.0f, Sc = cs.y, Sp = cs.y;
+    for (int k = 1; k < K; ++k) {
+        const float4 rn = __ldg(rec + k);
+        const int vn = base + __float_as_int(rn.x);
+        const float2 cn = chiS[vn];
+        const float hn = cn.x * rn.y;
+        const float Sn = cn.y;
+        const float u = hp + hc;
+        const IntervalF f = interval(u);
+        float al = f.a0, bg = f.a, ga = 0.0f;
+        if (PARAB) {
+            const float w = hc + hn;
+            const float q = __fdividef(u, w);
+            const float fw = clamp01(2.0f - 2.0f * u) * clamp01(2.0f - 0.5f * q);
+            if (fw > 0.0f) {
+                const float sd = fw * __fdividef(u, u + w) * f.d;
+                bg = f.a + sd;
+                ga = -q * sd;
+                al = f.a0 - sd;
+            }
+        }
+        I = f.E * I + al * Sp + bg * Sc + ga * (Sn - Sc);
+        atomicAdd(J + vc, (double)(cwc * I));
+        hp = hc;
+        hc = hn;
+        Sp = Sc;
+        Sc = Sn;
+        vc = vn;
+        cwc = rn.z;
+    }
+    const IntervalF f = interval(hp + hc);
+    I = f.E * I + f.a0 * Sp + f.a * Sc;
+    atomicAdd(J + vc, (double)(cwc * I));
+}
+
+__global__ void fold_kernel(int nx, int ny, int nz, const double *__restrict__ Jrep,
+                            double *__restrict__ J) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+        J[v] = (Jrep[rep_index(x, y, z, nx, ny)] + Jrep[rep_index(x + nx, y, z, nx, ny)]) +
+               (Jrep[rep_index(x, y + ny, z, nx, ny)] + Jrep[rep_index(x + nx, y + ny, z, nx, ny)]);
+    }
+}
+
 template <typename R, bool PARAB, bool LSTAR>
 cudaError_t launch_t(const FsParams &p, cudaStream_t s) {
     const int threads = 128;
@@ -236,6 +319,22 @@ cudaError_t launch_t(const FsParams &p, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, cudaStream_t s) {
+    const int threads = 128;
+    dim3 grid((p.nx * p.ny + threads - 1) / threads, p.nangles);
+    if (parabolic) fs_fast_kernel<true><<<grid, threads, 0, s>>>(p);
+    else fs_fast_kernel<false><<<grid, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(int nx, int ny, int nz, const double *Jrep, double *J, cudaStream_t s) {
+    const long long n = (long long)nx * ny * nz;
+    long long b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    fold_kernel<<<(int)b, 256, 0, s>>>(nx, ny, nz, Jrep, J);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_fs(const FsParams &p, bool fp64, bool parabolic, bool lstar, cudaStream_t s) {
     if (fp64) {

@@ -39,7 +39,20 @@ struct Template {
     double *cw64 = nullptr;     // [total] w_Omega l_k / (sum of l over the layer)
     float *cw32 = nullptr;
     uint64_t *win = nullptr;    // [total] Lambda* window: 9 x 5-bit neighbour codes
+    // [total] FP32 step record for the formal solution without Lambda*:
+    // (offset in the 2x2-replicated grid as int bits, l/2, J weight, 0)
+    float4 *rec32 = nullptr;
 };
+
+// The packed (chi, S) arrays are replicated 2 x 2 in x and y: element
+// (x, y, z) of the box sits at x + a nx + 2 nx (y + b ny + 2 ny z) for a, b in
+// {0, 1}. A characteristic from face cell (x0, y0) then finds its point at
+// replicated offset x0 + 2 nx y0 + o_k with o_k the cached offset of the
+// reference characteristic (wrapped offsets are < nx, < ny), without any
+// periodic wrap test.
+__host__ __device__ inline long long rep_index(int x, int y, int z, int nx, int ny) {
+    return (long long)x + 2LL * nx * ((long long)y + 2LL * ny * z);
+}
 
 struct FsParams {
     int nx, ny, nz;
@@ -52,12 +65,15 @@ struct FsParams {
     const void *len;   // float or double [total]
     const void *cw;    // float or double [total]
     const uint64_t *win;
-    const void *chiS;  // float2 or double2 [N]: (chi, S)
+    const void *chiS;  // float2 or double2 [4N]: (chi, S), replicated 2 x 2 in x, y
     double *J;         // [N], accumulated into (zeroed by the caller)
+    const float4 *rec32;  // FP32 step records (fast path)
+    double *Jrep;      // [4N] replicated accumulation target of the fast path
     double *lstar;     // nullable [27][N], accumulated into
     const double *top_face;  // nullable [ny*nx]
     const double *bot_face;  // nullable [ny*nx]
     double I_top, I_bot;
+    double I_irr;      // spherical grid: irradiation
     int homogeneous;   // 1: zero boundary intensity, whatever the faces say
 };
 
@@ -74,6 +90,7 @@ struct TraceParams {
     double *cw64;
     float *cw32;
     uint64_t *win;
+    float4 *rec32;
     double *layer_sum;        // scratch [nangles][nz]
     int *err;                 // out: first error code (0 ok)
 };
@@ -81,6 +98,10 @@ struct TraceParams {
 // Launchers (return the launch status).
 cudaError_t launch_trace(const TraceParams &p, cudaStream_t s);
 cudaError_t launch_fs(const FsParams &p, bool fp64, bool parabolic, bool lstar, cudaStream_t s);
+// FP32 formal solution without Lambda* into p.Jrep (zeroed by the caller)
+cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, cudaStream_t s);
+// J[v] = sum of the four replicas of v in Jrep
+cudaError_t launch_fold(int nx, int ny, int nz, const double *Jrep, double *J, cudaStream_t s);
 
 // ---- ALI / OS kernels (ali.cu) ----
 struct OsState {
@@ -95,18 +116,26 @@ struct OsState {
     int changed;                   // content comparison flag
 };
 
-cudaError_t launch_pack(int n, const double *chi, double chi_scale, const double *S,
-                        void *chiS, bool fp64, cudaStream_t s);
-cudaError_t launch_source(int n, const double *J, const double *eps, const double *B,
-                          void *chiS, bool fp64, bool homogeneous, cudaStream_t s);
+cudaError_t launch_pack(int nx, int ny, int nz, const double *chi, double chi_scale,
+                        const double *S, void *chiS, bool fp64, cudaStream_t s);
+cudaError_t launch_source(int nx, int ny, int nz, const double *J, const double *eps,
+                          const double *B, void *chiS, bool fp64, bool homogeneous,
+                          cudaStream_t s);
+// periodic axes of the 27-point OS stencil: Cartesian box x and y, spherical
+// grid phi (the third index)
+struct Periodic {
+    bool x, y, z;
+};
 cudaError_t launch_os_prep(int nx, int ny, int nz, const double *lstar, const double *eps,
-                           void *a, bool a64, double *inv_diag, cudaStream_t s);
+                           void *a, bool a64, double *inv_diag, cudaStream_t s,
+                           Periodic per = {true, true, false});
 cudaError_t launch_os_init(int n, const double *Jfs, const double *J, const double *rhs_extra,
                            const double *inv_diag, double *r, double *dJ0, OsState *st,
                            cudaStream_t s);
 cudaError_t launch_os_sweep(int nx, int ny, int nz, const void *a, bool a64,
                             const double *inv_diag, const double *r, double *const *buf,
-                            int m, double tol, OsState *st, cudaStream_t s);
+                            int m, double tol, OsState *st, cudaStream_t s,
+                            Periodic per = {true, true, false});
 cudaError_t launch_os_finish(int max_sweeps, double tol, OsState *st, cudaStream_t s);
 cudaError_t launch_ali_update(int n, double *J, double *const *buf, OsState *st,
                               double *dJ_out, cudaStream_t s);
@@ -117,6 +146,93 @@ cudaError_t launch_compare(long long n, const double *a, const double *b, OsStat
                            cudaStream_t s);
 cudaError_t launch_copy_buf(int n, double *const *buf, const OsState *st, double *dst,
                             cudaStream_t s);
+
+// ---- batched wavelengths (batch.cu) ----
+constexpr int kBatchSweeps = 50;  // Jacobi sweeps per OS solve (stop test 1e-3)
+constexpr int kHist = 11;         // changes kept per wavelength for the error estimate
+
+// Per-wavelength state in device memory (arrays of n_lambda, sweep maxima of
+// n_lambda x (kBatchSweeps + 1), change history of n_lambda x kHist).
+struct BatchState {
+    int *active;   // 1 while iterating
+    int *state;    // 0 running, 1 converged, 2 stagnated, 3 NaN, 4 iteration cap
+    int *done;     // Jacobi stop test met
+    int *count;    // Jacobi sweeps done
+    int *iters;    // ALI iterations done
+    unsigned long long *dmax, *jmax, *rel;
+    double *hist, *est;
+    int nactive;   // wavelengths still active (written on the device)
+};
+
+struct BatchFsParams {
+    int nx, ny, nz, nangles;
+    const int *order;
+    const long long *toff;
+    const int *tlen;
+    const signed char *up;
+    const float4 *rec32;
+    float2 *chiS;          // [n_lambda][4N]
+    double *Jrep;          // [n_lambda][4N]
+    const double *top_face, *bot_face;  // nullable [n_lambda][ny*nx]
+    double I_top, I_bot;
+    BatchState *bs;        // device copy
+};
+
+// One batched ALI iteration (source, formal solution, fold and OS right-hand
+// side, Jacobi sweeps, update, retirement, active count): a fixed launch
+// sequence, captured once into a CUDA graph.
+cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, double *J, const double *eps,
+                                   const double *B, const float *a, const double *inv_diag,
+                                   double *r, double *buf0, double *buf1, int max_sweeps,
+                                   double sweep_tol, double tol, int max_iter, bool parabolic,
+                                   cudaStream_t s);
+
+// ---- spherical grid (sph.cu) ----
+struct SphTables {
+    int nr, nt, np;
+    const double *re2;              // [nr+1] squared radial edges
+    const double *ct, *ctk;         // [nt+1] cos(theta_e), cos|cos|
+    const double *cpe, *spe;        // [np] cos/sin of the azimuth edges
+    const double *rc, *stc, *ctc, *cpc, *spc;  // cell centres
+};
+
+struct SphBuildParams {
+    SphTables T;
+    int nangles, o0, nchunk, pass, ncap;
+    const double *dir, *wt;
+    unsigned *hit;      // [nchunk][(N+31)/32]
+    double *tbuf;       // [nchunk][ncap]
+    double *den;        // [nchunk][N]
+    int *nrays;         // [nangles] (pass 1)
+    long long *nseg;    // [nangles] (pass 1)
+    const long long *ray_base, *seg_base;  // [nangles] (pass 2)
+    long long *ray_off;
+    int *ray_len, *ray_angle, *ray_launch, *ray_kind, *ray_face;
+    int *cell, *crep;
+    double *len64, *cw64;
+    float *len32, *cw32;
+    uint64_t *win;
+    int *err;
+};
+
+struct SphFsParams {
+    long long nrays;
+    int N;
+    const long long *ray_off;
+    const int *ray_len, *ray_kind, *ray_face;
+    const int *cell, *crep;
+    const void *len, *cw;
+    const uint64_t *win;
+    const void *chiS;              // replicated packed (chi, S)
+    double *J, *lstar;
+    const double *core_face;       // nullable [np][nt]
+    double I_core, I_out, I_irr;
+    int homogeneous;
+};
+
+cudaError_t launch_sph_build(const SphBuildParams &p, cudaStream_t s);
+cudaError_t launch_sph_fs(const SphFsParams &p, bool fp64, bool parabolic, bool lstar,
+                          cudaStream_t s);
 
 // Sets the message returned by rt3d_last_error() on this thread.
 void set_last_error(const char *msg);

@@ -1,0 +1,458 @@
+// Spherical (r, theta, phi) grid of the paper's SP test case (Sec. 3.2):
+// geometry cache of long characteristics and the formal solution over it.
+//
+// Ray set of a solid angle: the voxels are visited in index order and every
+// voxel that no ray of this angle has crossed yet launches the full line
+// through its centre, traced from its entry (outer sphere, or the core sphere
+// r = r_in) to its exit; all cells it crosses are marked. One thread per
+// angle builds the set (pass 1 counts rays and segments, pass 2 writes the
+// tables). Crossings with the radial spheres, the polar cones (the plane z = 0
+// for theta = pi/2) and the azimuthal half-planes are computed with
+// round-to-nearest FP64 intrinsics (no contraction), sorted, equal parameters
+// merged, and the cell of every interval found at its midpoint by comparisons
+// only (r^2, z|z| against cos|cos| r^2, signs of cross products), so the
+// cache is reproducible bit for bit. Per segment the cache stores the cell,
+// its index in the 2 x 2-replicated packed (chi, S) array, the chord, the J
+// weight w l / (chord sum of the cell for this angle) and the Lambda* window
+// (neighbourhood in index space, periodic in phi only).
+#include "rt3d_internal.cuh"
+
+namespace rt3d {
+
+namespace {
+
+__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dd(double a, double b) { return __ddiv_rn(a, b); }
+
+__device__ int sph_cell(const SphTables &T, double p0, double p1, double p2) {
+    const double r2 = da(da(dm(p0, p0), dm(p1, p1)), dm(p2, p2));
+    int ir = 0;
+    while (ir + 1 < T.nr && T.re2[ir + 1] <= r2) ++ir;
+    const double key = dm(p2, fabs(p2));
+    int it = 0;
+    while (it + 1 < T.nt && dm(T.ctk[it + 1], r2) >= key) ++it;
+    int ip = 0;
+    for (int k = 0; k < T.np; ++k) {
+        const int k1 = (k + 1) % T.np;
+        const double c0 = ds(dm(T.cpe[k], p1), dm(T.spe[k], p0));
+        const double c1 = ds(dm(T.cpe[k1], p1), dm(T.spe[k1], p0));
+        if (c0 >= 0.0 && c1 < 0.0) {
+            ip = k;
+            break;
+        }
+    }
+    return ir + T.nr * (it + T.nt * ip);
+}
+
+__device__ void heapsort(double *a, int n) {
+    for (int start = n / 2 - 1; start >= 0; --start) {
+        int root = start;
+        while (2 * root + 1 < n) {
+            int child = 2 * root + 1;
+            if (child + 1 < n && a[child] < a[child + 1]) ++child;
+            if (a[root] < a[child]) {
+                const double t = a[root];
+                a[root] = a[child];
+                a[child] = t;
+                root = child;
+            } else {
+                break;
+            }
+        }
+    }
+    for (int end = n - 1; end > 0; --end) {
+        const double t = a[0];
+        a[0] = a[end];
+        a[end] = t;
+        int root = 0;
+        while (2 * root + 1 < end) {
+            int child = 2 * root + 1;
+            if (child + 1 < end && a[child] < a[child + 1]) ++child;
+            if (a[root] < a[child]) {
+                const double u = a[root];
+                a[root] = a[child];
+                a[child] = u;
+                root = child;
+            } else {
+                break;
+            }
+        }
+    }
+}
+
+// Crossing parameters of the line P + t d strictly inside (t0, t1), sorted
+// and merged, with t0 and t1 at the ends; returns the number of parameters.
+// entry: 0 outer sphere, 1 core sphere.
+__device__ int sph_params(const SphTables &T, const double *P, const double *d, double *ts,
+                          int *entry, double *pin) {
+    const double b = da(da(dm(P[0], d[0]), dm(P[1], d[1])), dm(P[2], d[2]));
+    const double P2 = da(da(dm(P[0], P[0]), dm(P[1], P[1])), dm(P[2], P[2]));
+    const double disc = ds(dm(b, b), ds(P2, T.re2[T.nr]));
+    const double sq = __dsqrt_rn(disc);
+    double t0 = ds(-b, sq), t1 = da(-b, sq);
+    *entry = 0;
+    const double dc = ds(dm(b, b), ds(P2, T.re2[0]));
+    if (dc > 0.0) {
+        const double sc = __dsqrt_rn(dc);
+        const double a = ds(-b, sc), c = da(-b, sc);
+        if (c <= 0.0 && c > t0) {
+            t0 = c;
+            *entry = 1;
+        }
+        if (a >= 0.0 && a < t1) t1 = a;
+    }
+    int n = 1;  // ts[0] = t0 later
+    for (int i = 1; i < T.nr; ++i) {
+        const double di = ds(dm(b, b), ds(P2, T.re2[i]));
+        if (!(di > 0.0)) continue;
+        const double s = __dsqrt_rn(di);
+        const double r1 = ds(-b, s), r2 = da(-b, s);
+        if (r1 > t0 && r1 < t1) ts[n++] = r1;
+        if (r2 > t0 && r2 < t1) ts[n++] = r2;
+    }
+    for (int j = 1; j < T.nt; ++j) {
+        if (2 * j == T.nt) {
+            if (d[2] != 0.0) {
+                const double t = dd(-P[2], d[2]);
+                if (t > t0 && t < t1) ts[n++] = t;
+            }
+            continue;
+        }
+        const double c2 = dm(T.ct[j], T.ct[j]);
+        const double A = ds(dm(d[2], d[2]), c2);
+        const double Bh = ds(dm(P[2], d[2]), dm(c2, b));
+        const double C = ds(dm(P[2], P[2]), dm(c2, P2));
+        double roots[2];
+        int nr_ = 0;
+        if (A == 0.0) {
+            if (Bh != 0.0) roots[nr_++] = dd(-C, dm(2.0, Bh));
+        } else {
+            const double dq = ds(dm(Bh, Bh), dm(A, C));
+            if (dq > 0.0) {
+                const double s = __dsqrt_rn(dq);
+                roots[nr_++] = dd(ds(-Bh, s), A);
+                roots[nr_++] = dd(da(-Bh, s), A);
+            }
+        }
+        for (int q = 0; q < nr_; ++q) {
+            const double t = roots[q];
+            if (!(t > t0 && t < t1)) continue;
+            const double z = da(P[2], dm(t, d[2]));
+            if (dm(z, T.ct[j]) > 0.0) ts[n++] = t;
+        }
+    }
+    for (int k = 0; k < T.np; ++k) {
+        const double den = ds(dm(T.cpe[k], d[1]), dm(T.spe[k], d[0]));
+        if (den == 0.0) continue;
+        const double t = dd(ds(dm(T.spe[k], P[0]), dm(T.cpe[k], P[1])), den);
+        if (!(t > t0 && t < t1)) continue;
+        const double x = da(P[0], dm(t, d[0])), y = da(P[1], dm(t, d[1]));
+        if (da(dm(T.cpe[k], x), dm(T.spe[k], y)) > 0.0) ts[n++] = t;
+    }
+    heapsort(ts + 1, n - 1);
+    ts[0] = t0;
+    int m = 1;
+    for (int i = 1; i < n; ++i)
+        if (ts[i] != ts[m - 1]) ts[m++] = ts[i];
+    if (t1 != ts[m - 1]) ts[m++] = t1;
+    pin[0] = da(P[0], dm(t0, d[0]));
+    pin[1] = da(P[1], dm(t0, d[1]));
+    pin[2] = da(P[2], dm(t0, d[2]));
+    return m;
+}
+
+__device__ __forceinline__ int nb_code_sph(int nr, int nt, int np, int a, int b) {
+    const int ra = a % nr, ta = (a / nr) % nt, pa = a / (nr * nt);
+    const int rb = b % nr, tb = (b / nr) % nt, pb = b / (nr * nt);
+    const int dr = ra - rb, dt = ta - tb;
+    int dp = pa - pb;
+    if (dp < 0) dp += np;
+    if (dp == np - 1) dp = -1;
+    else if (dp > 1) return -1;
+    if (dr < -1 || dr > 1 || dt < -1 || dt > 1) return -1;
+    return (dr + 1) + 3 * (dt + 1) + 9 * (dp + 1);
+}
+
+__global__ void sph_build_kernel(SphBuildParams p) {
+    const int lo = blockIdx.x * blockDim.x + threadIdx.x;
+    const int o = p.o0 + lo;
+    if (lo >= p.nchunk || o >= p.nangles) return;
+    const SphTables &T = p.T;
+    const int N = T.nr * T.nt * T.np;
+    const int words = (N + 31) / 32;
+    unsigned *hit = p.hit + (long long)lo * words;
+    double *ts = p.tbuf + (long long)lo * p.ncap;
+    for (int i = 0; i < words; ++i) hit[i] = 0u;
+    const double d[3] = {p.dir[3 * o], p.dir[3 * o + 1], p.dir[3 * o + 2]};
+    long long seg = p.pass == 2 ? p.seg_base[o] : 0;
+    long long ray = p.pass == 2 ? p.ray_base[o] : 0;
+    const long long seg0 = seg;
+    int nrays = 0;
+    long long nseg = 0;
+    for (int v = 0; v < N; ++v) {
+        if (hit[v >> 5] & (1u << (v & 31))) continue;
+        const int ir = v % T.nr, it = (v / T.nr) % T.nt, ip = v / (T.nr * T.nt);
+        const double P[3] = {dm(dm(T.rc[ir], T.stc[it]), T.cpc[ip]),
+                             dm(dm(T.rc[ir], T.stc[it]), T.spc[ip]), dm(T.rc[ir], T.ctc[it])};
+        int entry;
+        double pin[3];
+        const int m = sph_params(T, P, d, ts, &entry, pin);
+        if (m > p.ncap) {
+            atomicCAS(p.err, 0, 4);
+            return;
+        }
+        const int K = m - 1;
+        hit[v >> 5] |= 1u << (v & 31);
+        for (int k = 0; k < K; ++k) {
+            const double mid = dm(0.5, da(ts[k], ts[k + 1]));
+            const int c = sph_cell(T, da(P[0], dm(mid, d[0])), da(P[1], dm(mid, d[1])),
+                                   da(P[2], dm(mid, d[2])));
+            hit[c >> 5] |= 1u << (c & 31);
+            if (p.pass == 2) {
+                const long long sidx = seg + k;
+                p.cell[sidx] = c;
+                const int cr = c % T.nr, ct = (c / T.nr) % T.nt, cp = c / (T.nr * T.nt);
+                p.crep[sidx] = (int)rep_index(cr, ct, cp, T.nr, T.nt);
+                const double l = ds(ts[k + 1], ts[k]);
+                p.len64[sidx] = l;
+                p.len32[sidx] = (float)l;
+            }
+        }
+        if (p.pass == 2) {
+            p.ray_off[ray] = seg;
+            p.ray_len[ray] = K;
+            p.ray_angle[ray] = o;
+            p.ray_launch[ray] = v;
+            int kind = 0, face = 0;
+            if (entry) {
+                kind = 2;
+                const int c0 = p.cell[seg];
+                face = (c0 / T.nr) % T.nt + T.nt * (c0 / (T.nr * T.nt));
+            } else if (pin[0] > 0.0 && d[0] < 0.0) {
+                kind = 1;
+            }
+            p.ray_kind[ray] = kind;
+            p.ray_face[ray] = face;
+            // Lambda* windows of this ray
+            for (int k = 0; k < K; ++k) {
+                const int vk = p.cell[seg + k];
+                const int jend = (k + 1 < K) ? k + 1 : k;
+                uint64_t wc = 0;
+                for (int r = 0; r < kWin; ++r) wc |= (uint64_t)kWinNone << (5 * r);
+                for (int j = jend; j >= 0; --j) {
+                    const int dc = nb_code_sph(T.nr, T.nt, T.np, p.cell[seg + j], vk);
+                    if (dc < 0) break;
+                    const int r = j - k + 7;
+                    if (r < 0) {
+                        atomicCAS(p.err, 0, 3);
+                        break;
+                    }
+                    wc &= ~((uint64_t)31 << (5 * r));
+                    wc |= (uint64_t)dc << (5 * r);
+                }
+                p.win[seg + k] = wc;
+            }
+            ++ray;
+        }
+        seg += K;
+        ++nrays;
+        nseg += K;
+    }
+    if (p.pass == 1) {
+        p.nrays[o] = nrays;
+        p.nseg[o] = nseg;
+        return;
+    }
+    // chord sum of every cell for this angle, then the J weights
+    double *den = p.den + (long long)lo * N;
+    for (int v = 0; v < N; ++v) den[v] = 0.0;
+    for (long long s = seg0; s < seg; ++s) den[p.cell[s]] += p.len64[s];
+    const double w = p.wt[o];
+    for (long long s = seg0; s < seg; ++s) {
+        const double c = w * (p.len64[s] / den[p.cell[s]]);
+        p.cw64[s] = c;
+        p.cw32[s] = (float)c;
+    }
+    for (int v = 0; v < N; ++v)
+        if (!(den[v] > 0.0)) atomicCAS(p.err, 0, 5);
+}
+
+// Interval functions (as on the Cartesian grid).
+__device__ __forceinline__ void ifn(float u, float &E, float &a0, float &a, float &d) {
+    if (u < 1.0f) {
+        constexpr float c0 = 2.0f / 6.0f, c1 = -2.0f / 24.0f, c2 = 2.0f / 120.0f,
+                        c3 = -2.0f / 720.0f, c4 = 2.0f / 5040.0f, c5 = -2.0f / 40320.0f,
+                        c6 = 2.0f / 362880.0f, c7 = -2.0f / 3628800.0f, c8 = 2.0f / 39916800.0f;
+        float q = fmaf(c8, u, c7);
+        q = fmaf(q, u, c6);
+        q = fmaf(q, u, c5);
+        q = fmaf(q, u, c4);
+        q = fmaf(q, u, c3);
+        q = fmaf(q, u, c2);
+        q = fmaf(q, u, c1);
+        q = fmaf(q, u, c0);
+        const float b = u * q;
+        a = 0.5f * u * (1.0f - b);
+        const float e0 = u * (1.0f - a);
+        E = 1.0f - e0;
+        a0 = e0 - a;
+        d = a - b;
+    } else {
+        E = __expf(-u);
+        const float ru = __fdividef(1.0f, u);
+        const float e0 = 1.0f - E;
+        a = fmaf(-e0, ru, 1.0f);
+        a0 = fmaf(-(1.0f + u), E, 1.0f) * ru;
+        d = fmaf(2.0f, a, -e0) * ru;
+    }
+}
+
+constexpr double pcd(int m) {
+    double f = 1.0;
+    for (int i = 2; i <= m + 3; ++i) f *= i;
+    return (m % 2 ? -2.0 : 2.0) / f;
+}
+// Taylor coefficients of p(u) = e2/u^3 = 2 sum_m (-1)^m u^m / (m+3)!
+__constant__ double kPcd[18] = {pcd(0),  pcd(1),  pcd(2),  pcd(3),  pcd(4),  pcd(5),
+                                pcd(6),  pcd(7),  pcd(8),  pcd(9),  pcd(10), pcd(11),
+                                pcd(12), pcd(13), pcd(14), pcd(15), pcd(16), pcd(17)};
+
+__device__ __forceinline__ void ifn(double u, double &E, double &a0, double &a, double &d) {
+    if (u < 0.5) {
+        double q = kPcd[17];
+#pragma unroll
+        for (int m = 16; m >= 0; --m) q = fma(q, u, kPcd[m]);
+        const double b = u * q;
+        a = 0.5 * u * (1.0 - b);
+        const double e0 = u * (1.0 - a);
+        E = 1.0 - e0;
+        a0 = e0 - a;
+        d = a - b;
+    } else {
+        E = exp(-u);
+        const double ru = 1.0 / u;
+        const double e0 = 1.0 - E;
+        a = fma(-e0, ru, 1.0);
+        a0 = fma(-(1.0 + u), E, 1.0) * ru;
+        d = fma(2.0, a, -e0) * ru;
+    }
+}
+
+template <typename R> struct V2s;
+template <> struct V2s<float> { using T = float2; };
+template <> struct V2s<double> { using T = double2; };
+
+template <typename R> __device__ __forceinline__ R clamp01s(R x) {
+    return x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
+}
+__device__ __forceinline__ float divs(float x, float y) { return __fdividef(x, y); }
+__device__ __forceinline__ double divs(double x, double y) { return x / y; }
+
+// One thread per characteristic of the cache (all angles flattened).
+template <typename R, bool PARAB, bool LSTAR>
+__global__ void __launch_bounds__(128) sph_fs_kernel(SphFsParams p) {
+    using R2 = typename V2s<R>::T;
+    const long long ray = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (ray >= p.nrays) return;
+    const long long s0 = p.ray_off[ray];
+    const int K = p.ray_len[ray];
+    const int kind = p.ray_kind[ray];
+    const R2 *__restrict__ chiS = static_cast<const R2 *>(p.chiS);
+    const R *__restrict__ len = static_cast<const R *>(p.len) + s0;
+    const R *__restrict__ cw = static_cast<const R *>(p.cw) + s0;
+    const int *__restrict__ cell = p.cell + s0;
+    const int *__restrict__ crep = p.crep + s0;
+    double I0 = 0.0;
+    if (!p.homogeneous) {
+        if (kind == 2) I0 = p.core_face ? p.core_face[p.ray_face[ray]] : p.I_core;
+        else if (kind == 1) I0 = p.I_irr;
+        else I0 = p.I_out;
+    }
+    R I = (R)I0;
+    int v = cell[0];
+    R2 cs = chiS[crep[0]];
+    R chil_c = cs.x * len[0], chil_p = R(0);
+    R S_c = cs.y, S_p = cs.y;
+    R ring[kWin];
+#pragma unroll
+    for (int i = 0; i < kWin; ++i) ring[i] = R(0);
+    for (int k = 0; k < K; ++k) {
+        const R u = R(0.5) * (chil_p + chil_c);
+        R E, a0, a, d;
+        ifn(u, E, a0, a, d);
+        const bool has_next = k + 1 < K;
+        int vn = v;
+        R chil_n = R(0), S_n = S_c;
+        if (has_next) {
+            vn = cell[k + 1];
+            const R2 c2 = chiS[crep[k + 1]];
+            chil_n = c2.x * len[k + 1];
+            S_n = c2.y;
+        }
+        R al = a0, bg = a, ga = R(0);
+        if (PARAB && has_next) {
+            const R w = R(0.5) * (chil_c + chil_n);
+            if (w > R(0)) {
+                const R q = divs(u, w);
+                const R fw = clamp01s(R(2) - R(2) * u) * clamp01s(R(2) - R(0.5) * q);
+                if (fw > R(0)) {
+                    const R sd = fw * divs(u, u + w) * d;
+                    bg = a + sd;
+                    ga = -q * sd;
+                    al = a0 - sd;
+                }
+            }
+        }
+        I = E * I + al * S_p + bg * S_c + ga * (S_n - S_c);
+        const R c = cw[k];
+        atomicAdd(p.J + v, (double)(c * I));
+        if (LSTAR) {
+#pragma unroll
+            for (int i = 0; i < kWin - 1; ++i) ring[i] = E * ring[i + 1];
+            if (k == 0) ring[7] += al;
+            else ring[6] += al;
+            ring[7] += bg - ga;
+            ring[8] = ga;
+            const uint64_t wc = p.win[s0 + k];
+#pragma unroll
+            for (int i = 0; i < kWin; ++i) {
+                const unsigned dc = (unsigned)(wc >> (5 * i)) & 31u;
+                if (dc != kWinNone) atomicAdd(p.lstar + (long long)dc * p.N + v, (double)(c * ring[i]));
+            }
+        }
+        chil_p = chil_c;
+        chil_c = chil_n;
+        S_p = S_c;
+        S_c = S_n;
+        v = vn;
+    }
+}
+
+template <typename R, bool PARAB, bool LSTAR>
+cudaError_t launch_sph_t(const SphFsParams &p, cudaStream_t s) {
+    const long long blocks = (p.nrays + 127) / 128;
+    sph_fs_kernel<R, PARAB, LSTAR><<<(unsigned)blocks, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sph_build(const SphBuildParams &p, cudaStream_t s) {
+    const int threads = 32;
+    sph_build_kernel<<<(p.nchunk + threads - 1) / threads, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sph_fs(const SphFsParams &p, bool fp64, bool parabolic, bool lstar,
+                          cudaStream_t s) {
+    if (fp64) {
+        if (parabolic) return lstar ? launch_sph_t<double, true, true>(p, s) : launch_sph_t<double, true, false>(p, s);
+        return lstar ? launch_sph_t<double, false, true>(p, s) : launch_sph_t<double, false, false>(p, s);
+    }
+    if (parabolic) return lstar ? launch_sph_t<float, true, true>(p, s) : launch_sph_t<float, true, false>(p, s);
+    return lstar ? launch_sph_t<float, false, true>(p, s) : launch_sph_t<float, false, false>(p, s);
+}
+
+}  // namespace rt3d

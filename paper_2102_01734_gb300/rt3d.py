@@ -26,9 +26,11 @@ except ImportError:  # pragma: no cover
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librt3d.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "rt3d.h")
+HEADERS = [HEADER, os.path.join(os.path.dirname(HERE), "include", "rt3d_nn.h")]
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ETIMEOUT, ENUMERIC = range(7)
 CARTESIAN_PERIODIC_XY = 0
+SPHERICAL = 1
 LINEAR, PARABOLIC = 0, 1
 FP64, FP32_FS_FP64_ALI = 0, 1
 ACCEL_NONE, ACCEL_KRYLOV = 0, 1
@@ -39,12 +41,13 @@ _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 class GridDesc(ctypes.Structure):
     _fields_ = [("geometry", _c_int), ("n", _c_int * 3), ("ntheta", _c_int), ("nphi", _c_int),
                 ("interp", _c_int), ("precision", _c_int), ("nlambda", _c_int),
-                ("cuda_stream", _vp), ("accel", _c_int)]
+                ("cuda_stream", _vp), ("accel", _c_int), ("r_in", _c_double),
+                ("r_out", _c_double)]
 
 
 class BC(ctypes.Structure):
     _fields_ = [("I_top", _c_double), ("I_bottom", _c_double), ("I_top_face", _vp),
-                ("I_bottom_face", _vp)]
+                ("I_bottom_face", _vp), ("I_irr", _c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -52,6 +55,17 @@ class SolveStats(ctypes.Structure):
                 ("jacobi_sweeps", _c_int), ("rel_change", _c_double),
                 ("residual64", _c_double), ("est_error", _c_double), ("seconds", _c_double),
                 ("fs32_ms", _c_double), ("fs64_ms", _c_double), ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("nlambda", _c_int), ("converged", _c_int), ("iterations", _c_int),
+                ("graph_replays", _c_int), ("fs_lambda32", ctypes.c_longlong),
+                ("fs_lambda64", ctypes.c_longlong), ("max_est_error", _c_double),
+                ("max_residual64", _c_double), ("batch_ms", _c_double), ("fs32_ms", _c_double),
+                ("fs64_ms", _c_double), ("seconds", _c_double), ("launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,17 +106,24 @@ def load(path: str | None = None):
     lib.rt3d_solve.argtypes = [_vp, _vp, _vp, _vp, P(BC), _vp, _c_double, _c_int, P(SolveStats)]
     lib.rt3d_os_solve_noalloc.argtypes = [_c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _c_int,
                                           _c_double, P(_c_int), _vp]
+    lib.rt3d_solve_batched.argtypes = [_vp, _c_int, _vp, _vp, _vp, P(BC), _vp, _c_double, _c_int,
+                                       _vp, P(BatchStats)]
+    lib.rt3d_grid_sph_ray.argtypes = [_vp, _c_int, _c_int, P(_c_int), _vp, _vp, P(_c_int),
+                                      P(_c_int)]
     lib.rt3d_last_error.restype = ctypes.c_char_p
     lib.rt3d_last_error.argtypes = []
     _lib = lib
     return lib
 
 
-def header_functions(path: str = HEADER):
-    """Names of the functions declared in include/rt3d.h."""
-    src = open(path).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(rt3d_[a-z0-9_]+)\s*\(", src)))
+def header_functions(paths=None):
+    """Names of the functions declared in include/rt3d.h and rt3d_nn.h."""
+    names = set()
+    for path in (paths or HEADERS):
+        src = open(path).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(rt3d_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def last_error() -> str:
@@ -159,6 +180,7 @@ def _bc(bc, keep):
             keep.append(val)
             setattr(s, fval, 0.0)
             setattr(s, fptr, _ptr(val))
+    s.I_irr = float(bc.get("I_irr", 0.0))
     return s
 
 
@@ -172,7 +194,8 @@ def _stream_handle(stream):
 
 # ------------------------------------------------------------- the C ABI
 def grid_create(n, ntheta: int, nphi: int, interp: int = LINEAR, precision: int = FP64,
-                stream=None, geometry: int = CARTESIAN_PERIODIC_XY, accel: int = ACCEL_KRYLOV):
+                stream=None, geometry: int = CARTESIAN_PERIODIC_XY, accel: int = ACCEL_KRYLOV,
+                r_in: float = 1.0, r_out: float = 1.3):
     lib = load()
     if np.isscalar(n):
         n = (int(n),) * 3
@@ -183,6 +206,7 @@ def grid_create(n, ntheta: int, nphi: int, interp: int = LINEAR, precision: int 
     d.interp, d.precision, d.nlambda = int(interp), int(precision), 1
     d.cuda_stream = _stream_handle(stream)
     d.accel = int(accel)
+    d.r_in, d.r_out = float(r_in), float(r_out)
     h = _vp()
     _check(lib.rt3d_grid_create(ctypes.byref(d), ctypes.byref(h)))
     return h
@@ -207,6 +231,21 @@ def grid_template(h, angle: int):
     ln = np.zeros(K.value, dtype=np.float64)
     _check(lib.rt3d_grid_template(h, angle, ctypes.byref(K), vox.ctypes.data, ln.ctypes.data))
     return vox, ln
+
+
+def grid_sph_ray(h, angle: int, index: int, cap: int = 4096):
+    """(vox, len, launching voxel, boundary kind) of one cached spherical ray,
+    or None past the last ray of the angle."""
+    lib = load()
+    K = _c_int(cap)
+    vox = np.zeros(cap, dtype=np.int32)
+    ln = np.zeros(cap)
+    launch, kind = _c_int(), _c_int()
+    st = lib.rt3d_grid_sph_ray(h, angle, index, ctypes.byref(K), vox.ctypes.data, ln.ctypes.data,
+                               ctypes.byref(launch), ctypes.byref(kind))
+    if st != OK:
+        return None
+    return vox[:K.value].copy(), ln[:K.value].copy(), launch.value, kind.value
 
 
 def formal_solution(h, chi, S, bc=None, J_out=None, lstar_out=None):
@@ -262,17 +301,41 @@ def solve(h, chi, eps, B, bc, J_inout, tol: float = 1e-8, max_iter: int = 2000,
     return out
 
 
+def solve_batched(h, chi, eps, B, bc, J_inout, tol: float = 1e-8, max_iter: int = 4000,
+                  raise_on_nonconv: bool = True) -> dict:
+    """n_lambda problems on one grid: arrays are (n_lambda, nz, ny, nx); bc face
+    arrays, when given, (n_lambda, ny, nx)."""
+    keep = []
+    b = _bc(bc, keep)
+    nl = int(J_inout.shape[0])
+    st = BatchStats()
+    status = np.zeros(nl, dtype=np.int32)
+    rc = load().rt3d_solve_batched(h, nl, _ptr(chi), _ptr(eps), _ptr(B),
+                                   ctypes.byref(b) if b else None, _ptr(J_inout), tol, max_iter,
+                                   status.ctypes.data, ctypes.byref(st))
+    out = st.as_dict()
+    out["status"] = rc
+    out["per_lambda"] = status
+    if rc != OK and (raise_on_nonconv or rc != ENOTCONVERGED):
+        raise RT3DError(rc, last_error())
+    return out
+
+
 class Grid:
     """Owning wrapper of an rt3d_grid handle."""
 
     def __init__(self, n, ntheta, nphi, interp=LINEAR, precision=FP64, stream=None,
-                 accel=ACCEL_KRYLOV):
+                 accel=ACCEL_KRYLOV, geometry=CARTESIAN_PERIODIC_XY, r_in=1.0, r_out=1.3):
         if np.isscalar(n):
             n = (int(n),) * 3
         self.n = tuple(int(v) for v in n)
         self.shape = (self.n[2], self.n[1], self.n[0])
         self.N = self.n[0] * self.n[1] * self.n[2]
-        self.handle = grid_create(n, ntheta, nphi, interp, precision, stream, accel=accel)
+        self.handle = grid_create(n, ntheta, nphi, interp, precision, stream, geometry=geometry,
+                                  accel=accel, r_in=r_in, r_out=r_out)
+
+    def sph_ray(self, angle, index, cap=4096):
+        return grid_sph_ray(self.handle, angle, index, cap)
 
     def close(self):
         if self.handle:
@@ -309,3 +372,6 @@ class Grid:
 
     def solve(self, chi, eps, B, bc, J, tol=1e-8, max_iter=2000, raise_on_nonconv=True):
         return solve(self.handle, chi, eps, B, bc, J, tol, max_iter, raise_on_nonconv)
+
+    def solve_batched(self, chi, eps, B, bc, J, tol=1e-8, max_iter=4000, raise_on_nonconv=True):
+        return solve_batched(self.handle, chi, eps, B, bc, J, tol, max_iter, raise_on_nonconv)

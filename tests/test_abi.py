@@ -30,6 +30,7 @@ def test_library_exports_every_declared_symbol(lib):
     ((3, 8, 8), 4, 4, 0, 0),        # nx < 4
     ((8, 8, 0), 4, 4, 0, 0),        # nz < 1
     ((2048, 8, 8), 4, 4, 0, 0),     # nx too large
+    ((2047, 2047, 200), 4, 4, 0, 0),  # replicated arrays beyond 2^31 elements
     ((8, 8, 8), 0, 4, 0, 0),        # no angles
     ((8, 8, 8), 4, 4, 7, 0),        # bad interpolation
     ((8, 8, 8), 4, 4, 0, 9),        # bad precision
