@@ -289,7 +289,7 @@ def run_ours(args):
         "fs_kernel_segments_per_s": fs_rate,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops,
-                     "traffic": None, "kernel": "fs_kernel<float, parabolic>",
+                     "traffic": None, "kernel": "fs_fast_kernel<parabolic>",
                      "peak_source": f"{SMS} SMs x {LANES} FP32 lanes x {sm_max:.0f} MHz "
                                     f"(sm_max_mhz, {peak_kind})",
                      "ops_per_segment": OPS_PER_SEGMENT},

@@ -130,7 +130,8 @@ __global__ void os_prep_kernel(int nx, int ny, int nz, const double *L, const do
 
 // r = Jfs - J (+ extra); dJ0 = r / diag; resets the sweep state.
 __global__ void os_init_kernel(int n, const double *Jfs, const double *J, const double *extra,
-                               const double *inv_diag, double *r, double *dJ0, OsState *st) {
+                               const double *inv_diag, double *r, double *dJ0, float *dJ0_32,
+                               OsState *st) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid == 0) {
         st->done = 0;
@@ -145,7 +146,9 @@ __global__ void os_init_kernel(int n, const double *Jfs, const double *J, const 
         if (J) rv -= J[v];
         if (extra) rv += extra[v];
         r[v] = rv;
-        dJ0[v] = rv * inv_diag[v];
+        const double d0 = rv * inv_diag[v];
+        dJ0[v] = d0;
+        if (dJ0_32) dJ0_32[v] = (float)d0;
     }
 }
 
@@ -154,7 +157,9 @@ __global__ void __launch_bounds__(256) os_sweep_kernel(int nx, int ny, int nz, c
                                                        const double *__restrict__ inv_diag,
                                                        const double *__restrict__ r,
                                                        const double *__restrict__ src,
-                                                       double *__restrict__ dst, int m, double tol,
+                                                       double *__restrict__ dst,
+                                                       const float *__restrict__ src32,
+                                                       float *__restrict__ dst32, int m, double tol,
                                                        OsState *st, Periodic per) {
     if (st->done) return;
     if (m >= 2) {
@@ -181,10 +186,14 @@ __global__ void __launch_bounds__(256) os_sweep_kernel(int nx, int ny, int nz, c
             ++plane;
             const long long u = nb_index(x, y, z, d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1, nx, ny, nz, per);
             if (u < 0) continue;
-            acc += coef * (A)src[u];
+            // FP32 coefficients multiply an FP32 copy of dJ (no FP64 conversion
+            // per neighbour); FP64 coefficients the FP64 dJ
+            if constexpr (sizeof(A) == 4) acc += coef * src32[u];
+            else acc += coef * (A)src[u];
         }
         const double nv = (r[v] + (double)acc) * inv_diag[v];
         dst[v] = nv;
+        if constexpr (sizeof(A) == 4) dst32[v] = (float)nv;
         dmax = fmax(dmax, fabs(nv - src[v]));
         jmax = fmax(jmax, fabs(nv));
     }
@@ -296,27 +305,32 @@ cudaError_t launch_os_prep(int nx, int ny, int nz, const double *lstar, const do
 }
 
 cudaError_t launch_os_init(int n, const double *Jfs, const double *J, const double *extra,
-                           const double *inv_diag, double *r, double *dJ0, OsState *st,
-                           cudaStream_t s) {
+                           const double *inv_diag, double *r, double *dJ0, float *dJ0_32,
+                           OsState *st, cudaStream_t s) {
     int g = grid_for(n, 256);
     if (g < 2) g = 2;  // >= 260 threads to reset the sweep maxima
-    os_init_kernel<<<g, 256, 0, s>>>(n, Jfs, J, extra, inv_diag, r, dJ0, st);
+    os_init_kernel<<<g, 256, 0, s>>>(n, Jfs, J, extra, inv_diag, r, dJ0, dJ0_32, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_os_sweep(int nx, int ny, int nz, const void *a, bool a64,
-                            const double *inv_diag, const double *r, double *const *buf, int m,
-                            double tol, OsState *st, cudaStream_t s, Periodic per) {
-    // buf is a host array of the two device ping-pong buffers
+                            const double *inv_diag, const double *r, double *const *buf,
+                            float *const *buf32, int m, double tol, OsState *st, cudaStream_t s,
+                            Periodic per) {
+    // buf, buf32: host arrays of the two device ping-pong buffers (FP64, FP32 copy)
     const long long N = (long long)nx * ny * nz;
     const double *src = buf[(m - 1) & 1];
     double *dst = buf[m & 1];
+    const float *src32 = buf32 ? buf32[(m - 1) & 1] : nullptr;
+    float *dst32 = buf32 ? buf32[m & 1] : nullptr;
     if (a64)
         os_sweep_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(
-            nx, ny, nz, static_cast<const double *>(a), inv_diag, r, src, dst, m, tol, st, per);
+            nx, ny, nz, static_cast<const double *>(a), inv_diag, r, src, dst, src32, dst32, m, tol,
+            st, per);
     else
         os_sweep_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(
-            nx, ny, nz, static_cast<const float *>(a), inv_diag, r, src, dst, m, tol, st, per);
+            nx, ny, nz, static_cast<const float *>(a), inv_diag, r, src, dst, src32, dst32, m, tol,
+            st, per);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,7 @@ struct rt3d_grid {
     double *top = nullptr, *bot = nullptr, *tmp = nullptr, *delta = nullptr, *r64 = nullptr;
     double *chi_ref = nullptr, *eps_ref = nullptr;
     double **dJ_dev = nullptr;  // device copy of {dJ[0], dJ[1]}
+    float *dJ32[2] = {nullptr, nullptr};  // FP32 copies for the mixed-mode stencil
     void *chiS32 = nullptr, *chiS64 = nullptr;  // [4N] replicated 2 x 2 in x, y
     double *Jrep = nullptr;                      // [4N] fast-path accumulation
     void *a = nullptr;  // [26][N] OS off-diagonals (f64 in FP64 mode, f32 otherwise)
@@ -122,6 +123,7 @@ struct rt3d_grid {
     int bl_cap = 0;
     double *bchi = nullptr, *beps = nullptr, *bB = nullptr, *bJ = nullptr, *br = nullptr;
     double *bbuf0 = nullptr, *bbuf1 = nullptr, *binv = nullptr, *bJrep = nullptr;
+    float *bb32_0 = nullptr, *bb32_1 = nullptr;
     double *btop = nullptr, *bbot = nullptr;
     float2 *bchiS = nullptr;
     float *ba = nullptr;
@@ -304,10 +306,11 @@ rt3d_status read_scalar_d(rt3d_grid *g, size_t off, double *out) {
 // Leaves the result in g->dJ[count & 1]; the count stays on the device.
 rt3d_status os_solve_dev(rt3d_grid *g, const double *Jfs, const double *J, const double *extra,
                          int max_sweeps, double tol) {
-    CK(launch_os_init((int)g->N, Jfs, J, extra, g->inv_diag, g->r, g->dJ[0], g->st, g->stream));
+    CK(launch_os_init((int)g->N, Jfs, J, extra, g->inv_diag, g->r, g->dJ[0],
+                      g->a64 ? nullptr : g->dJ32[0], g->st, g->stream));
     for (int m = 1; m <= max_sweeps; ++m)
-        CK(launch_os_sweep(g->nx, g->ny, g->nz, g->a, g->a64, g->inv_diag, g->r, g->dJ, m, tol,
-                           g->st, g->stream, g->per));
+        CK(launch_os_sweep(g->nx, g->ny, g->nz, g->a, g->a64, g->inv_diag, g->r, g->dJ,
+                           g->a64 ? nullptr : g->dJ32, m, tol, g->st, g->stream, g->per));
     CK(launch_os_finish(max_sweeps, tol, g->st, g->stream));
     g->launches += max_sweeps + 2;
     return RT3D_OK;
@@ -328,6 +331,8 @@ rt3d_status alloc_work(rt3d_grid *g) {
     TRY(g->alloc(&g->r, N));
     TRY(g->alloc(&g->dJ[0], N));
     TRY(g->alloc(&g->dJ[1], N));
+    TRY(g->alloc(&g->dJ32[0], N));
+    TRY(g->alloc(&g->dJ32[1], N));
     TRY(g->alloc(&g->inv_diag, N));
     TRY(g->alloc(&g->tmp, N));
     TRY(g->alloc(&g->delta, N));
@@ -948,6 +953,8 @@ rt3d_status batch_setup(rt3d_grid *g, int nl) {
     TRY(g->alloc(&g->br, L * N));
     TRY(g->alloc(&g->bbuf0, L * N));
     TRY(g->alloc(&g->bbuf1, L * N));
+    TRY(g->alloc(&g->bb32_0, L * N));
+    TRY(g->alloc(&g->bb32_1, L * N));
     TRY(g->alloc(&g->binv, L * N));
     TRY(g->alloc(&g->bJrep, 4 * L * N));
     TRY(g->alloc(&g->bchiS, 4 * L * N));
@@ -1366,8 +1373,8 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     cudaGraphExec_t exec = nullptr;
     CK(cudaStreamBeginCapture(g->bstream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = launch_batch_iteration(bp, nl, g->bJ, g->beps, g->bB, g->ba, g->binv, g->br,
-                                            g->bbuf0, g->bbuf1, kBatchSweeps, 1e-3, switch_tol,
-                                            iter_cap, g->parab, g->bstream);
+                                            g->bbuf0, g->bbuf1, g->bb32_0, g->bb32_1, kBatchSweeps,
+                                            1e-3, switch_tol, iter_cap, g->parab, g->bstream);
     cudaError_t ce = cudaStreamEndCapture(g->bstream, &graph);
     if (le != cudaSuccess || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);

@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(128) b_fs(BatchFsParams p) {
 // Jfs = fold(Jrep); r = Jfs - J; dJ0 = r / diag; Jrep zeroed for the next
 // formal solution; per-wavelength sweep state reset.
 __global__ void b_fold_init(int nx, int ny, int nz, double *Jrep, const double *J,
-                            const double *inv_diag, double *r, double *dJ0, BatchState *bs) {
+                            const double *inv_diag, double *r, double *dJ0, float *dJ0_32,
+                            BatchState *bs) {
     const int l = blockIdx.y;
     if (!bs->active[l]) return;
     const long long n = (long long)nx * ny * nz;
@@ -195,7 +196,9 @@ __global__ void b_fold_init(int nx, int ny, int nz, double *Jrep, const double *
         Jr[i3] = 0.0;
         const double rv = jfs - J[l * n + v];
         r[l * n + v] = rv;
-        dJ0[l * n + v] = rv * inv_diag[l * n + v];
+        const double d0 = rv * inv_diag[l * n + v];
+        dJ0[l * n + v] = d0;
+        dJ0_32[l * n + v] = (float)d0;
     }
 }
 
@@ -204,7 +207,8 @@ __global__ void b_fold_init(int nx, int ny, int nz, double *Jrep, const double *
 __global__ void __launch_bounds__(256) b_sweep(int nx, int ny, int nz, const float *__restrict__ a,
                                                const double *__restrict__ inv_diag,
                                                const double *__restrict__ r, double *buf0,
-                                               double *buf1, int m, double tol, BatchState *bs) {
+                                               double *buf1, float *b32_0, float *b32_1, int m,
+                                               double tol, BatchState *bs) {
     const int l = blockIdx.y;
     if (!bs->active[l] || bs->done[l]) return;
     unsigned long long *dmx = bs->dmax + l * (kBatchSweeps + 1);
@@ -221,6 +225,8 @@ __global__ void __launch_bounds__(256) b_sweep(int nx, int ny, int nz, const flo
     const long long n = (long long)nx * ny * nz;
     const double *src = ((m - 1) & 1 ? buf1 : buf0) + l * n;
     double *dst = (m & 1 ? buf1 : buf0) + l * n;
+    const float *src32 = ((m - 1) & 1 ? b32_1 : b32_0) + l * n;
+    float *dst32 = (m & 1 ? b32_1 : b32_0) + l * n;
     const float *al = a + 26 * l * n;
     const double *il = inv_diag + l * n, *rl = r + l * n;
     double dmax = 0.0, jmax = 0.0;
@@ -239,10 +245,11 @@ __global__ void __launch_bounds__(256) b_sweep(int nx, int ny, int nz, const flo
             ++plane;
             if (zz < 0 || zz >= nz) continue;
             const long long u = xs[d % 3] + (long long)nx * (ys[(d / 3) % 3] + (long long)ny * zz);
-            acc = fmaf(coef, (float)src[u], acc);
+            acc = fmaf(coef, src32[u], acc);
         }
         const double nv = (rl[v] + (double)acc) * il[v];
         dst[v] = nv;
+        dst32[v] = (float)nv;
         dmax = fmax(dmax, fabs(nv - src[v]));
         jmax = fmax(jmax, fabs(nv));
     }
@@ -323,9 +330,9 @@ int grid_x(long long n, int threads, int cap) {
 
 cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, double *J, const double *eps,
                                    const double *B, const float *a, const double *inv_diag,
-                                   double *r, double *buf0, double *buf1, int max_sweeps,
-                                   double sweep_tol, double tol, int max_iter, bool parabolic,
-                                   cudaStream_t s) {
+                                   double *r, double *buf0, double *buf1, float *b32_0,
+                                   float *b32_1, int max_sweeps, double sweep_tol, double tol,
+                                   int max_iter, bool parabolic, cudaStream_t s) {
     const long long n = (long long)p.nx * p.ny * p.nz;
     const int gx = grid_x(n, 256, 152 * 2);
     b_source<<<dim3(gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, J, eps, B, p.chiS, p.bs);
@@ -333,10 +340,10 @@ cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, double *J, co
     if (parabolic) b_fs<true><<<gfs, 128, 0, s>>>(p);
     else b_fs<false><<<gfs, 128, 0, s>>>(p);
     b_fold_init<<<dim3(gx < 2 ? 2 : gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, p.Jrep, J, inv_diag,
-                                                          r, buf0, p.bs);
+                                                          r, buf0, b32_0, p.bs);
     for (int m = 1; m <= max_sweeps; ++m)
-        b_sweep<<<dim3(gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, a, inv_diag, r, buf0, buf1, m,
-                                            sweep_tol, p.bs);
+        b_sweep<<<dim3(gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, a, inv_diag, r, buf0, buf1, b32_0,
+                                            b32_1, m, sweep_tol, p.bs);
     b_update<<<dim3(gx, nl), 256, 0, s>>>((int)n, J, buf0, buf1, max_sweeps, p.bs);
     b_retire<<<(nl + 127) / 128, 128, 0, s>>>(nl, tol, max_iter, p.bs);
     b_count_active<<<1, 32, 0, s>>>(nl, p.bs);

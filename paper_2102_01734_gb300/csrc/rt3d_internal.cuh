@@ -130,11 +130,12 @@ cudaError_t launch_os_prep(int nx, int ny, int nz, const double *lstar, const do
                            void *a, bool a64, double *inv_diag, cudaStream_t s,
                            Periodic per = {true, true, false});
 cudaError_t launch_os_init(int n, const double *Jfs, const double *J, const double *rhs_extra,
-                           const double *inv_diag, double *r, double *dJ0, OsState *st,
-                           cudaStream_t s);
+                           const double *inv_diag, double *r, double *dJ0, float *dJ0_32,
+                           OsState *st, cudaStream_t s);
+// buf32: FP32 copies of the ping-pong buffers (required when !a64)
 cudaError_t launch_os_sweep(int nx, int ny, int nz, const void *a, bool a64,
                             const double *inv_diag, const double *r, double *const *buf,
-                            int m, double tol, OsState *st, cudaStream_t s,
+                            float *const *buf32, int m, double tol, OsState *st, cudaStream_t s,
                             Periodic per = {true, true, false});
 cudaError_t launch_os_finish(int max_sweeps, double tol, OsState *st, cudaStream_t s);
 cudaError_t launch_ali_update(int n, double *J, double *const *buf, OsState *st,
@@ -183,9 +184,9 @@ struct BatchFsParams {
 // sequence, captured once into a CUDA graph.
 cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, double *J, const double *eps,
                                    const double *B, const float *a, const double *inv_diag,
-                                   double *r, double *buf0, double *buf1, int max_sweeps,
-                                   double sweep_tol, double tol, int max_iter, bool parabolic,
-                                   cudaStream_t s);
+                                   double *r, double *buf0, double *buf1, float *b32_0,
+                                   float *b32_1, int max_sweeps, double sweep_tol, double tol,
+                                   int max_iter, bool parabolic, cudaStream_t s);
 
 // ---- spherical grid (sph.cu) ----
 struct SphTables {
