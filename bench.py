@@ -285,7 +285,10 @@ def run_ours(args):
         "solves_per_s": solves_per_s,
         "solve": {"iterations": last["iterations"], "fs_fp32": last["fs_fp32"],
                   "fs_fp64": last["fs_fp64"], "residual64": last["residual64"],
-                  "est_error": last["est_error"]},
+                  "est_error": last["est_error"],
+                  "rounds": [[r64, nfs, res, est] for r64, nfs, res, est in
+                             zip(last["round_fp64"], last["round_fs"], last["round_res"],
+                                 last["round_est"])]},
         "fs_kernel_segments_per_s": fs_rate,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops,
@@ -322,6 +325,9 @@ def run_kernels(args):
     tbc = {"I_top": 0.0, "I_bottom": torch.from_numpy(bc["I_bottom"]).to(dev)}
     g = rt3d.Grid(cfg["n"], cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
     J = g.formal_solution(tchi, tB, tbc)
+    info = g.info()
+    print(json.dumps({"fs_shape": [info["fs_block"], info["fs_rays_per_thread"]],
+                      "fs_tune_ms": info["fs_tune_ms"], "segments": info["segments"]}))
     J = g.formal_solution(tchi, tB, tbc)
     J, L = g.formal_solution(tchi, tB, tbc, lstar=True)
     r = J - tB

@@ -115,6 +115,14 @@ typedef struct {
                            (CUDA events on the grid's stream) */
     double fs64_ms;     /* same for the FP64 formal-solution kernels */
     long long launches; /* kernels launched by the call */
+    int rounds;         /* Krylov solve: refinement rounds (residual, then an
+                           FGMRES cycle unless the residual certified J);
+                           the first 16 are recorded below */
+    int round_fp64[16];    /* 1 if the round's residual came from an FP64
+                              formal solution */
+    int round_fs[16];      /* formal solutions of the round's FGMRES cycle */
+    double round_res[16];  /* the round's residual max_v |r_v| / |J_v| */
+    double round_est[16];  /* estimated error at that residual (-1: none) */
 } rt3d_solve_stats;
 
 typedef struct {
@@ -123,6 +131,13 @@ typedef struct {
     long long segments;       /* ray-segment updates per formal solution:
                                  nx*ny * sum over angles of points per ray */
     long long device_bytes;   /* device memory held by the grid */
+    int fs_block;             /* threads per block of the FP32 formal solution
+                                 without Lambda* (0: not chosen yet) */
+    int fs_rays_per_thread;   /* characteristics per thread of that kernel */
+    float fs_tune_ms[6];      /* kernel time of each shape at the last
+                                 autotuning, shapes in the order
+                                 (128,1) (128,2) (64,1) (64,2) (256,1) (256,2);
+                                 0 if not tuned */
 } rt3d_grid_info;
 
 /* Creates a grid: builds the direction set (host, FP64) and traces one
@@ -137,6 +152,16 @@ rt3d_status rt3d_grid_create(const rt3d_grid_desc *desc, rt3d_grid **out);
 void rt3d_grid_destroy(rt3d_grid *grid);
 
 rt3d_status rt3d_grid_get_info(const rt3d_grid *grid, rt3d_grid_info *info);
+
+/* Ray-bundle shape of the FP32 formal solution without Lambda* (not in the
+ * paper, which maps characteristics to OpenACC gangs and vectors, Sec. 5).
+ * block = 0: autotune at the next such formal solution (the default for a new
+ * grid): every shape listed under rt3d_grid_info.fs_tune_ms is launched once
+ * on that call's input, timed with CUDA events on the grid's stream, and the
+ * fastest is kept. Otherwise block in {64, 128, 256} and rays_per_thread in
+ * {1, 2} fix the shape. The result does not depend on the shape beyond FP32
+ * reduction order. RT3D_EINVAL for other values. */
+rt3d_status rt3d_grid_set_fs_shape(rt3d_grid *grid, int block, int rays_per_thread);
 
 /* The traced characteristic of solid angle `angle` from face cell (0,0):
  * points K (in/out: capacity on input), voxel indices vox[K] and FP64 chords

@@ -90,7 +90,11 @@ struct rt3d_grid {
     double **dJ_dev = nullptr;  // device copy of {dJ[0], dJ[1]}
     float *dJ32[2] = {nullptr, nullptr};  // FP32 copies for the mixed-mode stencil
     void *chiS32 = nullptr, *chiS64 = nullptr;  // [4N] replicated 2 x 2 in x, y
-    double *Jrep = nullptr;                      // [4N] fast-path accumulation
+    // FP32 formal solution without Lambda*: replicated FP64 accumulation
+    // (zero between launches) and the kernel shape chosen by fs_tune
+    double *Jrep = nullptr;  // [4N]
+    int fs_block = 0, fs_rpt = 0;  // 0: not chosen yet
+    float fs_tune_ms[6] = {};      // last tuning: time of each shape
     void *a = nullptr;  // [26][N] OS off-diagonals (f64 in FP64 mode, f32 otherwise)
     bool a64 = true;
     OsState *st = nullptr;
@@ -226,6 +230,40 @@ rt3d_status collect_events(rt3d_grid *g) {
     return RT3D_OK;
 }
 
+// Shapes of the FP32 formal-solution kernel without Lambda* that fs_tune
+// times: (threads per block, characteristics per thread).
+constexpr int kFsShapes[][2] = {{128, 1}, {128, 2}, {64, 1}, {64, 2}, {256, 1}, {256, 2}};
+constexpr int kNumFsShapes = (int)(sizeof(kFsShapes) / sizeof(kFsShapes[0]));
+
+// Autotuner of the FP32 formal solution's ray-bundle shape: times one launch
+// of every shape on the grid's current (chi, S) (CUDA events on the grid's
+// stream, after one untimed launch) and keeps the fastest. Each launch is
+// folded into g->Jfs, which the caller's launch overwrites.
+rt3d_status fs_tune(rt3d_grid *g, const FsParams &p) {
+    TRY(collect_events(g));
+    float best = 0.0f;
+    int pick = 0;
+    for (int i = -1; i < kNumFsShapes; ++i) {
+        const int c = i < 0 ? 0 : i;
+        CK(cudaEventRecord(g->ev0, g->stream));
+        CK(launch_fs_fast(p, g->parab, kFsShapes[c][0], kFsShapes[c][1], g->stream));
+        CK(cudaEventRecord(g->ev1, g->stream));
+        CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
+        g->launches += 2;
+        CK(cudaEventSynchronize(g->ev1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+        if (i >= 0) g->fs_tune_ms[i] = ms;
+        if (i >= 0 && (i == 0 || ms < best)) {
+            best = ms;
+            pick = i;
+        }
+    }
+    g->fs_block = kFsShapes[pick][0];
+    g->fs_rpt = kFsShapes[pick][1];
+    return RT3D_OK;
+}
+
 // One formal solution of the packed (chi, S) of the given precision into
 // g->Jfs (zeroed here); Lambda* into g->lstar when requested.
 rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lstar) {
@@ -267,12 +305,12 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         return RT3D_OK;
     }
     const bool fast = !fp64 && !with_lstar;
-    if (fast) CK(cudaMemsetAsync(g->Jrep, 0, sizeof(double) * 4 * g->N, g->stream));
-    else CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
+    if (fast && g->fs_block == 0) TRY(fs_tune(g, p));
+    if (!fast) CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
     if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
     TRY(collect_events(g));
     CK(cudaEventRecord(g->ev0, g->stream));
-    if (fast) CK(launch_fs_fast(p, g->parab, g->stream));
+    if (fast) CK(launch_fs_fast(p, g->parab, g->fs_block, g->fs_rpt, g->stream));
     else CK(launch_fs(p, fp64, g->parab, with_lstar, g->stream));
     CK(cudaEventRecord(g->ev1, g->stream));
     g->ev_pending = fp64 ? 1 : 0;
@@ -346,6 +384,7 @@ rt3d_status alloc_work(rt3d_grid *g) {
     TRY(g->alloc(reinterpret_cast<double2 **>(&g->chiS64), 4 * N));
     TRY(g->alloc(reinterpret_cast<float2 **>(&g->chiS32), 4 * N));
     TRY(g->alloc(&g->Jrep, 4 * N));
+    CK(cudaMemsetAsync(g->Jrep, 0, sizeof(double) * 4 * N, s));
     if (g->a64) TRY(g->alloc(reinterpret_cast<double **>(&g->a), 26 * N));
     else TRY(g->alloc(reinterpret_cast<float **>(&g->a), 26 * N));
     TRY(g->alloc(&g->st, 1));
@@ -910,6 +949,14 @@ rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p
         TRY(read_scalar_d(g, offsetof(OsState, res), &res));
         if (!(res == res)) return fail(RT3D_ENUMERIC, "NaN in the residual");
         if (fs64) s.residual64 = res;
+        const int ri = s.rounds < 16 ? s.rounds : -1;
+        ++s.rounds;
+        if (ri >= 0) {
+            s.round_fp64[ri] = fs64 ? 1 : 0;
+            s.round_res[ri] = res;
+            s.round_est[ri] = (fs64 && gain >= 0.0) ? gain * res : -1.0;
+            s.round_fs[ri] = 0;
+        }
         // gain < 0: unknown (first round, or a residual relative to J = 0)
         if (fs64 && gain >= 0.0) {
             est = gain * res;
@@ -921,6 +968,7 @@ rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p
         double achieved = 0.0;
         int steps = 0;
         TRY(fgmres(g, fphom, g->fs64, g->r64, g->delta, eta, max_iter - it, &achieved, &steps));
+        if (ri >= 0) s.round_fs[ri] = steps;
         it += steps;
         if (g->fs64) s.fs_fp64 += steps;
         else s.fs_fp32 += steps;
@@ -1021,6 +1069,23 @@ rt3d_status rt3d_grid_get_info(const rt3d_grid *g, rt3d_grid_info *info) {
     info->kmax = g->tpl.kmax;
     info->segments = g->segments;
     info->device_bytes = g->dev_bytes;
+    info->fs_block = g->fs_block;
+    info->fs_rays_per_thread = g->fs_rpt;
+    for (int i = 0; i < 6; ++i) info->fs_tune_ms[i] = g->fs_tune_ms[i];
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_grid_set_fs_shape(rt3d_grid *g, int block, int rays_per_thread) {
+    if (!g) return fail(RT3D_EINVAL, "NULL grid");
+    if (block == 0) {
+        g->fs_block = 0;
+        g->fs_rpt = 0;
+        return RT3D_OK;
+    }
+    if ((block != 64 && block != 128 && block != 256) || (rays_per_thread != 1 && rays_per_thread != 2))
+        return fail(RT3D_EINVAL, "shape (%d, %d) not available", block, rays_per_thread);
+    g->fs_block = block;
+    g->fs_rpt = rays_per_thread;
     return RT3D_OK;
 }
 

@@ -234,79 +234,168 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
     }
 }
 
+// FP32 interval functions for the formal solution without Lambda*. Same
+// quantities as interval(float); for u < 1, p(u) = e2/u^3 is a degree-5
+// polynomial fitted to the exact function (least squares in relative error
+// at 200 Chebyshev nodes of [0, 1]; FP32 Horner error 1.2e-7 relative, as
+// for the 9-term Taylor series). For u >= 1 the caller passes ru = 1/u.
+__device__ __forceinline__ IntervalF interval_fast(float u, float ru) {
+    IntervalF r;
+    if (u < 1.0f) {
+        float p = -3.569704858819023e-05f;
+        p = fmaf(p, u, 3.819821577053517e-04f);
+        p = fmaf(p, u, -2.770215505734086e-03f);
+        p = fmaf(p, u, 1.6664894297719002e-02f);
+        p = fmaf(p, u, -8.333317935466766e-02f);
+        p = fmaf(p, u, 3.333333432674408e-01f);
+        const float b = u * p;
+        const float hu = 0.5f * u;
+        const float a = fmaf(-hu, b, hu);
+        const float e0 = fmaf(-u, a, u);
+        r.E = 1.0f - e0;
+        r.a = a;
+        r.a0 = e0 - a;
+        r.d = a - b;
+    } else {
+        const float E = __expf(-u);
+        const float e0 = 1.0f - E;
+        const float a = fmaf(-e0, ru, 1.0f);
+        r.E = E;
+        r.a = a;
+        r.a0 = fmaf(-(1.0f + u), E, 1.0f) * ru;
+        r.d = fmaf(2.0f, a, -e0) * ru;
+    }
+    return r;
+}
+
+// x as an FP64 value, by moving the fields of its IEEE binary32 encoding
+// into binary64 with the exponent rebiased by 1023 - 127: exact for every
+// normal x; a zero or subnormal x becomes +-2^-127 (1 + m 2^-23), below
+// 1.2e-38 in magnitude. Infinities and NaNs are not preserved: the kernel
+// below checks the intensity at the end of each characteristic instead
+// (a non-finite value persists along the recurrence). Integer instructions
+// only, where the conversion instruction would load the FP64 pipe.
+__device__ __forceinline__ double widen_f32(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned lo = b << 29;
+    const unsigned hi = (((b >> 3) & 0x0fffffffu) + 0x38000000u) | (b & 0x80000000u);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 // FP32 formal solution without Lambda* (every iteration after the first).
-// Per point: one 16-byte broadcast load of the step record (replicated
-// offset, l/2, J weight), one integer add for the replicated address, one
-// 8-byte (chi, S) gather, the interval arithmetic, and one FP64 reduction
-// into the replicated J (folded afterwards). The last point (linear form)
-// is peeled off the loop.
-template <bool PARAB>
-__global__ void __launch_bounds__(128) fs_fast_kernel(FsParams p) {
+// A thread integrates RPT characteristics of one solid angle (face cells
+// ray, ray + blockDim.x, ...), sharing the 16-byte broadcast load of each
+// step record (replicated offset, l/2, J weight). Per point and
+// characteristic: one integer add for the replicated address, one 8-byte
+// (chi, S) gather, the interval arithmetic, and one FP64 reduction
+// (red.global.add.f64 of the widened FP32 contribution) into the replicated
+// J, folded afterwards. FP64 accumulation keeps the operator's error at the
+// level of its FP32 arithmetic (an FP32 reduction over ~10^3 contributions
+// per voxel and angle group was measured to cost the refinement a fourth
+// FP64 formal solution and 60 more FP32 ones at 129^3). The reciprocal of
+// the next interval is carried into the next step. The last point (linear
+// form) is peeled off.
+template <bool PARAB, int RPT>
+__global__ void __launch_bounds__(256) fs_fast_kernel(FsParams p) {
     const int nray = p.nx * p.ny;
-    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ray >= nray) return;
+    const int ray0 = blockIdx.x * (blockDim.x * RPT) + threadIdx.x;
+    if (ray0 >= nray) return;
     const int o = p.order[blockIdx.y];
-    const int x0 = ray % p.nx, y0 = ray / p.nx;
-    const int base = x0 + 2 * p.nx * y0;
     const int K = p.tlen[o];
     const float4 *__restrict__ rec = p.rec32 + p.toff[o];
     const float2 *__restrict__ chiS = static_cast<const float2 *>(p.chiS);
-    double *__restrict__ J = p.Jrep;
+    double *__restrict__ Jd = p.Jrep;
 
-    double I0 = 0.0;
-    if (!p.homogeneous) {
-        if (p.up[o]) I0 = p.bot_face ? p.bot_face[ray] : p.I_bot;
-        else I0 = p.top_face ? p.top_face[ray] : p.I_top;
+    int base[RPT];
+    bool live[RPT];
+    float I[RPT], hp[RPT], hc[RPT], Sp[RPT], Sc[RPT], ru[RPT];
+    int vc[RPT];
+    const float4 r = __ldg(rec);
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int ray = ray0 + j * blockDim.x;
+        live[j] = ray < nray;
+        const int rr = live[j] ? ray : ray0;
+        const int x0 = rr % p.nx, y0 = rr / p.nx;
+        base[j] = x0 + 2 * p.nx * y0;
+        double I0 = 0.0;
+        if (!p.homogeneous) {
+            if (p.up[o]) I0 = p.bot_face ? p.bot_face[rr] : p.I_bot;
+            else I0 = p.top_face ? p.top_face[rr] : p.I_top;
+        }
+        I[j] = (float)I0;
+        vc[j] = base[j] + __float_as_int(r.x);
+        const float2 cs = chiS[vc[j]];
+        hc[j] = cs.x * r.y;  // half the optical depth of the chord of the point
+        hp[j] = 0.0f;
+        Sc[j] = cs.y;
+        Sp[j] = cs.y;
+        ru[j] = __fdividef(1.0f, hc[j]);
     }
-    float I = (float)I0;
-    float4 r = __ldg(rec);
-    int vc = base + __float_as_int(r.x);
-    float2 cs = chiS[vc];
-    float hc = cs.x * r.y;  // half the optical depth of the chord of the point
     float cwc = r.z;
-    float hp = 0.0f, Sc = cs.y, Sp = cs.y;
     for (int k = 1; k < K; ++k) {
         const float4 rn = __ldg(rec + k);
-        const int vn = base + __float_as_int(rn.x);
-        const float2 cn = chiS[vn];
-        const float hn = cn.x * rn.y;
-        const float Sn = cn.y;
-        const float u = hp + hc;
-        const IntervalF f = interval(u);
-        float al = f.a0, bg = f.a, ga = 0.0f;
-        if (PARAB) {
-            const float w = hc + hn;
-            const float q = __fdividef(u, w);
-            const float fw = clamp01(2.0f - 2.0f * u) * clamp01(2.0f - 0.5f * q);
-            if (fw > 0.0f) {
-                const float sd = fw * __fdividef(u, u + w) * f.d;
-                bg = f.a + sd;
-                ga = -q * sd;
-                al = f.a0 - sd;
+        const int off = __float_as_int(rn.x);
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const int vn = base[j] + off;
+            const float2 cn = chiS[vn];
+            const float hn = cn.x * rn.y;
+            const float Sn = cn.y;
+            const float u = hp[j] + hc[j];
+            const float w = hc[j] + hn;
+            const float rw = __fdividef(1.0f, w);
+            const IntervalF f = interval_fast(u, PARAB ? ru[j] : __fdividef(1.0f, u));
+            float al = f.a0, bg = f.a, ga = 0.0f;
+            if (PARAB) {
+                const float q = u * rw;
+                const float fw = __saturatef(fmaf(-2.0f, u, 2.0f)) * __saturatef(fmaf(-0.5f, q, 2.0f));
+                if (fw > 0.0f) {
+                    const float sd = fw * __fdividef(u, u + w) * f.d;
+                    bg = f.a + sd;
+                    ga = -q * sd;
+                    al = f.a0 - sd;
+                }
             }
+            I[j] = f.E * I[j] + al * Sp[j] + bg * Sc[j] + ga * (Sn - Sc[j]);
+            if (live[j]) atomicAdd(Jd + vc[j], widen_f32(cwc * I[j]));
+            hp[j] = hc[j];
+            hc[j] = hn;
+            Sp[j] = Sc[j];
+            Sc[j] = Sn;
+            vc[j] = vn;
+            ru[j] = rw;
         }
-        I = f.E * I + al * Sp + bg * Sc + ga * (Sn - Sc);
-        atomicAdd(J + vc, (double)(cwc * I));
-        hp = hc;
-        hc = hn;
-        Sp = Sc;
-        Sc = Sn;
-        vc = vn;
         cwc = rn.z;
     }
-    const IntervalF f = interval(hp + hc);
-    I = f.E * I + f.a0 * Sp + f.a * Sc;
-    atomicAdd(J + vc, (double)(cwc * I));
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const float u = hp[j] + hc[j];
+        const IntervalF f = interval_fast(u, PARAB ? ru[j] : __fdividef(1.0f, u));
+        I[j] = f.E * I[j] + f.a0 * Sp[j] + f.a * Sc[j];
+        if (live[j]) {
+            atomicAdd(Jd + vc[j], widen_f32(cwc * I[j]));
+            if (!(fabsf(I[j]) <= 3.402823466e38f))  // non-finite: make J NaN
+                atomicAdd(Jd + vc[j], __longlong_as_double(0x7ff8000000000000LL));
+        }
+    }
 }
 
-__global__ void fold_kernel(int nx, int ny, int nz, const double *__restrict__ Jrep,
+// J[v] = sum of the four replicas of v in Jrep (FP64); Jrep zeroed for the
+// next launch.
+__global__ void fold_kernel(int nx, int ny, int nz, double *__restrict__ Jrep,
                             double *__restrict__ J) {
     const long long n = (long long)nx * ny * nz;
+    const long long dy = 2LL * nx * ny;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
          v += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
-        J[v] = (Jrep[rep_index(x, y, z, nx, ny)] + Jrep[rep_index(x + nx, y, z, nx, ny)]) +
-               (Jrep[rep_index(x, y + ny, z, nx, ny)] + Jrep[rep_index(x + nx, y + ny, z, nx, ny)]);
+        const long long i0 = rep_index(x, y, z, nx, ny);
+        J[v] = (Jrep[i0] + Jrep[i0 + nx]) + (Jrep[i0 + dy] + Jrep[i0 + dy + nx]);
+        Jrep[i0] = 0.0;
+        Jrep[i0 + nx] = 0.0;
+        Jrep[i0 + dy] = 0.0;
+        Jrep[i0 + dy + nx] = 0.0;
     }
 }
 
@@ -320,15 +409,22 @@ cudaError_t launch_t(const FsParams &p, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, cudaStream_t s) {
-    const int threads = 128;
-    dim3 grid((p.nx * p.ny + threads - 1) / threads, p.nangles);
-    if (parabolic) fs_fast_kernel<true><<<grid, threads, 0, s>>>(p);
-    else fs_fast_kernel<false><<<grid, threads, 0, s>>>(p);
+cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, int block, int rpt, cudaStream_t s) {
+    if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
+    if (rpt != 1 && rpt != 2) return cudaErrorInvalidValue;
+    const int per = block * rpt;
+    dim3 grid((p.nx * p.ny + per - 1) / per, p.nangles);
+    if (parabolic) {
+        if (rpt == 2) fs_fast_kernel<true, 2><<<grid, block, 0, s>>>(p);
+        else fs_fast_kernel<true, 1><<<grid, block, 0, s>>>(p);
+    } else {
+        if (rpt == 2) fs_fast_kernel<false, 2><<<grid, block, 0, s>>>(p);
+        else fs_fast_kernel<false, 1><<<grid, block, 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_fold(int nx, int ny, int nz, const double *Jrep, double *J, cudaStream_t s) {
+cudaError_t launch_fold(int nx, int ny, int nz, double *Jrep, double *J, cudaStream_t s) {
     const long long n = (long long)nx * ny * nz;
     long long b = (n + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;

@@ -98,10 +98,12 @@ struct TraceParams {
 // Launchers (return the launch status).
 cudaError_t launch_trace(const TraceParams &p, cudaStream_t s);
 cudaError_t launch_fs(const FsParams &p, bool fp64, bool parabolic, bool lstar, cudaStream_t s);
-// FP32 formal solution without Lambda* into p.Jrep (zeroed by the caller)
-cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, cudaStream_t s);
-// J[v] = sum of the four replicas of v in Jrep
-cudaError_t launch_fold(int nx, int ny, int nz, const double *Jrep, double *J, cudaStream_t s);
+// FP32 formal solution without Lambda* into p.Jrep (zero on entry; the fold
+// zeroes it again). block in {64, 128, 256}, rpt (characteristics per thread)
+// in {1, 2}.
+cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, int block, int rpt, cudaStream_t s);
+// J[v] = sum of the four replicas of v in Jrep; zeroes Jrep
+cudaError_t launch_fold(int nx, int ny, int nz, double *Jrep, double *J, cudaStream_t s);
 
 // ---- ALI / OS kernels (ali.cu) ----
 struct OsState {

@@ -54,10 +54,16 @@ class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", _c_int), ("fs_fp32", _c_int), ("fs_fp64", _c_int),
                 ("jacobi_sweeps", _c_int), ("rel_change", _c_double),
                 ("residual64", _c_double), ("est_error", _c_double), ("seconds", _c_double),
-                ("fs32_ms", _c_double), ("fs64_ms", _c_double), ("launches", ctypes.c_longlong)]
+                ("fs32_ms", _c_double), ("fs64_ms", _c_double), ("launches", ctypes.c_longlong),
+                ("rounds", _c_int), ("round_fp64", _c_int * 16), ("round_fs", _c_int * 16),
+                ("round_res", _c_double * 16), ("round_est", _c_double * 16)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {k: getattr(self, k) for k, _ in self._fields_}
+        k = min(self.rounds, 16)
+        for name in ("round_fp64", "round_fs", "round_res", "round_est"):
+            out[name] = list(getattr(self, name))[:k]
+        return out
 
 
 class BatchStats(ctypes.Structure):
@@ -73,7 +79,8 @@ class BatchStats(ctypes.Structure):
 
 class GridInfo(ctypes.Structure):
     _fields_ = [("nangles", _c_int), ("kmax", _c_int), ("segments", ctypes.c_longlong),
-                ("device_bytes", ctypes.c_longlong)]
+                ("device_bytes", ctypes.c_longlong), ("fs_block", _c_int),
+                ("fs_rays_per_thread", _c_int), ("fs_tune_ms", ctypes.c_float * 6)]
 
 
 class RT3DError(RuntimeError):
@@ -99,6 +106,7 @@ def load(path: str | None = None):
     lib.rt3d_grid_destroy.argtypes = [_vp]
     lib.rt3d_grid_destroy.restype = None
     lib.rt3d_grid_get_info.argtypes = [_vp, P(GridInfo)]
+    lib.rt3d_grid_set_fs_shape.argtypes = [_vp, _c_int, _c_int]
     lib.rt3d_grid_template.argtypes = [_vp, _c_int, P(_c_int), _vp, _vp]
     lib.rt3d_formal_solution.argtypes = [_vp, _vp, _vp, P(BC), _vp, _vp]
     lib.rt3d_os_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, _c_int, _c_double, P(_c_int)]
@@ -219,7 +227,14 @@ def grid_destroy(h):
 def grid_get_info(h) -> dict:
     info = GridInfo()
     _check(load().rt3d_grid_get_info(h, ctypes.byref(info)))
-    return {k: getattr(info, k) for k, _ in info._fields_}
+    out = {k: getattr(info, k) for k, _ in info._fields_}
+    out["fs_tune_ms"] = list(info.fs_tune_ms)
+    return out
+
+
+def grid_set_fs_shape(h, block: int, rays_per_thread: int) -> None:
+    """Fixes the FP32 formal solution's ray-bundle shape; (0, 0) re-tunes."""
+    _check(load().rt3d_grid_set_fs_shape(h, block, rays_per_thread))
 
 
 def grid_template(h, angle: int):
@@ -350,6 +365,9 @@ class Grid:
 
     def info(self):
         return grid_get_info(self.handle)
+
+    def set_fs_shape(self, block, rays_per_thread):
+        grid_set_fs_shape(self.handle, block, rays_per_thread)
 
     def template(self, angle):
         return grid_template(self.handle, angle)

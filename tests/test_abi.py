@@ -47,4 +47,7 @@ def test_null_arguments_are_einval(lib):
     assert lib.rt3d_formal_solution(None, None, None, None, None, None) == rt3d.EINVAL
     assert lib.rt3d_solve(None, None, None, None, None, None, 1e-8, 10, None) == rt3d.EINVAL
     st = rt3d.SolveStats()
-    assert ctypes.sizeof(st) == 4 * 4 + 6 * 8 + 8
+    # 4 ints, 6 doubles, 1 long long, rounds, 2 x 16 ints (+4 padding), 2 x 16 doubles
+    assert ctypes.sizeof(st) == 4 * 4 + 6 * 8 + 8 + 4 + 2 * 16 * 4 + 4 + 2 * 16 * 8
+    assert ctypes.sizeof(rt3d.GridInfo) == 2 * 4 + 2 * 8 + 2 * 4 + 6 * 4
+    assert lib.rt3d_grid_set_fs_shape(None, 128, 1) == rt3d.EINVAL

@@ -120,6 +120,33 @@ def test_fs_fp32_parity(rt3d, n, nth, nph, seed, parabolic):
     assert relerr(J2.cpu().numpy(), Jo) < TOL32
 
 
+SHAPES = [(128, 1), (128, 2), (64, 1), (64, 2), (256, 1), (256, 2)]
+
+
+@pytest.mark.parametrize("n,nth,nph,seed", [((17, 13, 11), 12, 16, 5), ((4, 5, 3), 2, 6, 6)])
+def test_fs_fast_every_shape(rt3d, n, nth, nph, seed):
+    """The FP32 formal solution without Lambda* in every ray-bundle shape
+    (ragged bundles; 192 angles = two FP32 accumulation groups), and the
+    autotuner's choice."""
+    chi, S, bc = _case(n, seed)
+    for parabolic in (False, True):
+        Jo = oracle.fs_cart(chi, S, nth, nph, parabolic, bc)
+        g = rt3d.Grid(n, nth, nph, int(parabolic), rt3d.FP32_FS_FP64_ALI)
+        for block, rpt in SHAPES:
+            g.set_fs_shape(block, rpt)
+            for _ in range(2):  # the fold leaves the accumulators zeroed
+                J = g.formal_solution(dev(chi), dev(S), dev_bc(bc))
+                assert relerr(J.cpu().numpy(), Jo) < TOL32, (parabolic, block, rpt)
+        g.set_fs_shape(0, 0)
+        J = g.formal_solution(dev(chi), dev(S), dev_bc(bc))
+        assert relerr(J.cpu().numpy(), Jo) < TOL32
+        info = g.info()
+        assert (info["fs_block"], info["fs_rays_per_thread"]) in SHAPES
+        assert all(t > 0 for t in info["fs_tune_ms"])
+    with pytest.raises(rt3d.RT3DError):
+        g.set_fs_shape(96, 1)
+
+
 def test_fs_thick_thin_extremes(rt3d):
     """Per-voxel dtau from 1e-7 to 3e3 (both series and closed-form branches,
     vacuum-like and opaque voxels next to each other)."""
