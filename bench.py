@@ -335,6 +335,14 @@ def run_kernels(args):
     if args.fp64_fs:
         g64 = rt3d.Grid(cfg["n"], cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, rt3d.FP64)
         g64.formal_solution(tchi, tB, tbc)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        g64.formal_solution(tchi, tB, tbc)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"fp64_fs_ms": e0.elapsed_time(e1),
+                          "note": "includes the fold and staging on the current stream"}))
     torch.cuda.synchronize()
     print("kernels done")
     return 0

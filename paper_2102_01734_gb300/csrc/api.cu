@@ -200,6 +200,7 @@ rt3d_status fs_params(rt3d_grid *g, const rt3d_bc *bc, bool fp64, bool homogeneo
     q.cw = fp64 ? (const void *)g->tpl.cw64 : (const void *)g->tpl.cw32;
     q.win = g->tpl.win;
     q.rec32 = g->tpl.rec32;
+    q.rec64 = g->tpl.rec64;
     q.Jrep = g->Jrep;
     q.chiS = fp64 ? g->chiS64 : g->chiS32;
     q.homogeneous = homogeneous ? 1 : 0;
@@ -304,13 +305,15 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         ++g->launches;
         return RT3D_OK;
     }
-    const bool fast = !fp64 && !with_lstar;
-    if (fast && g->fs_block == 0) TRY(fs_tune(g, p));
+    // without Lambda*: the replicated-accumulation kernels (J folded after)
+    const bool fast = !with_lstar;
+    if (fast && !fp64 && g->fs_block == 0) TRY(fs_tune(g, p));
     if (!fast) CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
     if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
     TRY(collect_events(g));
     CK(cudaEventRecord(g->ev0, g->stream));
-    if (fast) CK(launch_fs_fast(p, g->parab, g->fs_block, g->fs_rpt, g->stream));
+    if (fast && fp64) CK(launch_fs64_fast(p, g->parab, g->stream));
+    else if (fast) CK(launch_fs_fast(p, g->parab, g->fs_block, g->fs_rpt, g->stream));
     else CK(launch_fs(p, fp64, g->parab, with_lstar, g->stream));
     CK(cudaEventRecord(g->ev1, g->stream));
     g->ev_pending = fp64 ? 1 : 0;
@@ -646,6 +649,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     TRY(g->alloc(&t.cw32, total));
     TRY(g->alloc(&t.win, total));
     TRY(g->alloc(&t.rec32, total));
+    TRY(g->alloc(&t.rec64, total));
     double *d_dir = nullptr, *d_wt = nullptr, *d_ls = nullptr;
     int *d_cap = nullptr, *d_err = nullptr;
     TRY(g->alloc(&d_dir, 3 * nO));
@@ -679,6 +683,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     tp.cw32 = t.cw32;
     tp.win = t.win;
     tp.rec32 = t.rec32;
+    tp.rec64 = t.rec64;
     tp.layer_sum = d_ls;
     tp.err = d_err;
     CK(launch_trace(tp, s));
@@ -845,7 +850,9 @@ rt3d_status precond(rt3d_grid *g, const double *v, double *z) {
 // One FGMRES cycle (right preconditioning, classical Gram-Schmidt applied
 // twice) for A x = r from x = 0. Stops when the residual estimate falls to
 // eta |r| or after kKrylov steps. Returns the achieved reduction and the
-// number of operator applications.
+// number of operator applications. (Scaling the system by diag|J|, so that
+// the 2-norm weighs residuals relative to J, was measured to need more
+// formal solutions on the 129^3 field workload, 253 against 167.)
 rt3d_status fgmres(rt3d_grid *g, const FsParams &fphom, bool fp64, const double *r, double *x,
                    double eta, int max_steps, double *achieved, int *steps) {
     const int n = (int)g->N;
@@ -906,6 +913,13 @@ rt3d_status fgmres(rt3d_grid *g, const FsParams &fphom, bool fp64, const double 
     return RT3D_OK;
 }
 
+#ifndef RT3D_KRYLOV_ETA
+#define RT3D_KRYLOV_ETA 1e-5
+#endif
+#ifndef RT3D_KRYLOV_ETA0
+#define RT3D_KRYLOV_ETA0 RT3D_KRYLOV_ETA
+#endif
+
 // Krylov-accelerated solve with FP64 iterative refinement. Rounds: residual
 // r = J_FS(S(J)) - J (FP32 before the first converged cycle in the mixed
 // mode, FP64 afterwards), FGMRES cycle on A delta = r (A in the grid's FS
@@ -921,11 +935,12 @@ rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p
     bool conv = false;
     double gain = -1.0, est = 1.0, res = 0.0;
     int it = 0, rounds32 = 0;
-    // Reduction asked of one FGMRES cycle. An FP64 formal solution costs
-    // about 60 FP32 ones on this GPU, so every cycle is driven down to 1e-5
-    // (the FP32 operator's rounding still allows that) to keep the number of
-    // FP64 residuals of the refinement at two or three.
-    const double eta = 1e-5;
+    // Reduction asked of one FGMRES cycle (eta0 for the cycle on the FP32
+    // residual of the starting J). An FP64 formal solution costs about 40
+    // FP32 ones on this GPU, so every cycle is driven deep (the FP32
+    // operator's rounding still allows that) to keep the number of FP64
+    // residuals of the refinement at two or three.
+    const double eta = RT3D_KRYLOV_ETA, eta0 = RT3D_KRYLOV_ETA0;
     for (int round = 0; round < 60 && it < max_iter; ++round) {
         // residual of the current J (the first one also builds Lambda*)
         const bool fs64 = res64;
@@ -967,7 +982,8 @@ rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p
         }
         double achieved = 0.0;
         int steps = 0;
-        TRY(fgmres(g, fphom, g->fs64, g->r64, g->delta, eta, max_iter - it, &achieved, &steps));
+        TRY(fgmres(g, fphom, g->fs64, g->r64, g->delta, res64 ? eta : eta0, max_iter - it, &achieved,
+                   &steps));
         if (ri >= 0) s.round_fs[ri] = steps;
         it += steps;
         if (g->fs64) s.fs_fp64 += steps;

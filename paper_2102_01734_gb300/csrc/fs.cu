@@ -381,6 +381,143 @@ __global__ void __launch_bounds__(256) fs_fast_kernel(FsParams p) {
     }
 }
 
+// ---- FP64 formal solution without Lambda* (refinement residuals, FP64 mode
+// after the first iteration). The FP64 pipe is the bound, so everything that
+// can leave it does: branch tests on the high word of non-negative doubles
+// (integer compares), reciprocals seeded in FP32, widening by integer moves.
+
+// Whether x < b for a double x >= 0 (or any negative x) and a bound b whose
+// low word is zero, given the high word of b.
+__device__ __forceinline__ bool hi_below(double x, int b_hi) { return __double2hiint(x) < b_hi; }
+
+// 1/x for x > 0. Seed: x truncated to FP32 by integer moves (for x and 1/x
+// inside the FP32 normal range: exponent field 897..1148), its FP32
+// reciprocal, widened back; then one third-order Newton-Raphson step
+// r = r0 + r0 (e + e^2), e = 1 - x r0, which takes the seed's relative error
+// (< 2^-21) to below 2^-63, so the result is within an ulp or so of 1/x.
+// Outside that range (and for 0, Inf, NaN): IEEE division.
+__device__ __forceinline__ double recip64(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x);
+    if (((hi >> 20) & 0x7ffu) - 897u > 251u || (hi >> 31)) return 1.0 / x;
+    const unsigned lo = (unsigned)__double2loint(x);
+    const float xf = __uint_as_float(((hi - 0x38000000u) << 3) | (lo >> 29));
+    const double r0 = widen_f32(__frcp_rn(xf));
+    const double e = fma(-x, r0, 1.0);
+    return fma(r0, fma(e, e, e), r0);
+}
+
+// Interval functions in FP64 (as interval(double)); for u < 1/2 p(u) =
+// e2/u^3 is a degree-9 polynomial fitted to the exact function (least squares
+// in relative error at 300 Chebyshev nodes of [0, 1/2]; FP64 Horner error
+// 1.6e-16 relative, the rounding of its leading coefficient 1/3). ru = 1/u
+// for u >= 1/2 (carried from the previous step, or computed here if CARRY is
+// false).
+template <bool CARRY>
+__device__ __forceinline__ IntervalD interval64(double u, double ru) {
+    IntervalD r;
+    if (hi_below(u, 0x3FE00000)) {
+        double p = -3.4475018036590732e-09;
+        p = fma(p, u, 4.9354831016668725e-08);
+        p = fma(p, u, -5.507115670485655e-07);
+        p = fma(p, u, 5.511310234105578e-06);
+        p = fma(p, u, -4.9603140878306714e-05);
+        p = fma(p, u, 3.9682539230545495e-04);
+        p = fma(p, u, -2.777777777429071e-03);
+        p = fma(p, u, 1.6666666666652976e-02);
+        p = fma(p, u, -8.333333333333312e-02);
+        p = fma(p, u, 3.333333333333333e-01);
+        const double b = u * p;
+        const double hu = 0.5 * u;
+        const double a = fma(-hu, b, hu);
+        const double e0 = fma(-u, a, u);
+        r.E = 1.0 - e0;
+        r.a = a;
+        r.a0 = e0 - a;
+        r.d = a - b;
+    } else {
+        if (!CARRY) ru = recip64(u);
+        const double E = exp(-u);
+        const double e0 = 1.0 - E;
+        const double a = fma(-e0, ru, 1.0);
+        r.E = E;
+        r.a = a;
+        r.a0 = fma(-(1.0 + u), E, 1.0) * ru;
+        r.d = fma(2.0, a, -e0) * ru;
+    }
+    return r;
+}
+
+// One thread per characteristic; per point: the replicated offset (FP32
+// record), the FP64 (l/2, J weight) record, the (chi, S) gather, and one
+// red.global.add.f64 into the replicated J (folded afterwards). The
+// parabolic blend f = clamp(2 - 2u) clamp(2 - q/2) is taken apart on integer
+// tests: f > 0 iff u < 1 and q < 4, each factor is 1 below 1/2 (resp. 2) and
+// one FMA between.
+template <bool PARAB>
+__global__ void __launch_bounds__(128) fs64_fast_kernel(FsParams p) {
+    const int nray = p.nx * p.ny;
+    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= nray) return;
+    const int o = p.order[blockIdx.y];
+    const int K = p.tlen[o];
+    const long long t0 = p.toff[o];
+    const float4 *__restrict__ rec = p.rec32 + t0;
+    const double2 *__restrict__ rd = p.rec64 + t0;
+    const double2 *__restrict__ chiS = static_cast<const double2 *>(p.chiS);
+    double *__restrict__ J = p.Jrep;
+    const int x0 = ray % p.nx, y0 = ray / p.nx;
+    const int base = x0 + 2 * p.nx * y0;
+
+    double I = 0.0;
+    if (!p.homogeneous) {
+        if (p.up[o]) I = p.bot_face ? p.bot_face[ray] : p.I_bot;
+        else I = p.top_face ? p.top_face[ray] : p.I_top;
+    }
+    int vc = base + __float_as_int(__ldg(&rec[0].x));
+    double2 r = __ldg(rd);
+    const double2 cs = chiS[vc];
+    double hc = cs.x * r.x;  // half the optical depth of the chord of the point
+    double cwc = r.y;
+    double hp = 0.0, Sc = cs.y, Sp = cs.y;
+    double ru = PARAB ? recip64(hc) : 0.0;
+    for (int k = 1; k < K; ++k) {
+        const int vn = base + __float_as_int(__ldg(&rec[k].x));
+        const double2 rn = __ldg(rd + k);
+        const double2 cn = chiS[vn];
+        const double hn = cn.x * rn.x;
+        const double Sn = cn.y;
+        const double u = hp + hc;
+        const IntervalD f = interval64<PARAB>(u, ru);
+        double al = f.a0, bg = f.a, ga = 0.0;
+        if (PARAB) {
+            const double w = hc + hn;
+            const double rw = recip64(w);
+            const double q = u * rw;
+            if (hi_below(u, 0x3FF00000) && hi_below(q, 0x40100000)) {
+                double fw = 1.0;
+                if (!hi_below(u, 0x3FE00000)) fw = fma(-2.0, u, 2.0);
+                if (!hi_below(q, 0x40000000)) fw *= fma(-0.5, q, 2.0);
+                const double sd = fw * (u * recip64(u + w)) * f.d;
+                bg = f.a + sd;
+                ga = -q * sd;
+                al = f.a0 - sd;
+            }
+            ru = rw;
+        }
+        I = f.E * I + al * Sp + bg * Sc + ga * (Sn - Sc);
+        atomicAdd(J + vc, cwc * I);
+        hp = hc;
+        hc = hn;
+        Sp = Sc;
+        Sc = Sn;
+        vc = vn;
+        cwc = rn.y;
+    }
+    const IntervalD f = interval64<PARAB>(hp + hc, ru);
+    I = f.E * I + f.a0 * Sp + f.a * Sc;
+    atomicAdd(J + vc, cwc * I);
+}
+
 // J[v] = sum of the four replicas of v in Jrep (FP64); Jrep zeroed for the
 // next launch.
 __global__ void fold_kernel(int nx, int ny, int nz, double *__restrict__ Jrep,
@@ -421,6 +558,14 @@ cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, int block, int rpt
         if (rpt == 2) fs_fast_kernel<false, 2><<<grid, block, 0, s>>>(p);
         else fs_fast_kernel<false, 1><<<grid, block, 0, s>>>(p);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fs64_fast(const FsParams &p, bool parabolic, cudaStream_t s) {
+    const int threads = 128;
+    dim3 grid((p.nx * p.ny + threads - 1) / threads, p.nangles);
+    if (parabolic) fs64_fast_kernel<true><<<grid, threads, 0, s>>>(p);
+    else fs64_fast_kernel<false><<<grid, threads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,8 @@ struct Template {
     // [total] FP32 step record for the formal solution without Lambda*:
     // (offset in the 2x2-replicated grid as int bits, l/2, J weight, 0)
     float4 *rec32 = nullptr;
+    // [total] FP64 step record of the same: (l/2, J weight)
+    double2 *rec64 = nullptr;
 };
 
 // The packed (chi, S) arrays are replicated 2 x 2 in x and y: element
@@ -68,6 +70,7 @@ struct FsParams {
     const void *chiS;  // float2 or double2 [4N]: (chi, S), replicated 2 x 2 in x, y
     double *J;         // [N], accumulated into (zeroed by the caller)
     const float4 *rec32;  // FP32 step records (fast path)
+    const double2 *rec64; // FP64 (l/2, J weight) records (FP64 path without Lambda*)
     double *Jrep;      // [4N] replicated accumulation target of the fast path
     double *lstar;     // nullable [27][N], accumulated into
     const double *top_face;  // nullable [ny*nx]
@@ -91,6 +94,7 @@ struct TraceParams {
     float *cw32;
     uint64_t *win;
     float4 *rec32;
+    double2 *rec64;
     double *layer_sum;        // scratch [nangles][nz]
     int *err;                 // out: first error code (0 ok)
 };
@@ -102,6 +106,8 @@ cudaError_t launch_fs(const FsParams &p, bool fp64, bool parabolic, bool lstar, 
 // zeroes it again). block in {64, 128, 256}, rpt (characteristics per thread)
 // in {1, 2}.
 cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, int block, int rpt, cudaStream_t s);
+// FP64 formal solution without Lambda* into p.Jrep (zero on entry)
+cudaError_t launch_fs64_fast(const FsParams &p, bool parabolic, cudaStream_t s);
 // J[v] = sum of the four replicas of v in Jrep; zeroes Jrep
 cudaError_t launch_fold(int nx, int ny, int nz, double *Jrep, double *J, cudaStream_t s);
 

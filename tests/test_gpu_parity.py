@@ -104,6 +104,9 @@ def test_fs_fp64_parity(rt3d, n, nth, nph, seed, parabolic):
     Jo, Lo = oracle.fs_cart(chi, S, nth, nph, parabolic, bc, lstar=True)
     assert relerr(J.cpu().numpy(), Jo) < TOL64
     assert lstar_err(L.cpu().numpy(), Lo) < TOL64
+    # the formal solution without Lambda* runs a separate kernel
+    J2 = g.formal_solution(dev(chi), dev(S), dev_bc(bc))
+    assert relerr(J2.cpu().numpy(), Jo) < TOL64
 
 
 @pytest.mark.parametrize("parabolic", [False, True])
