@@ -38,6 +38,10 @@ DESCR = ("129^3 periodic box, 32x64 angles, parabolic, eps=1e-6, chi=10^(-4+6(nz
 # interval optical depth, exp, 1/(u+w), 1/w, a, a0, d, s, q, coefficients,
 # intensity update, J weight)
 OPS_PER_SEGMENT = 28
+# Jacobi sweep, mixed mode, algorithmic bytes per voxel: 26 FP32 coefficients,
+# 1/diag and r (FP64), the FP32 copy of the previous sweep (one pass; the
+# neighbours come from cache), the FP64 iterate and its FP32 copy written
+SWEEP_BYTES_F32 = 26 * 4 + 8 + 8 + 4 + 8 + 4
 SMS = 152
 LANES = 128
 
@@ -326,12 +330,29 @@ def run_kernels(args):
     g = rt3d.Grid(cfg["n"], cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
     J = g.formal_solution(tchi, tB, tbc)
     info = g.info()
-    print(json.dumps({"fs_shape": [info["fs_block"], info["fs_rays_per_thread"]],
-                      "fs_tune_ms": info["fs_tune_ms"], "segments": info["segments"]}))
+    print(json.dumps({"fs_shape": info["fs_shape"],
+                      "fs_tune": [[list(rt3d.fs_tune_shape(i)), ms]
+                                  for i, ms in enumerate(info["fs_tune_ms"])],
+                      "segments": info["segments"]}))
     J = g.formal_solution(tchi, tB, tbc)
     J, L = g.formal_solution(tchi, tB, tbc, lstar=True)
     r = J - tB
     g.os_solve(L, teps, r, max_sweeps=4, tol=0.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for sweeps in (2, 22):
+        torch.cuda.synchronize()
+        e0.record()
+        g.os_solve(L, teps, r, max_sweeps=sweeps, tol=0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if sweeps == 2:
+            base = ms
+    per = (ms - base) / 20.0
+    n = cfg["n"] ** 3
+    print(json.dumps({"os_sweep_ms": per, "os_sweep_GBps": SWEEP_BYTES_F32 * n / per / 1e6,
+                      "bytes_per_voxel": SWEEP_BYTES_F32,
+                      "note": "difference of 22- and 2-sweep OS solves over 20 sweeps"}))
     if args.fp64_fs:
         g64 = rt3d.Grid(cfg["n"], cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, rt3d.FP64)
         g64.formal_solution(tchi, tB, tbc)

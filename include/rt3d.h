@@ -125,19 +125,32 @@ typedef struct {
     double round_est[16];  /* estimated error at that residual (-1: none) */
 } rt3d_solve_stats;
 
+/* Ray-bundle shape of the FP32 formal solution without Lambda* (not in the
+ * paper, which maps characteristics to OpenACC gangs and vectors, Sec. 5). */
+typedef struct {
+    int block;            /* threads per block: 64, 128 or 256 */
+    int rays_per_thread;  /* characteristics per thread: 1 or 2 */
+    int widen;            /* FP32 contribution to FP64 for the reduction: 0 the
+                             conversion instruction, 1 integer moves, 2 both,
+                             alternating from point to point */
+    int branchless;       /* 1: the parabolic correction is evaluated without
+                             a branch (multiplied by its blend weight 0 where
+                             the linear form applies) */
+} rt3d_fs_shape;
+
+#define RT3D_FS_TUNE_SHAPES 8
+
 typedef struct {
     int nangles;              /* ntheta * nphi */
     int kmax;                 /* longest characteristic, points */
     long long segments;       /* ray-segment updates per formal solution:
                                  nx*ny * sum over angles of points per ray */
     long long device_bytes;   /* device memory held by the grid */
-    int fs_block;             /* threads per block of the FP32 formal solution
-                                 without Lambda* (0: not chosen yet) */
-    int fs_rays_per_thread;   /* characteristics per thread of that kernel */
-    float fs_tune_ms[6];      /* kernel time of each shape at the last
-                                 autotuning, shapes in the order
-                                 (128,1) (128,2) (64,1) (64,2) (256,1) (256,2);
-                                 0 if not tuned */
+    rt3d_fs_shape fs_shape;   /* ray-bundle shape of the FP32 formal solution
+                                 without Lambda* (block 0: not chosen yet) */
+    float fs_tune_ms[RT3D_FS_TUNE_SHAPES]; /* kernel time of each candidate
+                                 shape (rt3d_fs_tune_shape order) at the last
+                                 autotuning; 0 if not tuned */
 } rt3d_grid_info;
 
 /* Creates a grid: builds the direction set (host, FP64) and traces one
@@ -153,15 +166,20 @@ void rt3d_grid_destroy(rt3d_grid *grid);
 
 rt3d_status rt3d_grid_get_info(const rt3d_grid *grid, rt3d_grid_info *info);
 
-/* Ray-bundle shape of the FP32 formal solution without Lambda* (not in the
- * paper, which maps characteristics to OpenACC gangs and vectors, Sec. 5).
- * block = 0: autotune at the next such formal solution (the default for a new
- * grid): every shape listed under rt3d_grid_info.fs_tune_ms is launched once
- * on that call's input, timed with CUDA events on the grid's stream, and the
- * fastest is kept. Otherwise block in {64, 128, 256} and rays_per_thread in
- * {1, 2} fix the shape. The result does not depend on the shape beyond FP32
- * reduction order. RT3D_EINVAL for other values. */
-rt3d_status rt3d_grid_set_fs_shape(rt3d_grid *grid, int block, int rays_per_thread);
+/* Candidate i (0 <= i < RT3D_FS_TUNE_SHAPES) of the autotuner of the FP32
+ * formal solution without Lambda*. RT3D_EINVAL for another i or out = NULL. */
+rt3d_status rt3d_fs_tune_shape(int i, rt3d_fs_shape *out);
+
+/* Sets the grid's ray-bundle shape of the FP32 formal solution without
+ * Lambda*. shape = NULL: autotune at the next such formal solution (the
+ * default for a new grid): every candidate of rt3d_fs_tune_shape is launched
+ * once on that call's input, timed with CUDA events on the grid's stream,
+ * and the fastest is kept. The result does not depend on the shape beyond
+ * FP64 reduction order (both widenings are exact for normal FP32 values;
+ * integer widening maps an FP32 zero or subnormal contribution to at most
+ * 1.2e-38 in magnitude). RT3D_EINVAL for a shape outside the ranges of
+ * rt3d_fs_shape. */
+rt3d_status rt3d_grid_set_fs_shape(rt3d_grid *grid, const rt3d_fs_shape *shape);
 
 /* The traced characteristic of solid angle `angle` from face cell (0,0):
  * points K (in/out: capacity on input), voxel indices vox[K] and FP64 chords

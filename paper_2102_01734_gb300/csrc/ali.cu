@@ -4,9 +4,10 @@
 // The OS system for the correction dJ = J_new - J_old is
 //   [1 - Lambda*(1 - eps)] dJ = r,  r = J_FS - J_old,
 // a 27-point stencil periodic in x and y. os_prep folds (1 - eps) of the
-// neighbour into the 26 off-diagonal planes a[d][v] = Lambda*[d][v] (1 -
-// eps_{v+d}) (FP64, or FP32 in the mixed mode) and stores 1/diag in FP64.
-// A sweep reads the 26 planes once (the HBM stream that bounds it), the
+// neighbour into the 26 off-diagonal coefficients a_d(v) = Lambda*[d][v] (1 -
+// eps_{v+d}) (FP64, or FP32 in the mixed mode; blocks of 32 voxels with
+// their 26 planes contiguous, os_coef_index) and stores 1/diag in FP64.
+// A sweep reads the coefficients once (the HBM stream that bounds it), the
 // neighbours of dJ through L1/L2, and writes dJ^{m+1} with the two maxima
 // of the stop test. Sweeps are launched back to back; each reads the
 // previous sweep's maxima and returns at once after the stop test is met,
@@ -122,7 +123,7 @@ __global__ void os_prep_kernel(int nx, int ny, int nz, const double *L, const do
             const long long u = nb_index(x, y, z, d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1, nx, ny, nz, per);
             double val = 0.0;
             if (u >= 0) val = L[(long long)d * N + v] * (1.0 - eps[u]);
-            a[(long long)plane * N + v] = (A)val;
+            a[os_coef_index(plane, v)] = (A)val;
             ++plane;
         }
     }
@@ -152,6 +153,11 @@ __global__ void os_init_kernel(int n, const double *Jfs, const double *J, const 
     }
 }
 
+// One Jacobi sweep dst = (r + sum_d a_d src_{v+d}) / diag over all voxels
+// (os_stencil), with the stop test of the previous sweep first. The mixed
+// mode (A = float) multiplies by the FP32 copy of the previous sweep and
+// keeps the iterate, r and 1/diag in FP64; its stop test compares against
+// that copy.
 template <typename A>
 __global__ void __launch_bounds__(256) os_sweep_kernel(int nx, int ny, int nz, const A *__restrict__ a,
                                                        const double *__restrict__ inv_diag,
@@ -172,33 +178,28 @@ __global__ void __launch_bounds__(256) os_sweep_kernel(int nx, int ny, int nz, c
             return;
         }
     }
-    const long long N = (long long)nx * ny * nz;
-    double dmax = 0.0, jmax = 0.0;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
-         v += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
-        A acc = A(0);
-        int plane = 0;
-#pragma unroll
-        for (int d = 0; d < 27; ++d) {
-            if (d == 13) continue;
-            const A coef = a[(long long)plane * N + v];
-            ++plane;
-            const long long u = nb_index(x, y, z, d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1, nx, ny, nz, per);
-            if (u < 0) continue;
-            // FP32 coefficients multiply an FP32 copy of dJ (no FP64 conversion
-            // per neighbour); FP64 coefficients the FP64 dJ
-            if constexpr (sizeof(A) == 4) acc += coef * src32[u];
-            else acc += coef * (A)src[u];
-        }
+    constexpr bool f32 = sizeof(A) == 4;
+    const int N = nx * ny * nz;
+    // stop-test maxima in A (FP32 in the mixed mode: a 1e-3 relative test)
+    A dmax = A(0), jmax = A(0);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+        A acc;
+        if constexpr (f32) acc = os_stencil(a, src32, v, nx, ny, nz, per);
+        else acc = os_stencil(a, src, v, nx, ny, nz, per);
         const double nv = (r[v] + (double)acc) * inv_diag[v];
         dst[v] = nv;
-        if constexpr (sizeof(A) == 4) dst32[v] = (float)nv;
-        dmax = fmax(dmax, fabs(nv - src[v]));
-        jmax = fmax(jmax, fabs(nv));
+        if constexpr (f32) {
+            const float nf = (float)nv;
+            dst32[v] = nf;
+            dmax = fmaxf(dmax, fabsf(nf - src32[v]));
+            jmax = fmaxf(jmax, fabsf(nf));
+        } else {
+            dmax = fmax(dmax, fabs(nv - src[v]));
+            jmax = fmax(jmax, fabs(nv));
+        }
     }
-    block_max_atomic(dmax, &st->dmax[m]);
-    block_max_atomic(jmax, &st->jmax[m]);
+    block_max_atomic((double)dmax, &st->dmax[m]);
+    block_max_atomic((double)jmax, &st->jmax[m]);
 }
 
 __global__ void os_finish_kernel(int max_sweeps, double tol, OsState *st) {

@@ -93,9 +93,9 @@ struct rt3d_grid {
     // FP32 formal solution without Lambda*: replicated FP64 accumulation
     // (zero between launches) and the kernel shape chosen by fs_tune
     double *Jrep = nullptr;  // [4N]
-    int fs_block = 0, fs_rpt = 0;  // 0: not chosen yet
-    float fs_tune_ms[6] = {};      // last tuning: time of each shape
-    void *a = nullptr;  // [26][N] OS off-diagonals (f64 in FP64 mode, f32 otherwise)
+    FsShape fs_shape{0, 0, 0, 0};  // block 0: not chosen yet
+    float fs_tune_ms[RT3D_FS_TUNE_SHAPES] = {};  // last tuning: time of each shape
+    void *a = nullptr;  // 26 OS off-diagonal planes, os_coef_index layout (f64 in FP64 mode, f32 otherwise)
     bool a64 = true;
     OsState *st = nullptr;
     bool lstar_valid = false;
@@ -231,10 +231,12 @@ rt3d_status collect_events(rt3d_grid *g) {
     return RT3D_OK;
 }
 
-// Shapes of the FP32 formal-solution kernel without Lambda* that fs_tune
-// times: (threads per block, characteristics per thread).
-constexpr int kFsShapes[][2] = {{128, 1}, {128, 2}, {64, 1}, {64, 2}, {256, 1}, {256, 2}};
-constexpr int kNumFsShapes = (int)(sizeof(kFsShapes) / sizeof(kFsShapes[0]));
+// Candidate shapes of the FP32 formal-solution kernel without Lambda* that
+// fs_tune times: (threads per block, characteristics per thread, widening,
+// branchless parabolic correction).
+constexpr FsShape kFsShapes[RT3D_FS_TUNE_SHAPES] = {
+    {256, 1, 0, 0}, {256, 1, 1, 0}, {256, 1, 2, 0}, {256, 1, 0, 1},
+    {256, 1, 2, 1}, {128, 1, 0, 0}, {128, 2, 0, 0}, {128, 1, 2, 1}};
 
 // Autotuner of the FP32 formal solution's ray-bundle shape: times one launch
 // of every shape on the grid's current (chi, S) (CUDA events on the grid's
@@ -244,10 +246,10 @@ rt3d_status fs_tune(rt3d_grid *g, const FsParams &p) {
     TRY(collect_events(g));
     float best = 0.0f;
     int pick = 0;
-    for (int i = -1; i < kNumFsShapes; ++i) {
+    for (int i = -1; i < RT3D_FS_TUNE_SHAPES; ++i) {
         const int c = i < 0 ? 0 : i;
         CK(cudaEventRecord(g->ev0, g->stream));
-        CK(launch_fs_fast(p, g->parab, kFsShapes[c][0], kFsShapes[c][1], g->stream));
+        CK(launch_fs_fast(p, g->parab, kFsShapes[c], g->stream));
         CK(cudaEventRecord(g->ev1, g->stream));
         CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
         g->launches += 2;
@@ -260,8 +262,7 @@ rt3d_status fs_tune(rt3d_grid *g, const FsParams &p) {
             pick = i;
         }
     }
-    g->fs_block = kFsShapes[pick][0];
-    g->fs_rpt = kFsShapes[pick][1];
+    g->fs_shape = kFsShapes[pick];
     return RT3D_OK;
 }
 
@@ -307,13 +308,13 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
     }
     // without Lambda*: the replicated-accumulation kernels (J folded after)
     const bool fast = !with_lstar;
-    if (fast && !fp64 && g->fs_block == 0) TRY(fs_tune(g, p));
+    if (fast && !fp64 && g->fs_shape.block == 0) TRY(fs_tune(g, p));
     if (!fast) CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
     if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
     TRY(collect_events(g));
     CK(cudaEventRecord(g->ev0, g->stream));
     if (fast && fp64) CK(launch_fs64_fast(p, g->parab, g->stream));
-    else if (fast) CK(launch_fs_fast(p, g->parab, g->fs_block, g->fs_rpt, g->stream));
+    else if (fast) CK(launch_fs_fast(p, g->parab, g->fs_shape, g->stream));
     else CK(launch_fs(p, fp64, g->parab, with_lstar, g->stream));
     CK(cudaEventRecord(g->ev1, g->stream));
     g->ev_pending = fp64 ? 1 : 0;
@@ -388,8 +389,8 @@ rt3d_status alloc_work(rt3d_grid *g) {
     TRY(g->alloc(reinterpret_cast<float2 **>(&g->chiS32), 4 * N));
     TRY(g->alloc(&g->Jrep, 4 * N));
     CK(cudaMemsetAsync(g->Jrep, 0, sizeof(double) * 4 * N, s));
-    if (g->a64) TRY(g->alloc(reinterpret_cast<double **>(&g->a), 26 * N));
-    else TRY(g->alloc(reinterpret_cast<float **>(&g->a), 26 * N));
+    if (g->a64) TRY(g->alloc(reinterpret_cast<double **>(&g->a), os_coef_count(N)));
+    else TRY(g->alloc(reinterpret_cast<float **>(&g->a), os_coef_count(N)));
     TRY(g->alloc(&g->st, 1));
     CK(cudaMemcpyAsync(g->dJ_dev, g->dJ, sizeof(double *) * 2, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(g->st, 0, sizeof(OsState), s));
@@ -1022,7 +1023,7 @@ rt3d_status batch_setup(rt3d_grid *g, int nl) {
     TRY(g->alloc(&g->binv, L * N));
     TRY(g->alloc(&g->bJrep, 4 * L * N));
     TRY(g->alloc(&g->bchiS, 4 * L * N));
-    TRY(g->alloc(&g->ba, 26 * L * N));
+    TRY(g->alloc(&g->ba, L * os_coef_count((long long)N)));
     TRY(g->alloc(&g->btop, L * nf));
     TRY(g->alloc(&g->bbot, L * nf));
     BatchState &b = g->bsh;
@@ -1085,23 +1086,34 @@ rt3d_status rt3d_grid_get_info(const rt3d_grid *g, rt3d_grid_info *info) {
     info->kmax = g->tpl.kmax;
     info->segments = g->segments;
     info->device_bytes = g->dev_bytes;
-    info->fs_block = g->fs_block;
-    info->fs_rays_per_thread = g->fs_rpt;
-    for (int i = 0; i < 6; ++i) info->fs_tune_ms[i] = g->fs_tune_ms[i];
+    info->fs_shape.block = g->fs_shape.block;
+    info->fs_shape.rays_per_thread = g->fs_shape.rays_per_thread;
+    info->fs_shape.widen = g->fs_shape.widen;
+    info->fs_shape.branchless = g->fs_shape.branchless;
+    for (int i = 0; i < RT3D_FS_TUNE_SHAPES; ++i) info->fs_tune_ms[i] = g->fs_tune_ms[i];
     return RT3D_OK;
 }
 
-rt3d_status rt3d_grid_set_fs_shape(rt3d_grid *g, int block, int rays_per_thread) {
+rt3d_status rt3d_fs_tune_shape(int i, rt3d_fs_shape *out) {
+    if (!out || i < 0 || i >= RT3D_FS_TUNE_SHAPES) return fail(RT3D_EINVAL, "bad candidate index or NULL");
+    out->block = kFsShapes[i].block;
+    out->rays_per_thread = kFsShapes[i].rays_per_thread;
+    out->widen = kFsShapes[i].widen;
+    out->branchless = kFsShapes[i].branchless;
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_grid_set_fs_shape(rt3d_grid *g, const rt3d_fs_shape *shape) {
     if (!g) return fail(RT3D_EINVAL, "NULL grid");
-    if (block == 0) {
-        g->fs_block = 0;
-        g->fs_rpt = 0;
+    if (!shape) {
+        g->fs_shape = FsShape{0, 0, 0, 0};
         return RT3D_OK;
     }
-    if ((block != 64 && block != 128 && block != 256) || (rays_per_thread != 1 && rays_per_thread != 2))
-        return fail(RT3D_EINVAL, "shape (%d, %d) not available", block, rays_per_thread);
-    g->fs_block = block;
-    g->fs_rpt = rays_per_thread;
+    const FsShape sh{shape->block, shape->rays_per_thread, shape->widen, shape->branchless};
+    if (!fs_shape_valid(sh))
+        return fail(RT3D_EINVAL, "shape (%d, %d, %d, %d) not available", sh.block, sh.rays_per_thread,
+                    sh.widen, sh.branchless);
+    g->fs_shape = sh;
     return RT3D_OK;
 }
 
@@ -1412,7 +1424,7 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
         CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * N, s));
         CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * N, s));
         CKL(launch_fs(p, false, g->parab, true, s));
-        CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->beps + l * N, g->ba + 26 * l * N,
+        CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->beps + l * N, g->ba + l * os_coef_count((long long)N),
                            false, g->binv + l * N, s, g->per));
         ++bs.fs_lambda32;
     }

@@ -8,7 +8,7 @@
 // times rho/(1-rho), rho from the last kHist changes) is below tol, or when
 // its changes stagnate (the FP32 floor), which hands it to the FP64
 // refinement.
-#include "rt3d_internal.cuh"
+#include "fs_step.cuh"
 
 namespace rt3d {
 
@@ -46,46 +46,6 @@ __device__ __forceinline__ void bmax_atomic(double x, unsigned long long *dst) {
     __syncthreads();
 }
 
-__device__ __forceinline__ float clamp01f(float x) { return x < 0.f ? 0.f : (x > 1.f ? 1.f : x); }
-
-// Interval functions (same construction as the unbatched FP32 path).
-struct IntF {
-    float E, a0, a, d;
-};
-__device__ __forceinline__ IntF interval_f(float u) {
-    IntF r;
-    if (u < 1.0f) {
-        constexpr float c0 = 2.0f / 6.0f, c1 = -2.0f / 24.0f, c2 = 2.0f / 120.0f,
-                        c3 = -2.0f / 720.0f, c4 = 2.0f / 5040.0f, c5 = -2.0f / 40320.0f,
-                        c6 = 2.0f / 362880.0f, c7 = -2.0f / 3628800.0f, c8 = 2.0f / 39916800.0f;
-        float p = fmaf(c8, u, c7);
-        p = fmaf(p, u, c6);
-        p = fmaf(p, u, c5);
-        p = fmaf(p, u, c4);
-        p = fmaf(p, u, c3);
-        p = fmaf(p, u, c2);
-        p = fmaf(p, u, c1);
-        p = fmaf(p, u, c0);
-        const float b = u * p;
-        const float a = 0.5f * u * (1.0f - b);
-        const float e0 = u * (1.0f - a);
-        r.E = 1.0f - e0;
-        r.a = a;
-        r.a0 = e0 - a;
-        r.d = a - b;
-    } else {
-        const float E = __expf(-u);
-        const float ru = __fdividef(1.0f, u);
-        const float e0 = 1.0f - E;
-        const float a = fmaf(-e0, ru, 1.0f);
-        r.E = E;
-        r.a = a;
-        r.a0 = fmaf(-(1.0f + u), E, 1.0f) * ru;
-        r.d = fmaf(2.0f, a, -e0) * ru;
-    }
-    return r;
-}
-
 // S = (1 - eps) J + eps B into the four replicas of the packed (chi, S) of
 // every active wavelength (blockIdx.y).
 __global__ void b_source(int nx, int ny, int nz, const double *J, const double *eps,
@@ -105,8 +65,9 @@ __global__ void b_source(int nx, int ny, int nz, const double *J, const double *
 }
 
 // FP32 formal solution (no Lambda*) of wavelength blockIdx.z into its
-// replicated FP64 J; the per-point arithmetic is that of the unbatched fast
-// kernel.
+// replicated FP64 J: the per-point step of the unbatched kernel (fast_step),
+// two points per trip, the FP64 widening alternating between the
+// conversion instruction and integer moves.
 template <bool PARAB>
 __global__ void __launch_bounds__(128) b_fs(BatchFsParams p) {
     const int l = blockIdx.z;
@@ -116,8 +77,6 @@ __global__ void __launch_bounds__(128) b_fs(BatchFsParams p) {
     if (ray >= nray) return;
     const long long n4 = 4LL * nray * p.nz;
     const int o = p.order[blockIdx.y];
-    const int x0 = ray % p.nx, y0 = ray / p.nx;
-    const int base = x0 + 2 * p.nx * y0;
     const int K = p.tlen[o];
     const float4 *__restrict__ rec = p.rec32 + p.toff[o];
     const float2 *__restrict__ chiS = p.chiS + l * n4;
@@ -125,45 +84,37 @@ __global__ void __launch_bounds__(128) b_fs(BatchFsParams p) {
     double I0;
     if (p.up[o]) I0 = p.bot_face ? p.bot_face[(long long)l * nray + ray] : p.I_bot;
     else I0 = p.top_face ? p.top_face[(long long)l * nray + ray] : p.I_top;
-    float I = (float)I0;
-    float4 r = __ldg(rec);
-    int vc = base + __float_as_int(r.x);
-    float2 cs = chiS[vc];
-    float hc = cs.x * r.y;
+    RayF s;
+    s.live = true;
+    s.base = ray % p.nx + 2 * p.nx * (ray / p.nx);
+    s.I = (float)I0;
+    const float4 r = __ldg(rec);
+    s.vc = s.base + __float_as_int(r.x);
+    const float2 cs = chiS[s.vc];
+    s.hc = cs.x * r.y;
+    s.u = s.hc;
+    s.Sc = cs.y;
+    s.Sp = cs.y;
+    s.dS = 0.0f;
+    s.ru = __fdividef(1.0f, s.hc);
     float cwc = r.z;
-    float hp = 0.0f, Sc = cs.y, Sp = cs.y;
-    for (int k = 1; k < K; ++k) {
-        const float4 rn = __ldg(rec + k);
-        const int vn = base + __float_as_int(rn.x);
-        const float2 cn = chiS[vn];
-        const float hn = cn.x * rn.y;
-        const float Sn = cn.y;
-        const float u = hp + hc;
-        const IntF f = interval_f(u);
-        float al = f.a0, bg = f.a, ga = 0.0f;
-        if (PARAB) {
-            const float w = hc + hn;
-            const float q = __fdividef(u, w);
-            const float fw = clamp01f(2.0f - 2.0f * u) * clamp01f(2.0f - 0.5f * q);
-            if (fw > 0.0f) {
-                const float sd = fw * __fdividef(u, u + w) * f.d;
-                bg = f.a + sd;
-                ga = -q * sd;
-                al = f.a0 - sd;
-            }
-        }
-        I = f.E * I + al * Sp + bg * Sc + ga * (Sn - Sc);
-        atomicAdd(J + vc, (double)(cwc * I));
-        hp = hc;
-        hc = hn;
-        Sp = Sc;
-        Sc = Sn;
-        vc = vn;
-        cwc = rn.z;
+    int k = 1;
+    for (; k + 1 < K; k += 2) {
+        const float4 r1 = __ldg(rec + k), r2 = __ldg(rec + k + 1);
+        fast_step<PARAB, false, false>(s, chiS, J, r1, cwc);
+        fast_step<PARAB, true, false>(s, chiS, J, r2, r1.z);
+        cwc = r2.z;
     }
-    const IntF f = interval_f(hp + hc);
-    I = f.E * I + f.a0 * Sp + f.a * Sc;
-    atomicAdd(J + vc, (double)(cwc * I));
+    if (k < K) {
+        const float4 r1 = __ldg(rec + k);
+        fast_step<PARAB, false, false>(s, chiS, J, r1, cwc);
+        cwc = r1.z;
+    }
+    const IntervalE f = interval_fast(s.u, PARAB ? s.ru : __fdividef(1.0f, s.u));
+    s.I = fmaf(f.a, s.dS, fmaf(f.e0, s.Sp - s.I, s.I));
+    atomicAdd(J + s.vc, (double)(cwc * s.I));
+    if (!(fabsf(s.I) <= 3.402823466e38f))  // non-finite: make J NaN
+        atomicAdd(J + s.vc, __longlong_as_double(0x7ff8000000000000LL));
 }
 
 // Jfs = fold(Jrep); r = Jfs - J; dJ0 = r / diag; Jrep zeroed for the next
@@ -223,34 +174,19 @@ __global__ void __launch_bounds__(256) b_sweep(int nx, int ny, int nz, const flo
         }
     }
     const long long n = (long long)nx * ny * nz;
-    const double *src = ((m - 1) & 1 ? buf1 : buf0) + l * n;
     double *dst = (m & 1 ? buf1 : buf0) + l * n;
     const float *src32 = ((m - 1) & 1 ? b32_1 : b32_0) + l * n;
     float *dst32 = (m & 1 ? b32_1 : b32_0) + l * n;
-    const float *al = a + 26 * l * n;
+    const float *al = a + l * os_coef_count(n);
     const double *il = inv_diag + l * n, *rl = r + l * n;
     double dmax = 0.0, jmax = 0.0;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
-        const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-        const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
-        float acc = 0.0f;
-        int plane = 0;
-#pragma unroll
-        for (int d = 0; d < 27; ++d) {
-            if (d == 13) continue;
-            const int zz = z + d / 9 - 1;
-            const float coef = al[(long long)plane * n + v];
-            ++plane;
-            if (zz < 0 || zz >= nz) continue;
-            const long long u = xs[d % 3] + (long long)nx * (ys[(d / 3) % 3] + (long long)ny * zz);
-            acc = fmaf(coef, src32[u], acc);
-        }
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < (int)n; v += gridDim.x * blockDim.x) {
+        const float acc = os_stencil(al, src32, v, nx, ny, nz, Periodic{true, true, false});
         const double nv = (rl[v] + (double)acc) * il[v];
         dst[v] = nv;
-        dst32[v] = (float)nv;
-        dmax = fmax(dmax, fabs(nv - src[v]));
+        const float nf = (float)nv;
+        dst32[v] = nf;
+        dmax = fmax(dmax, (double)fabsf(nf - src32[v]));
         jmax = fmax(jmax, fabs(nv));
     }
     bmax_atomic(dmax, &dmx[m]);

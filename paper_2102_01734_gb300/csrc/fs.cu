@@ -29,9 +29,12 @@
 // interval non-negative (the OS matrix stays diagonally dominant),
 // and I_k = E I_{k-1} + alpha S_{k-1} + (beta+gamma) S_k + gamma (S_{k+1} - S_k)
 // so that large |gamma| (short next interval) multiplies a difference instead
-// of cancelling between two products. The last point of a characteristic is
+// of cancelling between two products. The kernels without Lambda* use the
+// same update in difference form, I_k = I_{k-1} + e0 (S_{k-1} - I_{k-1}) +
+// a (S_k - S_{k-1}) + f s d ((S_k - S_{k-1}) - q (S_{k+1} - S_k)), which
+// needs neither E nor a0. The last point of a characteristic is
 // linear; the entry point has S_{-1} = S_0 and chi_{-1} l_{-1} = 0.
-#include "rt3d_internal.cuh"
+#include "fs_step.cuh"
 
 namespace rt3d {
 
@@ -234,68 +237,26 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
     }
 }
 
-// FP32 interval functions for the formal solution without Lambda*. Same
-// quantities as interval(float); for u < 1, p(u) = e2/u^3 is a degree-5
-// polynomial fitted to the exact function (least squares in relative error
-// at 200 Chebyshev nodes of [0, 1]; FP32 Horner error 1.2e-7 relative, as
-// for the 9-term Taylor series). For u >= 1 the caller passes ru = 1/u.
-__device__ __forceinline__ IntervalF interval_fast(float u, float ru) {
-    IntervalF r;
-    if (u < 1.0f) {
-        float p = -3.569704858819023e-05f;
-        p = fmaf(p, u, 3.819821577053517e-04f);
-        p = fmaf(p, u, -2.770215505734086e-03f);
-        p = fmaf(p, u, 1.6664894297719002e-02f);
-        p = fmaf(p, u, -8.333317935466766e-02f);
-        p = fmaf(p, u, 3.333333432674408e-01f);
-        const float b = u * p;
-        const float hu = 0.5f * u;
-        const float a = fmaf(-hu, b, hu);
-        const float e0 = fmaf(-u, a, u);
-        r.E = 1.0f - e0;
-        r.a = a;
-        r.a0 = e0 - a;
-        r.d = a - b;
-    } else {
-        const float E = __expf(-u);
-        const float e0 = 1.0f - E;
-        const float a = fmaf(-e0, ru, 1.0f);
-        r.E = E;
-        r.a = a;
-        r.a0 = fmaf(-(1.0f + u), E, 1.0f) * ru;
-        r.d = fmaf(2.0f, a, -e0) * ru;
-    }
-    return r;
-}
-
-// x as an FP64 value, by moving the fields of its IEEE binary32 encoding
-// into binary64 with the exponent rebiased by 1023 - 127: exact for every
-// normal x; a zero or subnormal x becomes +-2^-127 (1 + m 2^-23), below
-// 1.2e-38 in magnitude. Infinities and NaNs are not preserved: the kernel
-// below checks the intensity at the end of each characteristic instead
-// (a non-finite value persists along the recurrence). Integer instructions
-// only, where the conversion instruction would load the FP64 pipe.
-__device__ __forceinline__ double widen_f32(float x) {
-    const unsigned b = __float_as_uint(x);
-    const unsigned lo = b << 29;
-    const unsigned hi = (((b >> 3) & 0x0fffffffu) + 0x38000000u) | (b & 0x80000000u);
-    return __hiloint2double((int)hi, (int)lo);
-}
-
 // FP32 formal solution without Lambda* (every iteration after the first).
 // A thread integrates RPT characteristics of one solid angle (face cells
 // ray, ray + blockDim.x, ...), sharing the 16-byte broadcast load of each
 // step record (replicated offset, l/2, J weight). Per point and
 // characteristic: one integer add for the replicated address, one 8-byte
 // (chi, S) gather, the interval arithmetic, and one FP64 reduction
-// (red.global.add.f64 of the widened FP32 contribution) into the replicated
-// J, folded afterwards. FP64 accumulation keeps the operator's error at the
+// (red.global.add.f64) into the replicated J, folded afterwards; the FP32
+// contribution is widened by integer moves, by the conversion instruction
+// (which runs on the FP64 pipe), or alternately by both (the autotuner
+// picks, see fast_step and fs_fast_kernel). FP64 accumulation keeps the operator's error at the
 // level of its FP32 arithmetic (an FP32 reduction over ~10^3 contributions
 // per voxel and angle group was measured to cost the refinement a fourth
 // FP64 formal solution and 60 more FP32 ones at 129^3). The reciprocal of
 // the next interval is carried into the next step. The last point (linear
-// form) is peeled off.
-template <bool PARAB, int RPT>
+// form) is peeled off; the loop takes two points per trip so that the
+// carried values rotate through registers without moves.
+// CONV: how FP32 contributions become FP64 for the reduction: 0 the
+// conversion instruction (FP64 pipe), 1 integer moves, 2 alternating between
+// the two from point to point (both pipes half loaded).
+template <bool PARAB, int RPT, int CONV, bool BRANCHLESS>
 __global__ void __launch_bounds__(256) fs_fast_kernel(FsParams p) {
     const int nray = p.nx * p.ny;
     const int ray0 = blockIdx.x * (blockDim.x * RPT) + threadIdx.x;
@@ -305,78 +266,59 @@ __global__ void __launch_bounds__(256) fs_fast_kernel(FsParams p) {
     const float4 *__restrict__ rec = p.rec32 + p.toff[o];
     const float2 *__restrict__ chiS = static_cast<const float2 *>(p.chiS);
     double *__restrict__ Jd = p.Jrep;
+    constexpr bool W0 = CONV == 1, W1 = CONV >= 1;
 
-    int base[RPT];
-    bool live[RPT];
-    float I[RPT], hp[RPT], hc[RPT], Sp[RPT], Sc[RPT], ru[RPT];
-    int vc[RPT];
+    RayF ray[RPT];
     const float4 r = __ldg(rec);
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
-        const int ray = ray0 + j * blockDim.x;
-        live[j] = ray < nray;
-        const int rr = live[j] ? ray : ray0;
+        RayF &s = ray[j];
+        const int rj = ray0 + j * blockDim.x;
+        s.live = rj < nray;
+        const int rr = s.live ? rj : ray0;
         const int x0 = rr % p.nx, y0 = rr / p.nx;
-        base[j] = x0 + 2 * p.nx * y0;
+        s.base = x0 + 2 * p.nx * y0;
         double I0 = 0.0;
         if (!p.homogeneous) {
             if (p.up[o]) I0 = p.bot_face ? p.bot_face[rr] : p.I_bot;
             else I0 = p.top_face ? p.top_face[rr] : p.I_top;
         }
-        I[j] = (float)I0;
-        vc[j] = base[j] + __float_as_int(r.x);
-        const float2 cs = chiS[vc[j]];
-        hc[j] = cs.x * r.y;  // half the optical depth of the chord of the point
-        hp[j] = 0.0f;
-        Sc[j] = cs.y;
-        Sp[j] = cs.y;
-        ru[j] = __fdividef(1.0f, hc[j]);
+        s.I = (float)I0;
+        s.vc = s.base + __float_as_int(r.x);
+        const float2 cs = chiS[s.vc];
+        s.hc = cs.x * r.y;  // half the optical depth of the chord of the point
+        s.u = s.hc;         // the entry interval: chi_{-1} l_{-1} = 0
+        s.Sc = cs.y;
+        s.Sp = cs.y;        // S_{-1} = S_0
+        s.dS = 0.0f;
+        s.ru = __fdividef(1.0f, s.hc);
     }
     float cwc = r.z;
-    for (int k = 1; k < K; ++k) {
-        const float4 rn = __ldg(rec + k);
-        const int off = __float_as_int(rn.x);
+    int k = 1;
+    // two points per trip: the carried values rotate through registers
+    for (; k + 1 < K; k += 2) {
+        const float4 r1 = __ldg(rec + k), r2 = __ldg(rec + k + 1);
 #pragma unroll
-        for (int j = 0; j < RPT; ++j) {
-            const int vn = base[j] + off;
-            const float2 cn = chiS[vn];
-            const float hn = cn.x * rn.y;
-            const float Sn = cn.y;
-            const float u = hp[j] + hc[j];
-            const float w = hc[j] + hn;
-            const float rw = __fdividef(1.0f, w);
-            const IntervalF f = interval_fast(u, PARAB ? ru[j] : __fdividef(1.0f, u));
-            float al = f.a0, bg = f.a, ga = 0.0f;
-            if (PARAB) {
-                const float q = u * rw;
-                const float fw = __saturatef(fmaf(-2.0f, u, 2.0f)) * __saturatef(fmaf(-0.5f, q, 2.0f));
-                if (fw > 0.0f) {
-                    const float sd = fw * __fdividef(u, u + w) * f.d;
-                    bg = f.a + sd;
-                    ga = -q * sd;
-                    al = f.a0 - sd;
-                }
-            }
-            I[j] = f.E * I[j] + al * Sp[j] + bg * Sc[j] + ga * (Sn - Sc[j]);
-            if (live[j]) atomicAdd(Jd + vc[j], widen_f32(cwc * I[j]));
-            hp[j] = hc[j];
-            hc[j] = hn;
-            Sp[j] = Sc[j];
-            Sc[j] = Sn;
-            vc[j] = vn;
-            ru[j] = rw;
-        }
-        cwc = rn.z;
+        for (int j = 0; j < RPT; ++j) fast_step<PARAB, W0, BRANCHLESS>(ray[j], chiS, Jd, r1, cwc);
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) fast_step<PARAB, W1, BRANCHLESS>(ray[j], chiS, Jd, r2, r1.z);
+        cwc = r2.z;
+    }
+    if (k < K) {
+        const float4 r1 = __ldg(rec + k);
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) fast_step<PARAB, W0, BRANCHLESS>(ray[j], chiS, Jd, r1, cwc);
+        cwc = r1.z;
     }
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
-        const float u = hp[j] + hc[j];
-        const IntervalF f = interval_fast(u, PARAB ? ru[j] : __fdividef(1.0f, u));
-        I[j] = f.E * I[j] + f.a0 * Sp[j] + f.a * Sc[j];
-        if (live[j]) {
-            atomicAdd(Jd + vc[j], widen_f32(cwc * I[j]));
-            if (!(fabsf(I[j]) <= 3.402823466e38f))  // non-finite: make J NaN
-                atomicAdd(Jd + vc[j], __longlong_as_double(0x7ff8000000000000LL));
+        RayF &s = ray[j];
+        const IntervalE f = interval_fast(s.u, PARAB ? s.ru : __fdividef(1.0f, s.u));
+        s.I = fmaf(f.a, s.dS, fmaf(f.e0, s.Sp - s.I, s.I));
+        if (s.live) {
+            atomicAdd(Jd + s.vc, to_f64<W1>(cwc * s.I));
+            if (!(fabsf(s.I) <= 3.402823466e38f))  // non-finite: make J NaN
+                atomicAdd(Jd + s.vc, __longlong_as_double(0x7ff8000000000000LL));
         }
     }
 }
@@ -411,10 +353,13 @@ __device__ __forceinline__ double recip64(double x) {
 // in relative error at 300 Chebyshev nodes of [0, 1/2]; FP64 Horner error
 // 1.6e-16 relative, the rounding of its leading coefficient 1/3). ru = 1/u
 // for u >= 1/2 (carried from the previous step, or computed here if CARRY is
-// false).
+// false). Returns e0, a, d for the update in difference form.
+struct IntervalDE {
+    double e0, a, d;
+};
 template <bool CARRY>
-__device__ __forceinline__ IntervalD interval64(double u, double ru) {
-    IntervalD r;
+__device__ __forceinline__ IntervalDE interval64(double u, double ru) {
+    IntervalDE r;
     if (hi_below(u, 0x3FE00000)) {
         double p = -3.4475018036590732e-09;
         p = fma(p, u, 4.9354831016668725e-08);
@@ -429,19 +374,15 @@ __device__ __forceinline__ IntervalD interval64(double u, double ru) {
         const double b = u * p;
         const double hu = 0.5 * u;
         const double a = fma(-hu, b, hu);
-        const double e0 = fma(-u, a, u);
-        r.E = 1.0 - e0;
+        r.e0 = fma(-u, a, u);
         r.a = a;
-        r.a0 = e0 - a;
         r.d = a - b;
     } else {
         if (!CARRY) ru = recip64(u);
-        const double E = exp(-u);
-        const double e0 = 1.0 - E;
+        const double e0 = 1.0 - exp(-u);
         const double a = fma(-e0, ru, 1.0);
-        r.E = E;
+        r.e0 = e0;
         r.a = a;
-        r.a0 = fma(-(1.0 + u), E, 1.0) * ru;
         r.d = fma(2.0, a, -e0) * ru;
     }
     return r;
@@ -478,19 +419,21 @@ __global__ void __launch_bounds__(128) fs64_fast_kernel(FsParams p) {
     const double2 cs = chiS[vc];
     double hc = cs.x * r.x;  // half the optical depth of the chord of the point
     double cwc = r.y;
-    double hp = 0.0, Sc = cs.y, Sp = cs.y;
+    double u = hc;  // the entry interval: chi_{-1} l_{-1} = 0
+    double Sc = cs.y, Sp = cs.y, dS = 0.0;  // S_{-1} = S_0
     double ru = PARAB ? recip64(hc) : 0.0;
     for (int k = 1; k < K; ++k) {
         const int vn = base + __float_as_int(__ldg(&rec[k].x));
         const double2 rn = __ldg(rd + k);
         const double2 cn = chiS[vn];
         const double hn = cn.x * rn.x;
-        const double Sn = cn.y;
-        const double u = hp + hc;
-        const IntervalD f = interval64<PARAB>(u, ru);
-        double al = f.a0, bg = f.a, ga = 0.0;
+        const double dSn = cn.y - Sc;
+        const double w = hc + hn;
+        const IntervalDE f = interval64<PARAB>(u, ru);
+        // difference form of the update (as in the FP32 kernel)
+        double In = fma(f.e0, Sp - I, I);
+        In = fma(f.a, dS, In);
         if (PARAB) {
-            const double w = hc + hn;
             const double rw = recip64(w);
             const double q = u * rw;
             if (hi_below(u, 0x3FF00000) && hi_below(q, 0x40100000)) {
@@ -498,23 +441,22 @@ __global__ void __launch_bounds__(128) fs64_fast_kernel(FsParams p) {
                 if (!hi_below(u, 0x3FE00000)) fw = fma(-2.0, u, 2.0);
                 if (!hi_below(q, 0x40000000)) fw *= fma(-0.5, q, 2.0);
                 const double sd = fw * (u * recip64(u + w)) * f.d;
-                bg = f.a + sd;
-                ga = -q * sd;
-                al = f.a0 - sd;
+                In = fma(sd, fma(-q, dSn, dS), In);
             }
             ru = rw;
         }
-        I = f.E * I + al * Sp + bg * Sc + ga * (Sn - Sc);
+        I = In;
         atomicAdd(J + vc, cwc * I);
-        hp = hc;
+        u = w;
         hc = hn;
         Sp = Sc;
-        Sc = Sn;
+        Sc = cn.y;
+        dS = dSn;
         vc = vn;
         cwc = rn.y;
     }
-    const IntervalD f = interval64<PARAB>(hp + hc, ru);
-    I = f.E * I + f.a0 * Sp + f.a * Sc;
+    const IntervalDE f = interval64<PARAB>(u, ru);
+    I = fma(f.a, dS, fma(f.e0, Sp - I, I));
     atomicAdd(J + vc, cwc * I);
 }
 
@@ -546,18 +488,38 @@ cudaError_t launch_t(const FsParams &p, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, int block, int rpt, cudaStream_t s) {
-    if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
-    if (rpt != 1 && rpt != 2) return cudaErrorInvalidValue;
-    const int per = block * rpt;
-    dim3 grid((p.nx * p.ny + per - 1) / per, p.nangles);
-    if (parabolic) {
-        if (rpt == 2) fs_fast_kernel<true, 2><<<grid, block, 0, s>>>(p);
-        else fs_fast_kernel<true, 1><<<grid, block, 0, s>>>(p);
+template <bool PARAB, int CONV, bool BL>
+void launch_fast_t(const FsParams &p, dim3 grid, int block, int rpt, cudaStream_t s) {
+    if (rpt == 2) fs_fast_kernel<PARAB, 2, CONV, BL><<<grid, block, 0, s>>>(p);
+    else fs_fast_kernel<PARAB, 1, CONV, BL><<<grid, block, 0, s>>>(p);
+}
+
+template <bool PARAB>
+void launch_fast_p(const FsParams &p, dim3 grid, const FsShape &sh, cudaStream_t s) {
+    const int b = sh.block, r = sh.rays_per_thread;
+    if (sh.branchless) {
+        if (sh.widen == 0) launch_fast_t<PARAB, 0, true>(p, grid, b, r, s);
+        else if (sh.widen == 1) launch_fast_t<PARAB, 1, true>(p, grid, b, r, s);
+        else launch_fast_t<PARAB, 2, true>(p, grid, b, r, s);
     } else {
-        if (rpt == 2) fs_fast_kernel<false, 2><<<grid, block, 0, s>>>(p);
-        else fs_fast_kernel<false, 1><<<grid, block, 0, s>>>(p);
+        if (sh.widen == 0) launch_fast_t<PARAB, 0, false>(p, grid, b, r, s);
+        else if (sh.widen == 1) launch_fast_t<PARAB, 1, false>(p, grid, b, r, s);
+        else launch_fast_t<PARAB, 2, false>(p, grid, b, r, s);
     }
+}
+
+bool fs_shape_valid(const FsShape &sh) {
+    return (sh.block == 64 || sh.block == 128 || sh.block == 256) &&
+           (sh.rays_per_thread == 1 || sh.rays_per_thread == 2) && sh.widen >= 0 && sh.widen <= 2 &&
+           (sh.branchless == 0 || sh.branchless == 1);
+}
+
+cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, const FsShape &sh, cudaStream_t s) {
+    if (!fs_shape_valid(sh)) return cudaErrorInvalidValue;
+    const int per = sh.block * sh.rays_per_thread;
+    dim3 grid((p.nx * p.ny + per - 1) / per, p.nangles);
+    if (parabolic) launch_fast_p<true>(p, grid, sh, s);
+    else launch_fast_p<false>(p, grid, sh, s);
     return cudaGetLastError();
 }
 

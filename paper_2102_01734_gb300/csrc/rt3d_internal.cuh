@@ -102,10 +102,18 @@ struct TraceParams {
 // Launchers (return the launch status).
 cudaError_t launch_trace(const TraceParams &p, cudaStream_t s);
 cudaError_t launch_fs(const FsParams &p, bool fp64, bool parabolic, bool lstar, cudaStream_t s);
+// Ray-bundle shape of the FP32 formal solution without Lambda* (the same
+// fields as the public rt3d_fs_shape).
+struct FsShape {
+    int block;            // 64, 128 or 256 threads
+    int rays_per_thread;  // 1 or 2
+    int widen;            // FP32 -> FP64: 0 conversion, 1 integer moves, 2 alternating
+    int branchless;       // 1: parabolic correction evaluated without a branch
+};
+bool fs_shape_valid(const FsShape &sh);
 // FP32 formal solution without Lambda* into p.Jrep (zero on entry; the fold
-// zeroes it again). block in {64, 128, 256}, rpt (characteristics per thread)
-// in {1, 2}.
-cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, int block, int rpt, cudaStream_t s);
+// zeroes it again).
+cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, const FsShape &sh, cudaStream_t s);
 // FP64 formal solution without Lambda* into p.Jrep (zero on entry)
 cudaError_t launch_fs64_fast(const FsParams &p, bool parabolic, cudaStream_t s);
 // J[v] = sum of the four replicas of v in Jrep; zeroes Jrep
@@ -134,6 +142,53 @@ cudaError_t launch_source(int nx, int ny, int nz, const double *J, const double 
 struct Periodic {
     bool x, y, z;
 };
+// Layout of the 26 folded OS coefficients a[plane][v]: blocks of 32
+// consecutive voxels, each holding its 26 planes contiguously, so a warp's
+// loads of one plane are one 128-byte (FP32) line at a fixed offset.
+__host__ __device__ inline long long os_coef_index(int plane, long long v) {
+    return ((v >> 5) * 26 + plane) * 32 + (v & 31);
+}
+__host__ __device__ inline long long os_coef_count(long long N) { return ((N + 31) >> 5) * 26 * 32; }
+
+#ifdef __CUDACC__
+// Coordinate of the neighbour at offset -1 / +1 along an axis of n cells:
+// wrapped on a periodic axis, else clamped to the cell itself (its
+// coefficient is zero: os_prep stores 0 for a neighbour outside the grid).
+__device__ __forceinline__ int os_nb_lo(int c, int n, bool periodic) {
+    return c > 0 ? c - 1 : (periodic ? n - 1 : c);
+}
+__device__ __forceinline__ int os_nb_hi(int c, int n, bool periodic) {
+    return c < n - 1 ? c + 1 : (periodic ? 0 : c);
+}
+
+// sum_d a_d(v) x_{v+d} over the 26 off-diagonal neighbours of voxel v:
+// 26 coefficient loads from the voxel's warp-contiguous block (immediate
+// offsets), 26 loads of x at indices built from 9 wrapped or clamped
+// coordinates (no branch, all loads independent), then the products in A.
+template <typename A, typename T>
+__device__ __forceinline__ A os_stencil(const A *__restrict__ a, const T *__restrict__ x, int v,
+                                        int nx, int ny, int nz, Periodic per) {
+    const int nxy = nx * ny;
+    const int z = v / nxy, rem = v - z * nxy, y = rem / nx, xx = rem - y * nx;
+    const int X[3] = {os_nb_lo(xx, nx, per.x), xx, os_nb_hi(xx, nx, per.x)};
+    const int Y[3] = {os_nb_lo(y, ny, per.y) * nx, y * nx, os_nb_hi(y, ny, per.y) * nx};
+    const int Z[3] = {os_nb_lo(z, nz, per.z) * nxy, z * nxy, os_nb_hi(z, nz, per.z) * nxy};
+    const A *__restrict__ ab = a + os_coef_index(0, v);
+    A c[26], xv[26];
+#pragma unroll
+    for (int p = 0; p < 26; ++p) c[p] = ab[p * 32];
+#pragma unroll
+    for (int d = 0, p = 0; d < 27; ++d) {
+        if (d == 13) continue;
+        xv[p] = (A)x[X[d % 3] + Y[(d / 3) % 3] + Z[d / 9]];
+        ++p;
+    }
+    A acc = A(0);
+#pragma unroll
+    for (int p = 0; p < 26; ++p) acc += c[p] * xv[p];
+    return acc;
+}
+#endif
 cudaError_t launch_os_prep(int nx, int ny, int nz, const double *lstar, const double *eps,
                            void *a, bool a64, double *inv_diag, cudaStream_t s,
                            Periodic per = {true, true, false});

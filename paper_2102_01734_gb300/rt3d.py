@@ -77,10 +77,21 @@ class BatchStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class FsShape(ctypes.Structure):
+    _fields_ = [("block", _c_int), ("rays_per_thread", _c_int), ("widen", _c_int),
+                ("branchless", _c_int)]
+
+    def as_tuple(self):
+        return (self.block, self.rays_per_thread, self.widen, self.branchless)
+
+
+FS_TUNE_SHAPES = 8
+
+
 class GridInfo(ctypes.Structure):
     _fields_ = [("nangles", _c_int), ("kmax", _c_int), ("segments", ctypes.c_longlong),
-                ("device_bytes", ctypes.c_longlong), ("fs_block", _c_int),
-                ("fs_rays_per_thread", _c_int), ("fs_tune_ms", ctypes.c_float * 6)]
+                ("device_bytes", ctypes.c_longlong), ("fs_shape", FsShape),
+                ("fs_tune_ms", ctypes.c_float * FS_TUNE_SHAPES)]
 
 
 class RT3DError(RuntimeError):
@@ -106,7 +117,8 @@ def load(path: str | None = None):
     lib.rt3d_grid_destroy.argtypes = [_vp]
     lib.rt3d_grid_destroy.restype = None
     lib.rt3d_grid_get_info.argtypes = [_vp, P(GridInfo)]
-    lib.rt3d_grid_set_fs_shape.argtypes = [_vp, _c_int, _c_int]
+    lib.rt3d_grid_set_fs_shape.argtypes = [_vp, ctypes.POINTER(FsShape)]
+    lib.rt3d_fs_tune_shape.argtypes = [_c_int, ctypes.POINTER(FsShape)]
     lib.rt3d_grid_template.argtypes = [_vp, _c_int, P(_c_int), _vp, _vp]
     lib.rt3d_formal_solution.argtypes = [_vp, _vp, _vp, P(BC), _vp, _vp]
     lib.rt3d_os_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, _c_int, _c_double, P(_c_int)]
@@ -229,12 +241,26 @@ def grid_get_info(h) -> dict:
     _check(load().rt3d_grid_get_info(h, ctypes.byref(info)))
     out = {k: getattr(info, k) for k, _ in info._fields_}
     out["fs_tune_ms"] = list(info.fs_tune_ms)
+    out["fs_shape"] = info.fs_shape.as_tuple()
     return out
 
 
-def grid_set_fs_shape(h, block: int, rays_per_thread: int) -> None:
-    """Fixes the FP32 formal solution's ray-bundle shape; (0, 0) re-tunes."""
-    _check(load().rt3d_grid_set_fs_shape(h, block, rays_per_thread))
+def fs_tune_shape(i: int) -> tuple:
+    """Candidate i of the FP32 formal solution's autotuner:
+    (block, rays_per_thread, widen, branchless)."""
+    sh = FsShape()
+    _check(load().rt3d_fs_tune_shape(i, ctypes.byref(sh)))
+    return sh.as_tuple()
+
+
+def grid_set_fs_shape(h, shape) -> None:
+    """Fixes the FP32 formal solution's ray-bundle shape
+    (block, rays_per_thread, widen, branchless); None re-tunes."""
+    if shape is None:
+        _check(load().rt3d_grid_set_fs_shape(h, None))
+    else:
+        sh = FsShape(*shape)
+        _check(load().rt3d_grid_set_fs_shape(h, ctypes.byref(sh)))
 
 
 def grid_template(h, angle: int):
@@ -366,8 +392,8 @@ class Grid:
     def info(self):
         return grid_get_info(self.handle)
 
-    def set_fs_shape(self, block, rays_per_thread):
-        grid_set_fs_shape(self.handle, block, rays_per_thread)
+    def set_fs_shape(self, shape):
+        grid_set_fs_shape(self.handle, shape)
 
     def template(self, angle):
         return grid_template(self.handle, angle)

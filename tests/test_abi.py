@@ -49,5 +49,14 @@ def test_null_arguments_are_einval(lib):
     st = rt3d.SolveStats()
     # 4 ints, 6 doubles, 1 long long, rounds, 2 x 16 ints (+4 padding), 2 x 16 doubles
     assert ctypes.sizeof(st) == 4 * 4 + 6 * 8 + 8 + 4 + 2 * 16 * 4 + 4 + 2 * 16 * 8
-    assert ctypes.sizeof(rt3d.GridInfo) == 2 * 4 + 2 * 8 + 2 * 4 + 6 * 4
-    assert lib.rt3d_grid_set_fs_shape(None, 128, 1) == rt3d.EINVAL
+    assert ctypes.sizeof(rt3d.GridInfo) == 2 * 4 + 2 * 8 + 4 * 4 + 8 * 4
+    assert lib.rt3d_grid_set_fs_shape(None, None) == rt3d.EINVAL
+
+
+def test_fs_tune_shapes_are_valid(lib):
+    shapes = [rt3d.fs_tune_shape(i) for i in range(rt3d.FS_TUNE_SHAPES)]
+    assert len(set(shapes)) == rt3d.FS_TUNE_SHAPES
+    for block, rpt, widen, bl in shapes:
+        assert block in (64, 128, 256) and rpt in (1, 2) and widen in (0, 1, 2) and bl in (0, 1)
+    with pytest.raises(rt3d.RT3DError):
+        rt3d.fs_tune_shape(rt3d.FS_TUNE_SHAPES)

@@ -123,31 +123,33 @@ def test_fs_fp32_parity(rt3d, n, nth, nph, seed, parabolic):
     assert relerr(J2.cpu().numpy(), Jo) < TOL32
 
 
-SHAPES = [(128, 1), (128, 2), (64, 1), (64, 2), (256, 1), (256, 2)]
+SHAPES = [(b, r, w, bl) for b in (64, 128, 256) for r in (1, 2) for w in (0, 1, 2) for bl in (0, 1)]
 
 
 @pytest.mark.parametrize("n,nth,nph,seed", [((17, 13, 11), 12, 16, 5), ((4, 5, 3), 2, 6, 6)])
 def test_fs_fast_every_shape(rt3d, n, nth, nph, seed):
-    """The FP32 formal solution without Lambda* in every ray-bundle shape
-    (ragged bundles; 192 angles = two FP32 accumulation groups), and the
-    autotuner's choice."""
+    """The FP32 formal solution without Lambda* in every ray-bundle shape,
+    widening and branch form (ragged bundles; odd and even point counts
+    through the two-point loop), and the autotuner's choice."""
     chi, S, bc = _case(n, seed)
     for parabolic in (False, True):
         Jo = oracle.fs_cart(chi, S, nth, nph, parabolic, bc)
         g = rt3d.Grid(n, nth, nph, int(parabolic), rt3d.FP32_FS_FP64_ALI)
-        for block, rpt in SHAPES:
-            g.set_fs_shape(block, rpt)
+        for shape in SHAPES:
+            g.set_fs_shape(shape)
             for _ in range(2):  # the fold leaves the accumulators zeroed
                 J = g.formal_solution(dev(chi), dev(S), dev_bc(bc))
-                assert relerr(J.cpu().numpy(), Jo) < TOL32, (parabolic, block, rpt)
-        g.set_fs_shape(0, 0)
+                assert relerr(J.cpu().numpy(), Jo) < TOL32, (parabolic, shape)
+        g.set_fs_shape(None)
         J = g.formal_solution(dev(chi), dev(S), dev_bc(bc))
         assert relerr(J.cpu().numpy(), Jo) < TOL32
         info = g.info()
-        assert (info["fs_block"], info["fs_rays_per_thread"]) in SHAPES
+        assert info["fs_shape"] in [rt3d.fs_tune_shape(i) for i in range(rt3d.FS_TUNE_SHAPES)]
         assert all(t > 0 for t in info["fs_tune_ms"])
     with pytest.raises(rt3d.RT3DError):
-        g.set_fs_shape(96, 1)
+        g.set_fs_shape((96, 1, 0, 0))
+    with pytest.raises(rt3d.RT3DError):
+        g.set_fs_shape((128, 1, 3, 0))
 
 
 def test_fs_thick_thin_extremes(rt3d):
@@ -206,6 +208,24 @@ def test_os_solve_parity(rt3d):
     dJ, m = g.os_solve(dev(np.ascontiguousarray(Lo.T)), dev(eps), dev(r), max_sweeps=50, tol=1e-6)
     assert m == mo
     assert np.max(np.abs(dJ.cpu().numpy() - dJo)) < 1e-12 * np.max(np.abs(dJo))
+
+
+def test_os_solve_mixed_fixed_sweeps(rt3d):
+    """Mixed mode: FP32 coefficients times the FP32 copy of the sweep, FP64
+    state; a fixed number of sweeps against the oracle's FP64 Jacobi (ragged
+    voxel count: 693 is not a multiple of the 32-voxel coefficient block)."""
+    rng = np.random.default_rng(3)
+    n = (11, 9, 7)
+    shape = (7, 9, 11)
+    chi = 10 ** rng.uniform(-1, 1.5, shape)
+    _, Lo = oracle.fs_cart(chi, np.ones(shape), 4, 6, False, lstar=True)
+    eps = 10 ** rng.uniform(-4, -1, shape)
+    r = rng.standard_normal(shape)
+    dJo, mo = oracle.os_jacobi(Lo, eps, r, max_sweeps=12, tol=0.0)
+    g = rt3d.Grid(n, 4, 6, rt3d.LINEAR, rt3d.FP32_FS_FP64_ALI)
+    dJ, m = g.os_solve(dev(np.ascontiguousarray(Lo.T)), dev(eps), dev(r), max_sweeps=12, tol=0.0)
+    assert m == mo == 12
+    assert np.max(np.abs(dJ.cpu().numpy() - dJo)) < 2e-6 * np.max(np.abs(dJo))
 
 
 def test_ali_step_parity(rt3d):
