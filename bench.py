@@ -46,6 +46,39 @@ SMS = 152
 LANES = 128
 
 
+# The FP32 formal-solution kernel's sources: the DRAM traffic recorded in
+# its profile summary applies only while they are unchanged.
+FS_SOURCES = ("paper_2102_01734_gb300/csrc/fs.cu", "paper_2102_01734_gb300/csrc/fs_step.cuh",
+              "paper_2102_01734_gb300/csrc/rt3d_internal.cuh")
+FS_PROFILE = "profiles/fs_fast_kernel_box129_field.md"
+
+
+def fs_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in FS_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the FP32 formal-solution kernel from its
+    profile summary, or None if the kernel's sources changed since."""
+    try:
+        text = open(os.path.join(ROOT, FS_PROFILE)).read()
+    except OSError:
+        return None
+    vals = dict(line.split(":", 1) for line in text.splitlines()
+                if line.startswith(("source_sha256:", "dram_bytes_per_launch:")))
+    if vals.get("source_sha256", "").strip() != fs_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -296,7 +329,7 @@ def run_ours(args):
         "fs_kernel_segments_per_s": fs_rate,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops,
-                     "traffic": None, "kernel": "fs_fast_kernel<parabolic>",
+                     "traffic": recorded_traffic(), "kernel": "fs_fast_kernel<parabolic>",
                      "peak_source": f"{SMS} SMs x {LANES} FP32 lanes x {sm_max:.0f} MHz "
                                     f"(sm_max_mhz, {peak_kind})",
                      "ops_per_segment": OPS_PER_SEGMENT},
