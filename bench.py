@@ -402,6 +402,68 @@ def run_kernels(args):
     return 0
 
 
+def run_precisions(args):
+    """Converged solves/s of the mixed-precision path against the plain FP64 GPU
+    path on the workload: one FP64 Krylov solve (FP64 formal solutions and
+    Jacobi throughout), one mixed solve, and the paper's plain ALI in FP64
+    (a bounded number of iterations; its iteration count to the tolerance is
+    estimated from the measured contraction of the change, and labelled so)."""
+    import torch
+
+    from paper_2102_01734_gb300 import build, inputs, rt3d
+
+    build.build()
+    cfg = inputs.CONFIGS[WORKLOAD]
+    chi, eps, B, bc = inputs.cartesian_config(cfg["n"], cfg["eps"], seed=cfg["seed"])
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    tchi, teps, tB = d(chi), d(eps), d(B)
+    tbc = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}
+    n, nth, nph = cfg["n"], cfg["ntheta"], cfg["nphi"]
+    out = {"mode": "precisions", "workload": WORKLOAD, "tol": args.tol}
+    Jref = {}
+    for name, prec in (("mixed", rt3d.FP32_FS_FP64_ALI), ("fp64", rt3d.FP64)):
+        g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, prec)
+        J = tB.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.solve(tchi, teps, tB, tbc, J, tol=args.tol, max_iter=args.max_iter)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        Jref[name] = J
+        out[name] = {"seconds": dt, "solves_per_s": 1.0 / dt, "fs_fp32": st["fs_fp32"],
+                     "fs_fp64": st["fs_fp64"], "est_error": st["est_error"],
+                     "residual64": st["residual64"], "note": "includes the Lambda* build"}
+        del g
+    diff = torch.max(torch.abs(Jref["mixed"] - Jref["fp64"]) / torch.abs(Jref["fp64"])).item()
+    out["max_rel_diff_mixed_vs_fp64"] = diff
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    # plain ALI (Eq. alo iterated, no Krylov), FP64
+    g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, rt3d.FP64, accel=rt3d.ACCEL_NONE)
+    J = tB.clone()
+    k = args.ali_iters
+    rels = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        st = g.solve(tchi, teps, tB, tbc, J, tol=1e-300, max_iter=k, raise_on_nonconv=False)
+        rels.append(st["rel_change"])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    per_it = dt / (2 * k)
+    rho = (rels[1] / rels[0]) ** (1.0 / k) if rels[0] > 0 else float("nan")
+    # iterations for the estimated error rel * rho / (1 - rho) to reach tol
+    import math
+    est_iters = (2 * k + math.log(args.tol * (1 - rho) / (rho * rels[1])) / math.log(rho)
+                 if 0 < rho < 1 else float("inf"))
+    out["fp64_plain_ali"] = {"iterations_run": 2 * k, "seconds_per_iteration": per_it,
+                             "rel_change": rels, "contraction": rho,
+                             "estimated_iterations_to_tol": est_iters,
+                             "estimated_seconds_to_tol": est_iters * per_it,
+                             "note": "estimated from the measured contraction (not run to the end)"}
+    print(json.dumps(out))
+    return 0
+
+
 def run_warmstart(args):
     """Learned warm start (spec pattern, not in the paper): training data
     are converged solutions the method produces on 32 x 32 x nz boxes (the
@@ -434,9 +496,11 @@ def run_warmstart(args):
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
     tchi, teps, tB = d(chi), d(eps), d(B)
     tbc = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}
-    g = rt3d.Grid(nz, nth, nph, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
     res = {}
     for name in ("B", "net"):
+        # a fresh grid for each start: both solves include the Lambda* build
+        # and the autotuning of the formal solution
+        g = rt3d.Grid(nz, nth, nph, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if name == "B":
@@ -446,10 +510,16 @@ def run_warmstart(args):
         J0 = J.clone()
         st = g.solve(tchi, teps, tB, tbc, J, tol=args.tol, max_iter=args.max_iter)
         torch.cuda.synchronize()
+        err = torch.abs(torch.log(J0 / J))
         res[name] = {"seconds": time.perf_counter() - t0, "fs_fp32": st["fs_fp32"],
                      "fs_fp64": st["fs_fp64"], "iterations": st["iterations"],
-                     "start_error_max": float(torch.max(torch.abs(torch.log(J0 / J)))),
-                     "residual64": st["residual64"]}
+                     "start_error_max": float(torch.max(err)),
+                     "start_error_mean": float(torch.mean(err)),
+                     "residual64": st["residual64"],
+                     "rounds": [[a, b, c, e] for a, b, c, e in
+                                zip(st["round_fp64"], st["round_fs"], st["round_res"],
+                                    st["round_est"])]}
+        del g
     Jn, JB = None, None
     out = {"mode": "warmstart", "eval_grid": [nz, nz, nz], "angles": [nth, nph],
            "train": {"fields": len(data), "box": [32, 32, nz], "angles": [nth // 2, nph // 2],
@@ -519,6 +589,9 @@ def main():
     ap.add_argument("--batched", action="store_true", help="batched-wavelength measurement")
     ap.add_argument("--batch-n", type=int, default=97)
     ap.add_argument("--batch-lambdas", type=int, default=32)
+    ap.add_argument("--precisions", action="store_true",
+                    help="mixed against plain FP64 GPU path (converged solves/s)")
+    ap.add_argument("--ali-iters", type=int, default=10)
     ap.add_argument("--warmstart", action="store_true",
                     help="train the learned warm start and evaluate it")
     ap.add_argument("--ws-n", type=int, default=193)
@@ -530,6 +603,8 @@ def main():
         return run_kernels(args)
     if args.warmstart:
         return run_warmstart(args)
+    if args.precisions:
+        return run_precisions(args)
     if args.batched:
         return run_batched(args)
     if args.impl == "reference":
