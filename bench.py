@@ -33,10 +33,18 @@ UNIT = "ray-segment updates/s"
 WORKLOAD = "box129_field"
 DESCR = ("129^3 periodic box, 32x64 angles, parabolic, eps=1e-6, chi=10^(-4+6(nz-1-z)/(nz-1))"
          " x exp(0.5 g), g ~ k^-3 Gaussian field (seed 1), B=1+0.2g; FP32 formal solution,"
-         " FP64 ALI/Jacobi/refinement/certification; converged to est. rel error 1e-8 from J=B")
-# algorithmic FP32-pipe operations per parabolic segment (see the design doc:
-# interval optical depth, exp, 1/(u+w), 1/w, a, a0, d, s, q, coefficients,
-# intensity update, J weight)
+         " FP64 Jacobi/vector algebra, {refine} refinement residuals, FP64 formal solution"
+         " certifying the residual; converged to est. rel error 1e-8 from J=B")
+REFINE = {"ff": "float-float", "mixed": "FP64"}
+
+
+def precision_of(name):
+    from paper_2102_01734_gb300 import rt3d
+    return {"ff": rt3d.FP32_FS_FF_REFINE, "mixed": rt3d.FP32_FS_FP64_ALI,
+            "fp64": rt3d.FP64}[name]
+# algorithmic FP32-pipe operations per parabolic segment (interval optical
+# depth, exp, 1/(u+w), 1/w, e0, a, a0, d, s, q, blend weight, coefficients,
+# intensity update, J weight: 28)
 OPS_PER_SEGMENT = 28
 # Jacobi sweep, mixed mode, algorithmic bytes per voxel: 26 FP32 coefficients,
 # 1/diag and r (FP64), the FP32 copy of the previous sweep (one pass; the
@@ -199,7 +207,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "description": DESCR, "parallelism": "cpu-openmp"},
+        "config": {"workload": WORKLOAD, "description": DESCR.format(refine=REFINE[args.precision]),
+                   "precision": args.precision, "parallelism": "cpu-openmp"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"formal solution (parabolic, FP64) over {len(angles)} of "
                                    f"{cfg['ntheta'] * cfg['nphi']} solid angles of the "
@@ -226,7 +235,7 @@ def run_ours(args):
     n = cfg["n"]
     # weak scaling: every rank solves its own atmosphere (independent problems)
     chi, eps, B, bc = inputs.cartesian_config(n, cfg["eps"], seed=cfg["seed"] + rank)
-    g = rt3d.Grid(n, cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+    g = rt3d.Grid(n, cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, precision_of(args.precision))
     info = g.info()
     seg_per_fs = info["segments"]
     tchi, teps, tB = (torch.from_numpy(a).to(dev) for a in (chi, eps, B))
@@ -266,7 +275,7 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total = float(t.item())
         torch.distributed.barrier()
-    fs_count = sum(s["fs_fp32"] + s["fs_fp64"] for s in stats)
+    fs_count = sum(s["fs_fp32"] + s["fs_fp64"] + s["fs_ff"] for s in stats)
     segs = fs_count * seg_per_fs * world
     value = segs / total
     solves_per_s = args.steps * world / total
@@ -293,7 +302,7 @@ def run_ours(args):
         hJ.copy_(hB)
         st = g.solve(hchi, heps, hB, {"I_top": 0.0, "I_bottom": hbot}, hJ, tol=args.tol,
                      max_iter=args.max_iter)
-        e2e_segs += (st["fs_fp32"] + st["fs_fp64"]) * seg_per_fs
+        e2e_segs += (st["fs_fp32"] + st["fs_fp64"] + st["fs_ff"]) * seg_per_fs
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
     N = chi.size
@@ -315,13 +324,17 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "description": DESCR, "grid": [n, n, n],
+        "config": {"workload": WORKLOAD, "description": DESCR.format(refine=REFINE[args.precision]),
+                   "precision": args.precision, "grid": [n, n, n],
                    "angles": [cfg["ntheta"], cfg["nphi"]], "segments_per_fs": seg_per_fs,
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "solves_per_s": solves_per_s,
         "solve": {"iterations": last["iterations"], "fs_fp32": last["fs_fp32"],
-                  "fs_fp64": last["fs_fp64"], "residual64": last["residual64"],
+                  "fs_fp64": last["fs_fp64"], "fs_ff": last["fs_ff"],
+                  "fs_ms": {"fp32": last["fs32_ms"], "fp64": last["fs64_ms"],
+                            "ff": last["fsff_ms"]},
+                  "residual64": last["residual64"],
                   "est_error": last["est_error"],
                   "rounds": [[r64, nfs, res, est] for r64, nfs, res, est in
                              zip(last["round_fp64"], last["round_fs"], last["round_res"],
@@ -386,6 +399,15 @@ def run_kernels(args):
     print(json.dumps({"os_sweep_ms": per, "os_sweep_GBps": SWEEP_BYTES_F32 * n / per / 1e6,
                       "bytes_per_voxel": SWEEP_BYTES_F32,
                       "note": "difference of 22- and 2-sweep OS solves over 20 sweeps"}))
+    g.formal_solution_ff(tchi, tB, tbc)  # allocates the split inputs
+    torch.cuda.synchronize()
+    e0.record()
+    g.formal_solution_ff(tchi, tB, tbc)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"ff_fs_ms": e0.elapsed_time(e1),
+                      "note": "float-float formal solution; includes the split of (chi, S) and "
+                              "the fold"}))
     if args.fp64_fs:
         g64 = rt3d.Grid(cfg["n"], cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, rt3d.FP64)
         g64.formal_solution(tchi, tB, tbc)
@@ -421,7 +443,9 @@ def run_precisions(args):
     n, nth, nph = cfg["n"], cfg["ntheta"], cfg["nphi"]
     out = {"mode": "precisions", "workload": WORKLOAD, "tol": args.tol}
     Jref = {}
-    for name, prec in (("mixed", rt3d.FP32_FS_FP64_ALI), ("fp64", rt3d.FP64)):
+    names = ["ff", "mixed"] + ([] if args.no_fp64 else ["fp64"])
+    for name in names:
+        prec = precision_of(name)
         g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, prec)
         J = tB.clone()
         torch.cuda.synchronize()
@@ -431,12 +455,23 @@ def run_precisions(args):
         dt = time.perf_counter() - t0
         Jref[name] = J
         out[name] = {"seconds": dt, "solves_per_s": 1.0 / dt, "fs_fp32": st["fs_fp32"],
-                     "fs_fp64": st["fs_fp64"], "est_error": st["est_error"],
+                     "fs_fp64": st["fs_fp64"], "fs_ff": st["fs_ff"],
+                     "fs_ms": [st["fs32_ms"], st["fs64_ms"], st["fsff_ms"]],
+                     "est_error": st["est_error"],
+                     "rounds": [[a, b, c, e] for a, b, c, e in
+                                zip(st["round_fp64"], st["round_fs"], st["round_res"],
+                                    st["round_est"])],
                      "residual64": st["residual64"], "note": "includes the Lambda* build"}
         del g
-    diff = torch.max(torch.abs(Jref["mixed"] - Jref["fp64"]) / torch.abs(Jref["fp64"])).item()
-    out["max_rel_diff_mixed_vs_fp64"] = diff
-    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    ref = "fp64" if "fp64" in Jref else "mixed"
+    for name in names:
+        if name != ref:
+            out[f"max_rel_diff_{name}_vs_{ref}"] = torch.max(
+                torch.abs(Jref[name] - Jref[ref]) / torch.abs(Jref[ref])).item()
+            out[f"speedup_{name}_over_{ref}"] = out[ref]["seconds"] / out[name]["seconds"]
+    if args.no_fp64:
+        print(json.dumps(out))
+        return 0
     # plain ALI (Eq. alo iterated, no Krylov), FP64
     g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, rt3d.FP64, accel=rt3d.ACCEL_NONE)
     J = tB.clone()
@@ -479,7 +514,7 @@ def run_warmstart(args):
     nz = args.ws_n
     nth, nph = args.ws_angles
     t0 = time.perf_counter()
-    gtrain = rt3d.Grid((32, 32, nz), nth // 2, nph // 2, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+    gtrain = rt3d.Grid((32, 32, nz), nth // 2, nph // 2, rt3d.PARABOLIC, precision_of(args.precision))
     eps_l, _ = inputs.batched_wavelengths(args.ws_fields, seed=3)
     seeds = list(range(1000, 1000 + args.ws_fields))
     eps_of = lambda s: 1e-6 if s % 2 == 0 else max(float(eps_l[s - 1000]), 1e-6)
@@ -500,7 +535,7 @@ def run_warmstart(args):
     for name in ("B", "net"):
         # a fresh grid for each start: both solves include the Lambda* build
         # and the autotuning of the formal solution
-        g = rt3d.Grid(nz, nth, nph, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+        g = rt3d.Grid(nz, nth, nph, rt3d.PARABOLIC, precision_of(args.precision))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if name == "B":
@@ -553,7 +588,7 @@ def run_batched(args):
     tB = torch.from_numpy(B).to(dv)
     Bs = tB.expand(nl, *tB.shape).contiguous()
     bots = torch.from_numpy(bc["I_bottom"]).to(dv).expand(nl, n, n).contiguous()
-    g = rt3d.Grid(n, 16, 32, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
+    g = rt3d.Grid(n, 16, 32, rt3d.PARABOLIC, precision_of(args.precision))
     seg = g.info()["segments"]
     J = Bs.clone()
     torch.cuda.synchronize()
@@ -592,6 +627,9 @@ def main():
     ap.add_argument("--precisions", action="store_true",
                     help="mixed against plain FP64 GPU path (converged solves/s)")
     ap.add_argument("--ali-iters", type=int, default=10)
+    ap.add_argument("--no-fp64", action="store_true", help="with --precisions: skip the FP64 path")
+    ap.add_argument("--precision", default="ff", choices=["ff", "mixed"],
+                    help="refinement residuals: float-float (ff) or FP64 (mixed)")
     ap.add_argument("--warmstart", action="store_true",
                     help="train the learned warm start and evaluate it")
     ap.add_argument("--ws-n", type=int, default=193)

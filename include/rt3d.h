@@ -64,8 +64,12 @@ enum {
                              same OS operator; same fixed point as the ALI) */
 };
 enum {
-    RT3D_FP64 = 0,            /* formal solution and ALI in FP64 */
-    RT3D_FP32_FS_FP64_ALI = 1 /* FP32 formal solution, FP64 ALI/residual, FP64 refinement */
+    RT3D_FP64 = 0,             /* formal solution and ALI in FP64 */
+    RT3D_FP32_FS_FP64_ALI = 1, /* FP32 formal solution, FP64 ALI/residual, FP64 refinement */
+    RT3D_FP32_FS_FF_REFINE = 2 /* as RT3D_FP32_FS_FP64_ALI, but the refinement residuals
+                                  come from the float-float formal solution
+                                  (rt3d_formal_solution_ff) and only the residual
+                                  that certifies J from an FP64 formal solution */
 };
 
 typedef struct {
@@ -75,7 +79,7 @@ typedef struct {
     int ntheta, nphi; /* direction set: mu_i = -1 + (2i+1)/ntheta,
                          phi_j = (2j+1) pi / nphi, weight 1/(ntheta nphi) */
     int interp;       /* RT3D_LINEAR or RT3D_PARABOLIC source interpolation */
-    int precision;    /* RT3D_FP64 or RT3D_FP32_FS_FP64_ALI */
+    int precision;    /* RT3D_FP64, RT3D_FP32_FS_FP64_ALI or RT3D_FP32_FS_FF_REFINE */
     int nlambda;      /* reserved: must be 0 or 1 */
     void *cuda_stream;/* cudaStream_t to run on, or NULL for the legacy stream */
     int accel;        /* rt3d_solve iteration: RT3D_ACCEL_NONE (plain ALI, Eq. alo
@@ -115,11 +119,13 @@ typedef struct {
                            (CUDA events on the grid's stream) */
     double fs64_ms;     /* same for the FP64 formal-solution kernels */
     long long launches; /* kernels launched by the call */
+    int fs_ff;          /* float-float formal solutions (RT3D_FP32_FS_FF_REFINE) */
+    double fsff_ms;     /* their summed device time */
     int rounds;         /* Krylov solve: refinement rounds (residual, then an
                            FGMRES cycle unless the residual certified J);
                            the first 16 are recorded below */
-    int round_fp64[16];    /* 1 if the round's residual came from an FP64
-                              formal solution */
+    int round_fp64[16];    /* the formal solution of the round's residual:
+                              0 FP32, 1 FP64, 2 float-float */
     int round_fs[16];      /* formal solutions of the round's FGMRES cycle */
     double round_res[16];  /* the round's residual max_v |r_v| / |J_v| */
     double round_est[16];  /* estimated error at that residual (-1: none) */
@@ -215,6 +221,16 @@ rt3d_status rt3d_formal_solution(rt3d_grid *grid, const double *chi, const doubl
  * or after max_sweeps (1..256). lstar: double[27][N] as written by
  * rt3d_formal_solution; eps, r, dJ_out: double[N]. sweeps_out (nullable,
  * host) receives the number of sweeps. */
+/* The formal solution without Lambda* in float-float arithmetic (not in the
+ * paper: FP64-class accuracy, about 1e-13 relative, on the FP32 pipe; GB300's
+ * FP64 rate is about 1/64 of its FP32 rate). Same arguments, layouts and
+ * error behaviour as rt3d_formal_solution without lstar_out; Cartesian grids
+ * of any precision (RT3D_EINVAL for a spherical grid). The first call
+ * allocates the split step records (16 bytes per cached point) and the split
+ * replicated (chi, S) (64 bytes per voxel). */
+rt3d_status rt3d_formal_solution_ff(rt3d_grid *grid, const double *chi, const double *S,
+                                    const rt3d_bc *bc, double *J_out);
+
 rt3d_status rt3d_os_solve(rt3d_grid *grid, const double *lstar, const double *eps,
                           const double *r, double *dJ_out, int max_sweeps, double tol,
                           int *sweeps_out);
@@ -253,6 +269,8 @@ typedef struct {
     double fs32_ms, fs64_ms;
     double seconds;
     long long launches;
+    long long fs_lambda_ff; /* single-wavelength float-float formal solutions done */
+    double fsff_ms;
 } rt3d_batch_stats;
 
 /* Batched wavelengths (Sec. 4.1: the geometry is the same for all wavelength

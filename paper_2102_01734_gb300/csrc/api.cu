@@ -90,6 +90,11 @@ struct rt3d_grid {
     double **dJ_dev = nullptr;  // device copy of {dJ[0], dJ[1]}
     float *dJ32[2] = {nullptr, nullptr};  // FP32 copies for the mixed-mode stencil
     void *chiS32 = nullptr, *chiS64 = nullptr;  // [4N] replicated 2 x 2 in x, y
+    // float-float formal solution (allocated on first use): split step
+    // records and split replicated (chi, S); ff_refine: refinement residuals
+    // from it (RT3D_FP32_FS_FF_REFINE)
+    float4 *recff = nullptr, *chiSff = nullptr;
+    bool ff_refine = false;
     // FP32 formal solution without Lambda*: replicated FP64 accumulation
     // (zero between launches) and the kernel shape chosen by fs_tune
     double *Jrep = nullptr;  // [4N]
@@ -139,8 +144,8 @@ struct rt3d_grid {
     // instrumentation: formal-solution kernel time (CUDA events on the
     // grid's stream) and kernels launched
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    int ev_pending = -1;  // -1 none, 0 FP32, 1 FP64
-    double fs_ms[2] = {0.0, 0.0};
+    int ev_pending = -1;  // -1 none, 0 FP32, 1 FP64, 2 float-float
+    double fs_ms[3] = {0.0, 0.0, 0.0};
     long long launches = 0;
 
     template <typename T>
@@ -323,6 +328,27 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
         ++g->launches;
     }
+    return RT3D_OK;
+}
+
+// Float-float formal solution of S = src (or (1 - eps) src + eps B when eps
+// is given) into g->Jfs; allocates its split inputs on first use.
+rt3d_status run_fs_ff(rt3d_grid *g, const FsParams &base, const double *chi, const double *src,
+                      const double *eps, const double *B) {
+    if (g->sph) return fail(RT3D_EINVAL, "the float-float formal solution needs the Cartesian grid");
+    if (!g->recff) {
+        TRY(g->alloc(&g->recff, (size_t)g->tpl.total));
+        TRY(g->alloc(&g->chiSff, 4 * (size_t)g->N));
+        CKL(launch_recff(g->tpl.total, g->tpl.rec64, g->recff, g->stream));
+    }
+    CKL(launch_pack_ff(g->nx, g->ny, g->nz, chi, src, eps, B, g->chiSff, g->stream));
+    TRY(collect_events(g));
+    CK(cudaEventRecord(g->ev0, g->stream));
+    CK(launch_fsff(base, g->recff, g->chiSff, g->parab, g->stream));
+    CK(cudaEventRecord(g->ev1, g->stream));
+    g->ev_pending = 2;
+    CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
+    g->launches += 3;
     return RT3D_OK;
 }
 
@@ -580,8 +606,11 @@ rt3d_status validate_desc(const rt3d_grid_desc *d) {
         return fail(RT3D_EINVAL, "bad angle grid %d x %d", d->ntheta, d->nphi);
     if (d->interp != RT3D_LINEAR && d->interp != RT3D_PARABOLIC)
         return fail(RT3D_EINVAL, "bad interp %d", d->interp);
-    if (d->precision != RT3D_FP64 && d->precision != RT3D_FP32_FS_FP64_ALI)
+    if (d->precision != RT3D_FP64 && d->precision != RT3D_FP32_FS_FP64_ALI &&
+        d->precision != RT3D_FP32_FS_FF_REFINE)
         return fail(RT3D_EINVAL, "bad precision %d", d->precision);
+    if (d->precision == RT3D_FP32_FS_FF_REFINE && d->geometry == RT3D_SPHERICAL)
+        return fail(RT3D_EINVAL, "float-float refinement needs the Cartesian grid");
     if (d->nlambda > 1) return fail(RT3D_EINVAL, "nlambda > 1 is not supported by this call");
     if (d->accel != RT3D_ACCEL_NONE && d->accel != RT3D_ACCEL_KRYLOV)
         return fail(RT3D_EINVAL, "bad accel %d", d->accel);
@@ -597,6 +626,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     g->nO = d.ntheta * d.nphi;
     g->stream = static_cast<cudaStream_t>(d.cuda_stream);
     g->fs64 = d.precision == RT3D_FP64;
+    g->ff_refine = d.precision == RT3D_FP32_FS_FF_REFINE;
     g->parab = d.interp == RT3D_PARABOLIC;
     g->a64 = g->fs64;
     g->sph = d.geometry == RT3D_SPHERICAL;
@@ -921,12 +951,15 @@ rt3d_status fgmres(rt3d_grid *g, const FsParams &fphom, bool fp64, const double 
 #define RT3D_KRYLOV_ETA0 RT3D_KRYLOV_ETA
 #endif
 
-// Krylov-accelerated solve with FP64 iterative refinement. Rounds: residual
-// r = J_FS(S(J)) - J (FP32 before the first converged cycle in the mixed
-// mode, FP64 afterwards), FGMRES cycle on A delta = r (A in the grid's FS
-// precision), J += delta. The error after a round is estimated as
-// gain * (next FP64 residual), gain = |delta|/|r| of the previous round;
-// the FP64 residual that meets tol is the certification.
+// Krylov-accelerated solve with iterative refinement. A round: residual
+// r = J_FS(S(J)) - J of the current J, then (unless it certifies J) one
+// FGMRES cycle on A delta = r with A in the grid's FS precision, J += delta.
+// Residuals: FP32 before the first converged cycle in the mixed modes, then
+// FP64; with float-float refinement (RT3D_FP32_FS_FF_REFINE) from the
+// float-float formal solution, and an FP64 one only when the float-float
+// estimate meets tol. The error after a round is estimated as gain * (next
+// residual), gain = |delta|/|r| of the previous round; only an FP64 residual
+// that meets tol certifies J.
 rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p,
                          const FsParams &fphom, double tol, int max_iter, rt3d_solve_stats &s,
                          bool *conv_out) {
@@ -940,51 +973,74 @@ rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p
     // residual of the starting J). An FP64 formal solution costs about 40
     // FP32 ones on this GPU, so every cycle is driven deep (the FP32
     // operator's rounding still allows that) to keep the number of FP64
-    // residuals of the refinement at two or three.
+    // residuals of the refinement at two or three; a cycle whose estimated
+    // error is already near tol is asked only for the reduction it needs,
+    // with a margin of 100: eta = max(RT3D_KRYLOV_ETA, min(0.1, 0.01 tol/est)).
     const double eta = RT3D_KRYLOV_ETA, eta0 = RT3D_KRYLOV_ETA0;
-    for (int round = 0; round < 60 && it < max_iter; ++round) {
-        // residual of the current J (the first one also builds Lambda*)
-        const bool fs64 = res64;
+    // residual kinds: 0 FP32, 1 FP64, 2 float-float
+    auto residual = [&](int kind, double *res_out) -> rt3d_status {
         const bool build = !g->lstar_valid;
-        CKL(launch_source(g->nx, g->ny, g->nz, g->J, g->eps, g->B, fs64 ? g->chiS64 : g->chiS32, fs64, false,
-                          g->stream));
-        TRY(run_fs(g, fs64 ? fp64p : fp, fs64, build));
-        if (fs64) ++s.fs_fp64;
-        else ++s.fs_fp32;
-        if (build) {
-            CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag,
-                               g->stream, g->per));
-            CK(cudaMemcpyAsync(g->chi_ref, g->chi, sizeof(double) * n, cudaMemcpyDeviceToDevice,
-                               g->stream));
-            CK(cudaMemcpyAsync(g->eps_ref, g->eps, sizeof(double) * n, cudaMemcpyDeviceToDevice,
-                               g->stream));
-            g->lstar_valid = true;
+        if (kind == 2) {
+            TRY(run_fs_ff(g, fp64p, g->chi, g->J, g->eps, g->B));
+            ++s.fs_ff;
+        } else {
+            const bool f64 = kind == 1;
+            CKL(launch_source(g->nx, g->ny, g->nz, g->J, g->eps, g->B, f64 ? g->chiS64 : g->chiS32,
+                              f64, false, g->stream));
+            TRY(run_fs(g, f64 ? fp64p : fp, f64, build));
+            if (f64) ++s.fs_fp64;
+            else ++s.fs_fp32;
+            if (build) {
+                CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag,
+                                   g->stream, g->per));
+                CK(cudaMemcpyAsync(g->chi_ref, g->chi, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                   g->stream));
+                CK(cudaMemcpyAsync(g->eps_ref, g->eps, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                   g->stream));
+                g->lstar_valid = true;
+            }
         }
         TRY(reset_scalar(g, offsetof(OsState, res), sizeof(unsigned long long)));
         CKL(launch_residual(n, g->Jfs, g->J, g->r64, g->st, g->stream));
-        TRY(read_scalar_d(g, offsetof(OsState, res), &res));
-        if (!(res == res)) return fail(RT3D_ENUMERIC, "NaN in the residual");
-        if (fs64) s.residual64 = res;
+        TRY(read_scalar_d(g, offsetof(OsState, res), res_out));
+        if (!(*res_out == *res_out)) return fail(RT3D_ENUMERIC, "NaN in the residual");
+        return RT3D_OK;
+    };
+    auto record = [&](int kind, double r, double e) {
         const int ri = s.rounds < 16 ? s.rounds : -1;
         ++s.rounds;
         if (ri >= 0) {
-            s.round_fp64[ri] = fs64 ? 1 : 0;
-            s.round_res[ri] = res;
-            s.round_est[ri] = (fs64 && gain >= 0.0) ? gain * res : -1.0;
+            s.round_fp64[ri] = kind;
+            s.round_res[ri] = r;
+            s.round_est[ri] = e;
             s.round_fs[ri] = 0;
         }
+        return ri;
+    };
+    for (int round = 0; round < 60 && it < max_iter; ++round) {
+        // the first residual also builds Lambda* (FP32 or FP64 kind)
+        int kind = res64 ? ((g->ff_refine && g->lstar_valid) ? 2 : 1) : 0;
+        TRY(residual(kind, &res));
         // gain < 0: unknown (first round, or a residual relative to J = 0)
-        if (fs64 && gain >= 0.0) {
+        est = (kind != 0 && gain >= 0.0) ? gain * res : -1.0;
+        int ri = record(kind, res, est);
+        if (kind == 2 && est >= 0.0 && est <= tol) {
+            // float-float estimate met: the FP64 formal solution decides
+            kind = 1;
+            TRY(residual(1, &res));
             est = gain * res;
-            if (est <= tol) {
-                conv = true;
-                break;
-            }
+            ri = record(1, res, est);
         }
+        if (kind == 1) s.residual64 = res;
+        if (kind == 1 && est >= 0.0 && est <= tol) {
+            conv = true;
+            break;
+        }
+        double eta_k = res64 ? eta : eta0;
+        if (est > tol) eta_k = std::max(eta_k, std::min(0.1, 0.01 * tol / est));
         double achieved = 0.0;
         int steps = 0;
-        TRY(fgmres(g, fphom, g->fs64, g->r64, g->delta, res64 ? eta : eta0, max_iter - it, &achieved,
-                   &steps));
+        TRY(fgmres(g, fphom, g->fs64, g->r64, g->delta, eta_k, max_iter - it, &achieved, &steps));
         if (ri >= 0) s.round_fs[ri] = steps;
         it += steps;
         if (g->fs64) s.fs_fp64 += steps;
@@ -1194,6 +1250,21 @@ rt3d_status rt3d_formal_solution(rt3d_grid *g, const double *chi, const double *
     return RT3D_OK;
 }
 
+rt3d_status rt3d_formal_solution_ff(rt3d_grid *g, const double *chi, const double *S,
+                                    const rt3d_bc *bc, double *J_out) {
+    if (!g || !chi || !S || !J_out) return fail(RT3D_EINVAL, "NULL argument");
+    const size_t N = (size_t)g->N;
+    const double *dchi = nullptr, *dS = nullptr;
+    TRY(stage_in(g, chi, N, g->chi, &dchi));
+    TRY(stage_in(g, S, N, g->S, &dS));
+    FsParams fp;
+    TRY(fs_params(g, bc, false, false, &fp));
+    TRY(run_fs_ff(g, fp, dchi, dS, nullptr, nullptr));
+    TRY(deliver(g, J_out, g->Jfs, N));
+    CK(cudaStreamSynchronize(g->stream));
+    return RT3D_OK;
+}
+
 rt3d_status rt3d_os_solve(rt3d_grid *g, const double *lstar, const double *eps, const double *r,
                           double *dJ_out, int max_sweeps, double tol, int *sweeps_out) {
     if (!g || !lstar || !eps || !r || !dJ_out) return fail(RT3D_EINVAL, "NULL argument");
@@ -1240,7 +1311,7 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     const size_t N = (size_t)g->N;
     const int n = (int)N;
     rt3d_solve_stats s{};
-    g->fs_ms[0] = g->fs_ms[1] = 0.0;
+    g->fs_ms[0] = g->fs_ms[1] = g->fs_ms[2] = 0.0;
     g->launches = 0;
     TRY(load_problem(g, chi, eps, B));
     CK(cudaMemcpyAsync(g->J, J_inout, N * sizeof(double), cudaMemcpyDefault, g->stream));
@@ -1259,6 +1330,7 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
         TRY(collect_events(g));
         s.fs32_ms = g->fs_ms[0];
         s.fs64_ms = g->fs_ms[1];
+        s.fsff_ms = g->fs_ms[2];
         s.launches = g->launches;
         s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         if (stats) *stats = s;
@@ -1367,6 +1439,7 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     TRY(collect_events(g));
     s.fs32_ms = g->fs_ms[0];
     s.fs64_ms = g->fs_ms[1];
+    s.fsff_ms = g->fs_ms[2];
     s.launches = g->launches;
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = s;
@@ -1386,7 +1459,7 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     const size_t N = (size_t)g->N, nf = (size_t)g->nx * g->ny, L = (size_t)nl;
     rt3d_batch_stats bs{};
     bs.nlambda = nl;
-    g->fs_ms[0] = g->fs_ms[1] = 0.0;
+    g->fs_ms[0] = g->fs_ms[1] = g->fs_ms[2] = 0.0;
     g->launches = 0;
     TRY(batch_setup(g, nl));
     cudaStream_t s = g->stream;
@@ -1544,6 +1617,7 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
         CK(cudaMemcpyAsync(g->bJ + l * N, g->J, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
         bs.fs_lambda32 += sl.fs_fp32;
         bs.fs_lambda64 += sl.fs_fp64;
+        bs.fs_lambda_ff += sl.fs_ff;
         max_est = std::max(max_est, sl.est_error);
         max_res = std::max(max_res, sl.residual64);
         if (kconv) ++nconv;
@@ -1558,6 +1632,7 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     bs.max_residual64 = max_res;
     bs.fs32_ms = g->fs_ms[0] + bs.batch_ms;
     bs.fs64_ms = g->fs_ms[1];
+    bs.fsff_ms = g->fs_ms[2];
     bs.launches = g->launches;
     bs.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = bs;

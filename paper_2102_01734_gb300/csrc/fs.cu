@@ -328,9 +328,13 @@ __global__ void __launch_bounds__(256) fs_fast_kernel(FsParams p) {
 // can leave it does: branch tests on the high word of non-negative doubles
 // (integer compares), reciprocals seeded in FP32, widening by integer moves.
 
-// Whether x < b for a double x >= 0 (or any negative x) and a bound b whose
-// low word is zero, given the high word of b.
-__device__ __forceinline__ bool hi_below(double x, int b_hi) { return __double2hiint(x) < b_hi; }
+// Whether x < b for a double x >= 0 and a bound b > 0 whose low word is
+// zero, given the high word of b: an unsigned compare of the high words, so
+// a NaN of either sign (0 * Inf where a zero-opacity interval meets a zero
+// one) counts as not below.
+__device__ __forceinline__ bool hi_below(double x, int b_hi) {
+    return (unsigned)__double2hiint(x) < (unsigned)b_hi;
+}
 
 // 1/x for x > 0. Seed: x truncated to FP32 by integer moves (for x and 1/x
 // inside the FP32 normal range: exponent field 897..1148), its FP32

@@ -84,7 +84,9 @@ __device__ __forceinline__ void fast_step(RayF &s, const float2 *__restrict__ ch
     const float hn = cn.x * rn.y;
     const float dSn = cn.y - s.Sc;
     const float w = s.hc + hn;
-    const float rw = __fdividef(1.0f, w);
+    // 1/w with w floored at 1e-30: a zero-opacity pair (w = 0) gives q = 0 or
+    // a large finite q (blend weight 0) instead of Inf or NaN
+    const float rw = __fdividef(1.0f, fmaxf(w, 1e-30f));
     const float u = s.u;
     const IntervalE f = interval_fast(u, PARAB ? s.ru : __fdividef(1.0f, u));
     float In = fmaf(f.e0, s.Sp - s.I, s.I);
@@ -93,7 +95,7 @@ __device__ __forceinline__ void fast_step(RayF &s, const float2 *__restrict__ ch
         const float q = u * rw;
         const float fw = __saturatef(fmaf(-2.0f, u, 2.0f)) * __saturatef(fmaf(-0.5f, q, 2.0f));
         if (BRANCHLESS || fw > 0.0f) {
-            const float sd = fw * __fdividef(u, u + w) * f.d;
+            const float sd = fw * __fdividef(u, u + fmaxf(w, 1e-30f)) * f.d;
             In = fmaf(sd, fmaf(-q, dSn, s.dS), In);
         }
     }

@@ -1,0 +1,227 @@
+// Float-float formal solution without Lambda*: the formal solution of
+// fs.cu (Eq. frmsol, long characteristics, parabolic or linear weights of
+// Olson & Kunasz with the limited parabola, the update in difference form)
+// evaluated in float-float arithmetic (ff.cuh, about 48 significant bits) on
+// the FP32 pipe. It serves the refinement residuals of the mixed-precision
+// solve, which need FP64-class accuracy (about 1e-13 relative here, against
+// 2e-5 for the FP32 formal solution) but not the FP64 pipe, which on this GPU
+// runs at about 1/64 of the FP32 rate; the residual that certifies a
+// solution is still an FP64 formal solution.
+//
+// Inputs are split once per formal solution: the packed replicated (chi, S)
+// as float4 (chi_hi, chi_lo, S_hi, S_lo), and per step of the geometry
+// cache a float4 (l/2 hi, lo, J weight hi, lo). The J contribution cw I is
+// reduced in FP64 (the two widened parts added on the FP64 pipe, one
+// operation per point).
+#include "ff.cuh"
+#include "fs_step.cuh"
+
+namespace rt3d {
+
+namespace {
+
+// Cody-Waite split of ln2/32: c1 and c2 carry 11 significant bits (so n c1
+// and n c2 are exact for |n| < 2^13), (c3, c4) the rest as a float-float.
+constexpr float kC1 = 0.02166748f, kC2 = -6.6310167e-06f;
+constexpr float kC3 = -5.9520444e-11f, kC4 = -2.744745e-18f;
+constexpr float kInvL = 46.16624f;  // 32 / ln2
+
+// e^-u for u >= 1/2 (Tang's table-driven method, in float-float): n =
+// nearest integer to u 32/ln2, r = u - n ln2/32 (|r| <= ln2/64 + rounding),
+// e^-u = 2^-(n>>5) 2^-((n&31)/32) e^-r with tab[j] = 2^(-j/32) and
+// e^-r = 1 - r + r^2/2 (float-float) + (-r^3/6 + r^4/24 - r^5/120) (FP32,
+// below 2.2e-7 in magnitude). Returns 0 for u > 87 (below 1.7e-38).
+__device__ __forceinline__ ff ff_exp_neg(ff u, const float2 *tab) {
+    if (u.hi > 87.0f) return ff_of(0.0f);
+    const float nf = rintf(u.hi * kInvL);
+    const int n = (int)nf;
+    ff r = two_sum(fmaf(-nf, kC1, u.hi), -nf * kC2);
+    r = ff_add_f(r, u.lo);
+    r = ff_sub(r, ff_mul_f(ff{kC3, kC4}, nf));
+    ff e = ff_add(ff_sub(ff_of(1.0f), r), ff_scale(ff_mul(r, r), 0.5f));
+    const float x = r.hi;
+    e = ff_add_f(e, x * x * x * fmaf(x, fmaf(-x, 1.0f / 120.0f, 1.0f / 24.0f), -1.0f / 6.0f));
+    const float2 t = tab[n & 31];
+    e = ff_mul(e, ff{t.x, t.y});
+    return ff_scale(e, __int_as_float((127 - (n >> 5)) << 23));
+}
+
+struct IntervalFF {
+    ff e0, a, d;
+};
+
+// e0, a, d of the interval of optical depth u (the quantities of
+// interval_fast). u < 1/2: p(u) = e2/u^3 as the degree-9 polynomial fitted to
+// it on [0, 1/2] (approximation error 1.6e-18 relative), levels 9..6 of its
+// Horner scheme in FP32 (their share of p is below 2.6e-7), 5..0 in
+// float-float; b = u p, a = u/2 (1 - b), e0 = u (1 - a), d = a - b. Otherwise
+// E = e^-u, e0 = 1 - E, a = 1 - e0/u, d = (2a - e0)/u with ru = 1/u.
+__device__ __forceinline__ IntervalFF interval_ff(ff u, ff ru, const float2 *tab) {
+    IntervalFF r;
+    if (u.hi < 0.5f) {
+        float q = -3.4475018e-09f;
+        q = fmaf(q, u.hi, 4.935483e-08f);
+        q = fmaf(q, u.hi, -5.5071155e-07f);
+        q = fmaf(q, u.hi, 5.51131e-06f);
+        ff P = ff_fma(ff_of(q), u, ff{-4.9603143e-05f, 1.6644579e-12f});
+        P = ff_fma(P, u, ff{3.968254e-04f, -9.971136e-12f});
+        P = ff_fma(P, u, ff{-2.7777778e-03f, 6.7610896e-11f});
+        P = ff_fma(P, u, ff{1.6666668e-02f, -8.692481e-10f});
+        P = ff_fma(P, u, ff{-8.3333336e-02f, 2.4835272e-09f});
+        P = ff_fma(P, u, ff{3.3333334e-01f, -9.934108e-09f});
+        const ff b = ff_mul(u, P);
+        const ff hu = ff_scale(u, 0.5f);
+        r.a = ff_sub(hu, ff_mul(hu, b));
+        r.e0 = ff_sub(u, ff_mul(u, r.a));
+        r.d = ff_sub(r.a, b);
+    } else {
+        r.e0 = ff_sub(ff_of(1.0f), ff_exp_neg(u, tab));
+        r.a = ff_sub(ff_of(1.0f), ff_mul(r.e0, ru));
+        r.d = ff_mul(ff_sub(ff_scale(r.a, 2.0f), r.e0), ru);
+    }
+    return r;
+}
+
+// 1/x with x floored at 1e-30 (a zero-opacity pair gives a blend weight 0)
+__device__ __forceinline__ ff ff_recip_floor(ff x) {
+    return ff_recip(x.hi > 1e-30f ? x : ff_of(1e-30f));
+}
+
+// One thread per characteristic (blocks: 128 characteristics of one solid
+// angle). The table 2^(-j/32) is built per block in shared memory from the
+// FP64 exp2.
+template <bool PARAB>
+__global__ void __launch_bounds__(128) fsff_kernel(FsParams p, const float4 *__restrict__ recff,
+                                                   const float4 *__restrict__ chiS) {
+    __shared__ float2 tab[32];
+    if (threadIdx.x < 32) {
+        const double t = exp2(-(double)threadIdx.x / 32.0);
+        const float h = __double2float_rn(t);
+        tab[threadIdx.x] = make_float2(h, __double2float_rn(t - (double)h));
+    }
+    __syncthreads();
+    const int nray = p.nx * p.ny;
+    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= nray) return;
+    const int o = p.order[blockIdx.y];
+    const int K = p.tlen[o];
+    const long long t0 = p.toff[o];
+    const float4 *__restrict__ rec = p.rec32 + t0;  // offsets
+    const float4 *__restrict__ rf = recff + t0;     // (l/2, J weight) as float-float
+    double *__restrict__ J = p.Jrep;
+    const int base = ray % p.nx + 2 * p.nx * (ray / p.nx);
+
+    double I0 = 0.0;
+    if (!p.homogeneous) {
+        if (p.up[o]) I0 = p.bot_face ? p.bot_face[ray] : p.I_bot;
+        else I0 = p.top_face ? p.top_face[ray] : p.I_top;
+    }
+    ff I = ff_split(I0);
+    int vc = base + __float_as_int(__ldg(&rec[0].x));
+    float4 r = __ldg(rf);
+    float4 cs = chiS[vc];
+    ff hc = ff_mul(ff{cs.x, cs.y}, ff{r.x, r.y});  // half the optical depth of the chord
+    ff cw = ff{r.z, r.w};
+    ff u = hc;  // the entry interval: chi_{-1} l_{-1} = 0
+    ff Sc = ff{cs.z, cs.w}, Sp = Sc, dS = ff_of(0.0f);
+    ff ru = ff_recip_floor(hc);
+    for (int k = 1; k < K; ++k) {
+        const int vn = base + __float_as_int(__ldg(&rec[k].x));
+        const float4 rn = __ldg(rf + k);
+        const float4 cn = chiS[vn];
+        const ff hn = ff_mul(ff{cn.x, cn.y}, ff{rn.x, rn.y});
+        const ff Sn = ff{cn.z, cn.w};
+        const ff dSn = ff_sub(Sn, Sc);
+        const ff w = ff_add(hc, hn);
+        const IntervalFF f = interval_ff(u, ru, tab);
+        ff In = ff_fma(f.e0, ff_sub(Sp, I), I);
+        In = ff_fma(f.a, dS, In);
+        const ff rw = ff_recip_floor(w);
+        if (PARAB) {
+            const ff q = ff_mul(u, rw);
+            if (u.hi < 1.0f && q.hi < 4.0f) {
+                ff fw = ff_of(1.0f);
+                if (!(u.hi < 0.5f)) fw = ff_sub(ff_of(2.0f), ff_scale(u, 2.0f));
+                if (!(q.hi < 2.0f)) fw = ff_mul(fw, ff_sub(ff_of(2.0f), ff_scale(q, 0.5f)));
+                const ff s = ff_mul(u, ff_recip_floor(ff_add(u, w)));
+                const ff sd = ff_mul(ff_mul(fw, s), f.d);
+                In = ff_fma(sd, ff_fma(ff_neg(q), dSn, dS), In);
+            }
+        }
+        I = In;
+        const ff c = ff_mul(cw, I);
+        atomicAdd(J + vc, widen_f32(c.hi) + widen_f32(c.lo));
+        u = w;
+        ru = rw;
+        hc = hn;
+        Sp = Sc;
+        Sc = Sn;
+        dS = dSn;
+        vc = vn;
+        cw = ff{rn.z, rn.w};
+    }
+    const IntervalFF f = interval_ff(u, ru, tab);
+    I = ff_fma(f.a, dS, ff_fma(f.e0, ff_sub(Sp, I), I));
+    const ff c = ff_mul(cw, I);
+    atomicAdd(J + vc, widen_f32(c.hi) + widen_f32(c.lo));
+    if (!(fabsf(I.hi) <= 3.402823466e38f))  // non-finite: make J NaN
+        atomicAdd(J + vc, __longlong_as_double(0x7ff8000000000000LL));
+}
+
+// (chi, S) split into float-float, written to the four replicas of every
+// voxel; S = src, or (1 - eps) src + eps B when eps is given
+__global__ void pack_ff_kernel(int nx, int ny, int nz, const double *chi, const double *src,
+                               const double *eps, const double *B, float4 *out) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+        double sv = src[v];
+        if (eps) sv = (1.0 - eps[v]) * sv + eps[v] * B[v];
+        const ff c = ff_split(chi[v]), s = ff_split(sv);
+        const float4 val = make_float4(c.hi, c.lo, s.hi, s.lo);
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) out[rep_index(x + a * nx, y + b * ny, z, nx, ny)] = val;
+    }
+}
+
+// per step: (l/2, J weight) split into float-float
+__global__ void recff_kernel(long long total, const double2 *rec64, float4 *out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double2 r = rec64[i];
+        const ff l = ff_split(r.x), c = ff_split(r.y);
+        out[i] = make_float4(l.hi, l.lo, c.hi, c.lo);
+    }
+}
+
+int blocks_cap(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_fsff(const FsParams &p, const float4 *recff, const float4 *chiS, bool parabolic,
+                        cudaStream_t s) {
+    const int threads = 128;
+    dim3 grid((p.nx * p.ny + threads - 1) / threads, p.nangles);
+    if (parabolic) fsff_kernel<true><<<grid, threads, 0, s>>>(p, recff, chiS);
+    else fsff_kernel<false><<<grid, threads, 0, s>>>(p, recff, chiS);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_ff(int nx, int ny, int nz, const double *chi, const double *src,
+                           const double *eps, const double *B, float4 *out, cudaStream_t s) {
+    const long long n = (long long)nx * ny * nz;
+    pack_ff_kernel<<<blocks_cap(n, 256), 256, 0, s>>>(nx, ny, nz, chi, src, eps, B, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recff(long long total, const double2 *rec64, float4 *out, cudaStream_t s) {
+    recff_kernel<<<blocks_cap(total, 256), 256, 0, s>>>(total, rec64, out);
+    return cudaGetLastError();
+}
+
+}  // namespace rt3d

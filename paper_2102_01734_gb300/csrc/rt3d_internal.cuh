@@ -114,6 +114,15 @@ bool fs_shape_valid(const FsShape &sh);
 // FP32 formal solution without Lambda* into p.Jrep (zero on entry; the fold
 // zeroes it again).
 cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, const FsShape &sh, cudaStream_t s);
+// Float-float formal solution without Lambda* into p.Jrep (zero on entry):
+// recff = per-step (l/2, J weight) split, chiS = replicated split (chi, S)
+cudaError_t launch_fsff(const FsParams &p, const float4 *recff, const float4 *chiS, bool parabolic,
+                        cudaStream_t s);
+// split (chi, S) into the four replicas; S = src, or (1 - eps) src + eps B
+cudaError_t launch_pack_ff(int nx, int ny, int nz, const double *chi, const double *src,
+                           const double *eps, const double *B, float4 *out, cudaStream_t s);
+// split the FP64 step records (l/2, J weight)
+cudaError_t launch_recff(long long total, const double2 *rec64, float4 *out, cudaStream_t s);
 // FP64 formal solution without Lambda* into p.Jrep (zero on entry)
 cudaError_t launch_fs64_fast(const FsParams &p, bool parabolic, cudaStream_t s);
 // J[v] = sum of the four replicas of v in Jrep; zeroes Jrep

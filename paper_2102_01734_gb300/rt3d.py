@@ -32,7 +32,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ETIMEOUT, ENUMERIC = range(7)
 CARTESIAN_PERIODIC_XY = 0
 SPHERICAL = 1
 LINEAR, PARABOLIC = 0, 1
-FP64, FP32_FS_FP64_ALI = 0, 1
+FP64, FP32_FS_FP64_ALI, FP32_FS_FF_REFINE = 0, 1, 2
 ACCEL_NONE, ACCEL_KRYLOV = 0, 1
 
 _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -55,7 +55,7 @@ class SolveStats(ctypes.Structure):
                 ("jacobi_sweeps", _c_int), ("rel_change", _c_double),
                 ("residual64", _c_double), ("est_error", _c_double), ("seconds", _c_double),
                 ("fs32_ms", _c_double), ("fs64_ms", _c_double), ("launches", ctypes.c_longlong),
-                ("rounds", _c_int), ("round_fp64", _c_int * 16), ("round_fs", _c_int * 16),
+                ("fs_ff", _c_int), ("fsff_ms", _c_double), ("rounds", _c_int), ("round_fp64", _c_int * 16), ("round_fs", _c_int * 16),
                 ("round_res", _c_double * 16), ("round_est", _c_double * 16)]
 
     def as_dict(self):
@@ -71,7 +71,8 @@ class BatchStats(ctypes.Structure):
                 ("graph_replays", _c_int), ("fs_lambda32", ctypes.c_longlong),
                 ("fs_lambda64", ctypes.c_longlong), ("max_est_error", _c_double),
                 ("max_residual64", _c_double), ("batch_ms", _c_double), ("fs32_ms", _c_double),
-                ("fs64_ms", _c_double), ("seconds", _c_double), ("launches", ctypes.c_longlong)]
+                ("fs64_ms", _c_double), ("seconds", _c_double), ("launches", ctypes.c_longlong),
+                ("fs_lambda_ff", ctypes.c_longlong), ("fsff_ms", _c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -122,6 +123,7 @@ def load(path: str | None = None):
     lib.rt3d_grid_template.argtypes = [_vp, _c_int, P(_c_int), _vp, _vp]
     lib.rt3d_formal_solution.argtypes = [_vp, _vp, _vp, P(BC), _vp, _vp]
     lib.rt3d_os_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, _c_int, _c_double, P(_c_int)]
+    lib.rt3d_formal_solution_ff.argtypes = [_vp, _vp, _vp, P(BC), _vp]
     lib.rt3d_ali_step.argtypes = [_vp, _vp, _vp, _vp, P(BC), _vp, P(_c_double)]
     lib.rt3d_solve.argtypes = [_vp, _vp, _vp, _vp, P(BC), _vp, _c_double, _c_int, P(SolveStats)]
     lib.rt3d_os_solve_noalloc.argtypes = [_c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _c_int,
@@ -297,6 +299,15 @@ def formal_solution(h, chi, S, bc=None, J_out=None, lstar_out=None):
     return J_out
 
 
+def formal_solution_ff(h, chi, S, bc=None, J_out=None):
+    """Float-float formal solution (FP64-class accuracy on the FP32 pipe)."""
+    keep = []
+    b = _bc(bc, keep)
+    _check(load().rt3d_formal_solution_ff(h, _ptr(chi), _ptr(S), ctypes.byref(b) if b else None,
+                                          _ptr(J_out)))
+    return J_out
+
+
 def os_solve(h, lstar, eps, r, dJ_out, max_sweeps: int = 50, tol: float = 1e-3) -> int:
     m = _c_int(0)
     _check(load().rt3d_os_solve(h, _ptr(lstar), _ptr(eps), _ptr(r), _ptr(dJ_out), max_sweeps,
@@ -405,6 +416,11 @@ class Grid:
             L = lstar_out if lstar_out is not None else _empty_like(chi, (27, self.N))
         formal_solution(self.handle, chi, S, bc, J, L)
         return (J, L) if lstar else J
+
+    def formal_solution_ff(self, chi, S, bc=None, J_out=None):
+        J = J_out if J_out is not None else _empty_like(chi, self.shape)
+        formal_solution_ff(self.handle, chi, S, bc, J)
+        return J
 
     def os_solve(self, lstar, eps, r, max_sweeps=50, tol=1e-3):
         dJ = _empty_like(r, r.shape)

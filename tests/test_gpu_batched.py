@@ -32,12 +32,13 @@ def _batch(n, nl, seed):
     return chis, epss, Bs, bots
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "mixed_ff", "fp64"])
 def test_batched_matches_oracle_per_wavelength(rt3d, precision):
     n = (12, 10, 9)
     nl = 5
     chis, epss, Bs, bots = _batch(n, nl, 2)
-    prec = rt3d.FP64 if precision == "fp64" else rt3d.FP32_FS_FP64_ALI
+    prec = {"fp64": rt3d.FP64, "mixed": rt3d.FP32_FS_FP64_ALI,
+            "mixed_ff": rt3d.FP32_FS_FF_REFINE}[precision]
     g = rt3d.Grid(n, 4, 8, rt3d.PARABOLIC, prec)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
     J = d(Bs).clone()

@@ -152,13 +152,68 @@ def test_fs_fast_every_shape(rt3d, n, nth, nph, seed):
         g.set_fs_shape((128, 1, 3, 0))
 
 
+# Float-float formal solution: per-step coefficient errors measured on a CPU
+# emulation of its arithmetic against mpmath are <= 2e-12 relative for d (the
+# closed form just above u = 1/2), 2e-13 for a and 6e-14 for e0; J, a weighted
+# mean of intensities built from them, is held to 1e-11.
+TOLFF = 1e-11
+
+
+@pytest.mark.parametrize("parabolic", [False, True])
+@pytest.mark.parametrize("n,nth,nph,seed", CASES)
+def test_fs_ff_parity(rt3d, n, nth, nph, seed, parabolic):
+    """Float-float formal solution against the FP64 oracle (grids of both
+    mixed precisions)."""
+    chi, S, bc = _case(n, seed)
+    Jo = oracle.fs_cart(chi, S, nth, nph, parabolic, bc)
+    for prec in (rt3d.FP32_FS_FP64_ALI, rt3d.FP32_FS_FF_REFINE):
+        g = rt3d.Grid(n, nth, nph, int(parabolic), prec)
+        for _ in range(2):
+            J = g.formal_solution_ff(dev(chi), dev(S), dev_bc(bc))
+            assert relerr(J.cpu().numpy(), Jo) < TOLFF, (prec, relerr(J.cpu().numpy(), Jo))
+
+
+def test_fs_ff_extremes(rt3d):
+    """dtau from 1e-7 to 3e3 and zero (series branch, Tang exp branch, e^-u
+    below FP32 range), S and chi over many decades."""
+    rng = np.random.default_rng(11)
+    n = (16, 12, 10)
+    shape = (10, 12, 16)
+    chi = 10 ** rng.uniform(-7, 3.5, shape)
+    chi[2:4, 3:6, 4:9] = 0.0
+    S = 10 ** rng.uniform(-3, 3, shape)
+    bc = {"I_top": 0.5, "I_bottom": 1.5}
+    for parabolic in (False, True):
+        Jo = oracle.fs_cart(chi, S, 4, 8, parabolic, bc)
+        g = rt3d.Grid(n, 4, 8, int(parabolic), rt3d.FP32_FS_FF_REFINE)
+        J = g.formal_solution_ff(dev(chi), dev(S), bc)
+        assert relerr(J.cpu().numpy(), Jo) < TOLFF, (parabolic, relerr(J.cpu().numpy(), Jo))
+
+
+def test_fs_ff_box129_sampled(rt3d):
+    """Full-size box (129^3, 32 x 64 angles, parabolic): sampled voxels of the
+    float-float formal solution against the oracle's per-voxel route."""
+    cfg = inputs.CONFIGS["box129_field"]
+    chi, eps, B, bc = inputs.cartesian_config(129, cfg["eps"], seed=cfg["seed"])
+    S = B.copy()
+    g = rt3d.Grid(129, 32, 64, rt3d.PARABOLIC, rt3d.FP32_FS_FF_REFINE)
+    J = g.formal_solution_ff(dev(chi), dev(S), dev_bc(bc)).cpu().numpy().reshape(-1)
+    rng = np.random.default_rng(1)
+    vs = [0, 129 * 129 * 100 + 7, chi.size - 1] + list(rng.integers(0, chi.size, 2))
+    for v in vs:
+        Jv = oracle.fs_cart_voxel(chi, S, 32, 64, int(v), True, bc)
+        assert abs(J[v] - Jv) / abs(Jv) < TOLFF, (v, abs(J[v] - Jv) / abs(Jv))
+
+
 def test_fs_thick_thin_extremes(rt3d):
-    """Per-voxel dtau from 1e-7 to 3e3 (both series and closed-form branches,
-    vacuum-like and opaque voxels next to each other)."""
+    """Per-voxel dtau from 1e-7 to 3e3 and zero (both series and closed-form
+    branches, vacuum and opaque voxels next to each other), every FP32
+    ray-bundle shape."""
     rng = np.random.default_rng(9)
     n = (16, 12, 10)
     shape = (10, 12, 16)
     chi = 10 ** rng.uniform(-7, 3.5, shape)
+    chi[2:4, 3:6, 4:9] = 0.0  # a vacuum patch: zero-length optical intervals
     S = rng.uniform(0.1, 3.0, shape)
     bc = {"I_top": 0.5, "I_bottom": 1.5}
     for parabolic in (False, True):
@@ -167,6 +222,11 @@ def test_fs_thick_thin_extremes(rt3d):
             g = rt3d.Grid(n, 4, 8, int(parabolic), prec)
             J = g.formal_solution(dev(chi), dev(S), bc)
             assert relerr(J.cpu().numpy(), Jo) < tol, (parabolic, prec)
+            if prec == rt3d.FP32_FS_FP64_ALI:
+                for shape in SHAPES:
+                    g.set_fs_shape(shape)
+                    J = g.formal_solution(dev(chi), dev(S), bc)
+                    assert relerr(J.cpu().numpy(), Jo) < tol, (parabolic, shape)
 
 
 def test_fs_host_pointers_match_device(rt3d):
@@ -251,10 +311,11 @@ def _golden33():
 
 
 @pytest.mark.parametrize("accel", ["ali", "krylov"])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_ff"])
 def test_solve_box33_matches_golden(rt3d, precision, accel):
     chi, eps, B, bc = inputs.cartesian_config(33, 1e-2)
-    prec = rt3d.FP64 if precision == "fp64" else rt3d.FP32_FS_FP64_ALI
+    prec = {"fp64": rt3d.FP64, "mixed": rt3d.FP32_FS_FP64_ALI,
+            "mixed_ff": rt3d.FP32_FS_FF_REFINE}[precision]
     acc = rt3d.ACCEL_NONE if accel == "ali" else rt3d.ACCEL_KRYLOV
     g = rt3d.Grid(33, 8, 16, rt3d.LINEAR, prec, accel=acc)
     J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
@@ -273,7 +334,7 @@ def test_solve_field_matches_oracle(rt3d, parabolic, accel):
     Jo, it, _, _ = oracle.ali_solve(chi, eps, B, 4, 8, parabolic, bc, tol=1e-13, max_iter=3000)
     assert it > 0
     acc = rt3d.ACCEL_NONE if accel == "ali" else rt3d.ACCEL_KRYLOV
-    for prec in (rt3d.FP64, rt3d.FP32_FS_FP64_ALI):
+    for prec in (rt3d.FP64, rt3d.FP32_FS_FP64_ALI, rt3d.FP32_FS_FF_REFINE):
         g = rt3d.Grid(n, 4, 8, int(parabolic), prec, accel=acc)
         J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
         st = g.solve(dev(chi), dev(eps), dev(B), dev_bc(bc), J, tol=1e-9, max_iter=3000)
