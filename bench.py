@@ -152,6 +152,23 @@ def dist_env():
     return rank, world, local
 
 
+def job_totals(segments, seconds, solves, device="cpu"):
+    """Whole-job (segments, seconds, solves): segments and solves summed over
+    the ranks (weak scaling: each rank solves its own atmosphere, so their
+    formal-solution counts differ), seconds the maximum over the ranks (each
+    timed its own steps between barriers). One process: unchanged."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(segments), float(seconds), float(solves)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(segments), float(solves)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(c[0].item()), float(t.item()), float(c[1].item())
+
+
 def cpu_info():
     model = ""
     try:
@@ -269,16 +286,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
     clocks = sampler.stop()
-    total = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
-        torch.distributed.barrier()
     fs_count = sum(s["fs_fp32"] + s["fs_fp64"] + s["fs_ff"] for s in stats)
-    segs = fs_count * seg_per_fs * world
+    segs, total, solves = job_totals(fs_count * seg_per_fs, float(np.sum(times)), args.steps, dev)
+    if world > 1:
+        torch.distributed.barrier()
     value = segs / total
-    solves_per_s = args.steps * world / total
+    solves_per_s = solves / total
     fs32_ms = sum(s["fs32_ms"] for s in stats)
     n32 = sum(s["fs_fp32"] for s in stats)
     fs_rate = n32 * seg_per_fs / (fs32_ms / 1e3) if fs32_ms > 0 else 0.0
@@ -296,6 +309,8 @@ def run_ours(args):
     hJ = torch.empty(chi.shape, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     e2e_segs = 0
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -304,7 +319,7 @@ def run_ours(args):
                      max_iter=args.max_iter)
         e2e_segs += (st["fs_fp32"] + st["fs_fp64"] + st["fs_ff"]) * seg_per_fs
     torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - t0
+    e2e_segs, e2e_t, _ = job_totals(e2e_segs, time.perf_counter() - t0, e2e_steps, dev)
     N = chi.size
     h2d = (4 * N + hbot.numel()) * 8
     d2h = N * 8
