@@ -514,6 +514,58 @@ def run_precisions(args):
     return 0
 
 
+def run_spherical(args):
+    """Spherical shell (the paper's second test geometry) at a reduced size:
+    the ray-set build, FP32 and FP64 formal solutions and a converged solve
+    (FP32 formal solutions, FP64 refinement and certification)."""
+    import torch
+
+    from paper_2102_01734_gb300 import build, inputs, rt3d
+
+    build.build()
+    n = tuple(args.sph_n)
+    nth, nph = args.sph_angles
+    chi, eps, B, bc = inputs.spherical_config(n, args.sph_eps)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    tchi, teps, tB = d(chi), d(eps), d(B)
+    tbc = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"]), "I_irr": bc["I_irr"]}
+    out = {"mode": "spherical", "grid": list(n), "angles": [nth, nph], "eps": args.sph_eps}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, prec in (("fp32", rt3d.FP32_FS_FP64_ALI), ("fp64", rt3d.FP64)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, prec, geometry=rt3d.SPHERICAL)
+        torch.cuda.synchronize()
+        info = g.info()
+        out.setdefault("build_seconds", time.perf_counter() - t0)
+        out["segments_per_fs"] = info["segments"]
+        out["device_bytes"] = info["device_bytes"]
+        g.formal_solution(tchi, tB, tbc)
+        torch.cuda.synchronize()
+        e0.record()
+        g.formal_solution(tchi, tB, tbc)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[f"fs_{name}_ms"] = ms
+        out[f"fs_{name}_segments_per_s"] = info["segments"] / (ms / 1e3)
+        if name == "fp32":
+            J = tB.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = g.solve(tchi, teps, tB, tbc, J, tol=args.tol, max_iter=args.max_iter)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out["solve"] = {"seconds": dt, "solves_per_s": 1.0 / dt, "fs_fp32": st["fs_fp32"],
+                            "fs_fp64": st["fs_fp64"], "est_error": st["est_error"],
+                            "residual64": st["residual64"],
+                            "segments_per_s": (st["fs_fp32"] + st["fs_fp64"]) * info["segments"] / dt,
+                            "note": "includes the Lambda* build"}
+        del g
+    print(json.dumps(out))
+    return 0
+
+
 def run_warmstart(args):
     """Learned warm start (spec pattern, not in the paper): training data
     are converged solutions the method produces on 32 x 32 x nz boxes (the
@@ -645,6 +697,11 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="with --precisions: skip the FP64 path")
     ap.add_argument("--precision", default="ff", choices=["ff", "mixed"],
                     help="refinement residuals: float-float (ff) or FP64 (mixed)")
+    ap.add_argument("--spherical", action="store_true",
+                    help="spherical shell at a reduced size (ray-set build, FS, solve)")
+    ap.add_argument("--sph-n", type=int, nargs=3, default=[65, 33, 65])
+    ap.add_argument("--sph-angles", type=int, nargs=2, default=[32, 64])
+    ap.add_argument("--sph-eps", type=float, default=1e-4)
     ap.add_argument("--warmstart", action="store_true",
                     help="train the learned warm start and evaluate it")
     ap.add_argument("--ws-n", type=int, default=193)
@@ -658,6 +715,8 @@ def main():
         return run_warmstart(args)
     if args.precisions:
         return run_precisions(args)
+    if args.spherical:
+        return run_spherical(args)
     if args.batched:
         return run_batched(args)
     if args.impl == "reference":

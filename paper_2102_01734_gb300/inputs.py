@@ -18,7 +18,15 @@ dataset is involved):
   B = 1 + 0.2 g, uniform eps; boundary: no incoming intensity at the top,
   I = B of the entered bottom voxel at the bottom.
 
-Arrays have shape (nz, ny, nx), x fastest.
+* ``spherical_config(...)``: the paper's second test geometry (a spherical
+  shell, Sec. 3.2) on a (r, theta, phi) grid with log-spaced radial edges from
+  r_in to r_out: chi = C r^-12 at the cell's geometric-mean radius with C set
+  by the radial optical depth tau_core of the shell, B = 1, uniform eps;
+  boundary: I = B leaving the core, no incoming intensity at the outer sphere
+  except an irradiation I_irr (in units of B) from the side x > 0.
+
+Cartesian arrays have shape (nz, ny, nx), x fastest; spherical ones
+(nphi, ntheta, nr), r fastest.
 """
 from __future__ import annotations
 
@@ -75,6 +83,21 @@ CONFIGS = {
     # 97^3 box, 16 x 32 angles, batched wavelengths
     "box97_batched": dict(n=97, eps=None, seed=1, ntheta=16, nphi=32, parabolic=True),
 }
+
+
+def spherical_config(n, eps: float, tau_core: float = 100.0, r_in: float = 1.0,
+                     r_out: float = 1.3, I_irr: float = 10.0):
+    """(chi, eps, B, bc) on an (nr, ntheta, nphi) spherical grid; chi = C r^-12
+    with tau(r_in) = integral of chi over [r_in, r_out] = tau_core."""
+    nr, nt, np_ = (int(v) for v in n)
+    re = r_in * (r_out / r_in) ** (np.arange(nr + 1) / nr)
+    rc = np.sqrt(re[:-1] * re[1:])
+    C = tau_core * 11.0 / (r_in ** -11 - r_out ** -11)
+    chi = np.broadcast_to(C * rc ** -12.0, (np_, nt, nr)).copy()
+    B = np.ones_like(chi)
+    eps_a = np.full_like(chi, eps)
+    bc = {"I_top": 0.0, "I_bottom": np.ones((np_, nt)), "I_irr": float(I_irr)}
+    return chi, eps_a, B, bc
 
 
 def batched_wavelengths(nlambda: int, seed: int = 3):
