@@ -4,7 +4,7 @@
 // Ray set of a solid angle: the voxels are visited in index order and every
 // voxel that no ray of this angle has crossed yet launches the full line
 // through its centre, traced from its entry (outer sphere, or the core sphere
-// r = r_in) to its exit; all cells it crosses are marked. One thread per
+// r = r_in) to its exit; all cells it crosses are marked. One warp per
 // angle builds the set (pass 1 counts rays and segments, pass 2 writes the
 // tables). Crossings with the radial spheres, the polar cones (the plane z = 0
 // for theta = pi/2) and the azimuthal half-planes are computed with
@@ -175,108 +175,289 @@ __device__ __forceinline__ int nb_code_sph(int nr, int nt, int np, int a, int b)
     return (dr + 1) + 3 * (dt + 1) + 9 * (dp + 1);
 }
 
-__global__ void sph_build_kernel(SphBuildParams p) {
-    const int lo = blockIdx.x * blockDim.x + threadIdx.x;
+// Warp-cooperative construction of one angle's ray set (one warp per angle,
+// the same set and the same arithmetic as the sequential definition in the
+// file header): the next launch voxel is the first unset bit of the angle's
+// hit bitset at or after a cursor, found 1024 voxels at a time with a ballot;
+// the crossing candidates of its line are generated lane-strided over the
+// spheres, cones and half-planes (each candidate with the same FP64
+// operations as a sequential scan), appended through ballots, sorted by a
+// bitonic network in shared memory and merged by lane 0; the cells of the
+// intervals are found lane-strided. Shared memory per warp: npow doubles
+// (sort buffer, npow = power of two >= ncap), ncap doubles (merged
+// parameters) and ncap ints (cells).
+__global__ void __launch_bounds__(32) sph_build_kernel(SphBuildParams p, int npow) {
+    extern __shared__ double smem[];
+    double *sb = smem;                                      // [npow]
+    double *ts = smem + npow;                               // [ncap]
+    int *cells = reinterpret_cast<int *>(ts + p.ncap);      // [ncap]
+    const int lane = threadIdx.x;
+    const int lo = blockIdx.x;
     const int o = p.o0 + lo;
     if (lo >= p.nchunk || o >= p.nangles) return;
     const SphTables &T = p.T;
     const int N = T.nr * T.nt * T.np;
     const int words = (N + 31) / 32;
     unsigned *hit = p.hit + (long long)lo * words;
-    double *ts = p.tbuf + (long long)lo * p.ncap;
-    for (int i = 0; i < words; ++i) hit[i] = 0u;
+    for (int i = lane; i < words; i += 32) hit[i] = 0u;
+    __syncwarp();
     const double d[3] = {p.dir[3 * o], p.dir[3 * o + 1], p.dir[3 * o + 2]};
     long long seg = p.pass == 2 ? p.seg_base[o] : 0;
     long long ray = p.pass == 2 ? p.ray_base[o] : 0;
     const long long seg0 = seg;
     int nrays = 0;
-    long long nseg = 0;
-    for (int v = 0; v < N; ++v) {
-        if (hit[v >> 5] & (1u << (v & 31))) continue;
+    int cursor = 0;
+    for (;;) {
+        // next voxel no line of this angle has crossed yet
+        int v = -1;
+        while (cursor < N) {
+            const int w0 = cursor >> 5, wi = w0 + lane;
+            unsigned fr = 0u;
+            if (wi < words) {
+                fr = ~__ldcg(hit + wi);
+                if (wi == w0) fr &= ~0u << (cursor & 31);
+                if (wi == words - 1 && (N & 31)) fr &= (1u << (N & 31)) - 1u;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, fr != 0u);
+            if (bal) {
+                const int f = __ffs(bal) - 1;
+                const unsigned fm = __shfl_sync(0xffffffffu, fr, f);
+                v = (w0 + f) * 32 + __ffs(fm) - 1;
+                break;
+            }
+            cursor = (w0 + 32) * 32;
+        }
+        if (v < 0) break;
+        cursor = v + 1;
         const int ir = v % T.nr, it = (v / T.nr) % T.nt, ip = v / (T.nr * T.nt);
         const double P[3] = {dm(dm(T.rc[ir], T.stc[it]), T.cpc[ip]),
                              dm(dm(T.rc[ir], T.stc[it]), T.spc[ip]), dm(T.rc[ir], T.ctc[it])};
-        int entry;
-        double pin[3];
-        const int m = sph_params(T, P, d, ts, &entry, pin);
-        if (m > p.ncap) {
-            atomicCAS(p.err, 0, 4);
+        // ends of the line (as in sph_params)
+        const double b = da(da(dm(P[0], d[0]), dm(P[1], d[1])), dm(P[2], d[2]));
+        const double P2 = da(da(dm(P[0], P[0]), dm(P[1], P[1])), dm(P[2], P[2]));
+        const double disc = ds(dm(b, b), ds(P2, T.re2[T.nr]));
+        const double sq = __dsqrt_rn(disc);
+        double t0 = ds(-b, sq), t1 = da(-b, sq);
+        int entry = 0;
+        const double dc = ds(dm(b, b), ds(P2, T.re2[0]));
+        if (dc > 0.0) {
+            const double sc = __dsqrt_rn(dc);
+            const double a = ds(-b, sc), c = da(-b, sc);
+            if (c <= 0.0 && c > t0) {
+                t0 = c;
+                entry = 1;
+            }
+            if (a >= 0.0 && a < t1) t1 = a;
+        }
+        // crossing candidates strictly inside (t0, t1), appended in any order
+        int n = 0;
+        auto put = [&](bool ok, double t) {
+            const unsigned bl = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const int at = n + __popc(bl & ((1u << lane) - 1u));
+                if (at < npow) sb[at] = t;
+            }
+            n += __popc(bl);
+        };
+        for (int i0 = 1; i0 < T.nr; i0 += 32) {
+            const int i = i0 + lane;
+            bool ok1 = false, ok2 = false;
+            double r1 = 0.0, r2 = 0.0;
+            if (i < T.nr) {
+                const double di = ds(dm(b, b), ds(P2, T.re2[i]));
+                if (di > 0.0) {
+                    const double s_ = __dsqrt_rn(di);
+                    r1 = ds(-b, s_);
+                    r2 = da(-b, s_);
+                    ok1 = r1 > t0 && r1 < t1;
+                    ok2 = r2 > t0 && r2 < t1;
+                }
+            }
+            put(ok1, r1);
+            put(ok2, r2);
+        }
+        for (int j0 = 1; j0 < T.nt; j0 += 32) {
+            const int j = j0 + lane;
+            bool ok1 = false, ok2 = false;
+            double q1 = 0.0, q2 = 0.0;
+            if (j < T.nt) {
+                if (2 * j == T.nt) {
+                    if (d[2] != 0.0) {
+                        q1 = dd(-P[2], d[2]);
+                        ok1 = q1 > t0 && q1 < t1;
+                    }
+                } else {
+                    const double c2 = dm(T.ct[j], T.ct[j]);
+                    const double A = ds(dm(d[2], d[2]), c2);
+                    const double Bh = ds(dm(P[2], d[2]), dm(c2, b));
+                    const double C = ds(dm(P[2], P[2]), dm(c2, P2));
+                    int nq = 0;
+                    double roots[2] = {0.0, 0.0};
+                    if (A == 0.0) {
+                        if (Bh != 0.0) roots[nq++] = dd(-C, dm(2.0, Bh));
+                    } else {
+                        const double dq = ds(dm(Bh, Bh), dm(A, C));
+                        if (dq > 0.0) {
+                            const double s_ = __dsqrt_rn(dq);
+                            roots[nq++] = dd(ds(-Bh, s_), A);
+                            roots[nq++] = dd(da(-Bh, s_), A);
+                        }
+                    }
+                    for (int q = 0; q < nq; ++q) {
+                        const double t = roots[q];
+                        if (!(t > t0 && t < t1)) continue;
+                        const double z = da(P[2], dm(t, d[2]));
+                        if (dm(z, T.ct[j]) > 0.0) {
+                            if (q == 0) {
+                                q1 = t;
+                                ok1 = true;
+                            } else {
+                                q2 = t;
+                                ok2 = true;
+                            }
+                        }
+                    }
+                }
+            }
+            put(ok1, q1);
+            put(ok2, q2);
+        }
+        for (int k0 = 0; k0 < T.np; k0 += 32) {
+            const int k = k0 + lane;
+            bool ok = false;
+            double t = 0.0;
+            if (k < T.np) {
+                const double den = ds(dm(T.cpe[k], d[1]), dm(T.spe[k], d[0]));
+                if (den != 0.0) {
+                    t = dd(ds(dm(T.spe[k], P[0]), dm(T.cpe[k], P[1])), den);
+                    if (t > t0 && t < t1) {
+                        const double x = da(P[0], dm(t, d[0])), y = da(P[1], dm(t, d[1]));
+                        ok = da(dm(T.cpe[k], x), dm(T.spe[k], y)) > 0.0;
+                    }
+                }
+            }
+            put(ok, t);
+        }
+        if (n + 2 > p.ncap || n > npow) {
+            if (lane == 0) atomicCAS(p.err, 0, 4);
             return;
         }
+        // bitonic sort of sb[0, npw) ascending (padding +Inf), npw = 2^k >= n
+        int npw = 1;
+        while (npw < n) npw <<= 1;
+        for (int i = n + lane; i < npw; i += 32) sb[i] = __longlong_as_double(0x7ff0000000000000LL);
+        __syncwarp();
+        for (int kk = 2; kk <= npw; kk <<= 1) {
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (int i = lane; i < npw; i += 32) {
+                    const int ix = i ^ jj;
+                    if (ix > i) {
+                        const double x = sb[i], y = sb[ix];
+                        if ((x > y) == ((i & kk) == 0)) {
+                            sb[i] = y;
+                            sb[ix] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // merge equal parameters, t0 and t1 at the ends
+        if (lane == 0) {
+            ts[0] = t0;
+            int m = 1;
+            for (int i = 0; i < n; ++i)
+                if (sb[i] != ts[m - 1]) ts[m++] = sb[i];
+            if (t1 != ts[m - 1]) ts[m++] = t1;
+            cells[0] = m;  // passed to the other lanes below
+        }
+        __syncwarp();
+        const int m = __shfl_sync(0xffffffffu, lane == 0 ? cells[0] : 0, 0);
+        __syncwarp();
         const int K = m - 1;
-        hit[v >> 5] |= 1u << (v & 31);
-        for (int k = 0; k < K; ++k) {
+        if (lane == 0) atomicOr(hit + (v >> 5), 1u << (v & 31));
+        for (int k = lane; k < K; k += 32) {
             const double mid = dm(0.5, da(ts[k], ts[k + 1]));
             const int c = sph_cell(T, da(P[0], dm(mid, d[0])), da(P[1], dm(mid, d[1])),
                                    da(P[2], dm(mid, d[2])));
-            hit[c >> 5] |= 1u << (c & 31);
-            if (p.pass == 2) {
+            cells[k] = c;
+            atomicOr(hit + (c >> 5), 1u << (c & 31));
+        }
+        __syncwarp();
+        if (p.pass == 2) {
+            for (int k = lane; k < K; k += 32) {
                 const long long sidx = seg + k;
+                const int c = cells[k];
                 p.cell[sidx] = c;
                 const int cr = c % T.nr, ct = (c / T.nr) % T.nt, cp = c / (T.nr * T.nt);
                 p.crep[sidx] = (int)rep_index(cr, ct, cp, T.nr, T.nt);
                 const double l = ds(ts[k + 1], ts[k]);
                 p.len64[sidx] = l;
                 p.len32[sidx] = (float)l;
-            }
-        }
-        if (p.pass == 2) {
-            p.ray_off[ray] = seg;
-            p.ray_len[ray] = K;
-            p.ray_angle[ray] = o;
-            p.ray_launch[ray] = v;
-            int kind = 0, face = 0;
-            if (entry) {
-                kind = 2;
-                const int c0 = p.cell[seg];
-                face = (c0 / T.nr) % T.nt + T.nt * (c0 / (T.nr * T.nt));
-            } else if (pin[0] > 0.0 && d[0] < 0.0) {
-                kind = 1;
-            }
-            p.ray_kind[ray] = kind;
-            p.ray_face[ray] = face;
-            // Lambda* windows of this ray
-            for (int k = 0; k < K; ++k) {
-                const int vk = p.cell[seg + k];
+                // Lambda* window of the segment
                 const int jend = (k + 1 < K) ? k + 1 : k;
                 uint64_t wc = 0;
                 for (int r = 0; r < kWin; ++r) wc |= (uint64_t)kWinNone << (5 * r);
                 for (int j = jend; j >= 0; --j) {
-                    const int dc = nb_code_sph(T.nr, T.nt, T.np, p.cell[seg + j], vk);
-                    if (dc < 0) break;
+                    const int dcode = nb_code_sph(T.nr, T.nt, T.np, cells[j], c);
+                    if (dcode < 0) break;
                     const int r = j - k + 7;
                     if (r < 0) {
                         atomicCAS(p.err, 0, 3);
                         break;
                     }
                     wc &= ~((uint64_t)31 << (5 * r));
-                    wc |= (uint64_t)dc << (5 * r);
+                    wc |= (uint64_t)dcode << (5 * r);
                 }
-                p.win[seg + k] = wc;
+                p.win[sidx] = wc;
+            }
+            if (lane == 0) {
+                p.ray_off[ray] = seg;
+                p.ray_len[ray] = K;
+                p.ray_angle[ray] = o;
+                p.ray_launch[ray] = v;
+                int kind = 0, face = 0;
+                if (entry) {
+                    kind = 2;
+                    const int c0 = cells[0];
+                    face = (c0 / T.nr) % T.nt + T.nt * (c0 / (T.nr * T.nt));
+                } else if (da(P[0], dm(t0, d[0])) > 0.0 && d[0] < 0.0) {
+                    kind = 1;
+                }
+                p.ray_kind[ray] = kind;
+                p.ray_face[ray] = face;
             }
             ++ray;
         }
         seg += K;
         ++nrays;
-        nseg += K;
+        __syncwarp();
     }
     if (p.pass == 1) {
-        p.nrays[o] = nrays;
-        p.nseg[o] = nseg;
+        if (lane == 0) {
+            p.nrays[o] = nrays;
+            p.nseg[o] = seg;
+        }
         return;
     }
-    // chord sum of every cell for this angle, then the J weights
+    // chord sum of every cell for this angle, in segment order (each cell's
+    // sum accumulated by one lane), then the J weights
     double *den = p.den + (long long)lo * N;
-    for (int v = 0; v < N; ++v) den[v] = 0.0;
-    for (long long s = seg0; s < seg; ++s) den[p.cell[s]] += p.len64[s];
-    const double w = p.wt[o];
-    for (long long s = seg0; s < seg; ++s) {
-        const double c = w * (p.len64[s] / den[p.cell[s]]);
-        p.cw64[s] = c;
-        p.cw32[s] = (float)c;
+    for (int c = lane; c < N; c += 32) den[c] = 0.0;
+    __syncwarp();
+    for (long long sg = seg0; sg < seg; ++sg) {
+        const int c = p.cell[sg];
+        if ((c & 31) == lane) den[c] += p.len64[sg];
     }
-    for (int v = 0; v < N; ++v)
-        if (!(den[v] > 0.0)) atomicCAS(p.err, 0, 5);
+    __syncwarp();
+    const double w = p.wt[o];
+    for (long long sg = seg0 + lane; sg < seg; sg += 32) {
+        const double c = w * (p.len64[sg] / den[p.cell[sg]]);
+        p.cw64[sg] = c;
+        p.cw32[sg] = (float)c;
+    }
+    for (int c = lane; c < N; c += 32)
+        if (!(den[c] > 0.0)) atomicCAS(p.err, 0, 5);
 }
 
 // Interval functions (as on the Cartesian grid).
@@ -440,8 +621,15 @@ cudaError_t launch_sph_t(const SphFsParams &p, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_sph_build(const SphBuildParams &p, cudaStream_t s) {
-    const int threads = 32;
-    sph_build_kernel<<<(p.nchunk + threads - 1) / threads, threads, 0, s>>>(p);
+    int npow = 1;
+    while (npow < p.ncap) npow <<= 1;
+    const size_t shm = sizeof(double) * (npow + p.ncap) + sizeof(int) * p.ncap;
+    if (shm > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(sph_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e != cudaSuccess) return e;
+    }
+    sph_build_kernel<<<p.nchunk, 32, shm, s>>>(p, npow);
     return cudaGetLastError();
 }
 
