@@ -127,6 +127,8 @@ struct rt3d_grid {
     double *s_len64 = nullptr, *s_cw64 = nullptr;
     float *s_len32 = nullptr, *s_cw32 = nullptr;
     uint64_t *s_win = nullptr;
+    float4 *s_rec = nullptr;  // [segments] (replicated index bits, l/2, J weight, 0)
+    int *s_perm = nullptr;    // [rays] by decreasing length
 
     // batched-wavelength workspace (allocated for the largest n_lambda seen)
     int bl_cap = 0;
@@ -301,14 +303,20 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         sp.I_out = base.I_top;
         sp.I_irr = base.I_irr;
         sp.homogeneous = base.homogeneous;
-        CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
+        const bool sfast = !fp64 && !with_lstar;
+        if (!sfast) CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
         if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
         TRY(collect_events(g));
         CK(cudaEventRecord(g->ev0, g->stream));
-        CK(launch_sph_fs(sp, fp64, g->parab, with_lstar, g->stream));
+        if (sfast) CK(launch_sph_fs_fast(sp, g->s_rec, g->s_perm, g->Jrep, g->parab, g->stream));
+        else CK(launch_sph_fs(sp, fp64, g->parab, with_lstar, g->stream));
         CK(cudaEventRecord(g->ev1, g->stream));
         g->ev_pending = fp64 ? 1 : 0;
         ++g->launches;
+        if (sfast) {
+            CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
+            ++g->launches;
+        }
         return RT3D_OK;
     }
     // without Lambda*: the replicated-accumulation kernels (J folded after)
@@ -581,6 +589,26 @@ rt3d_status sph_build(rt3d_grid *g) {
     if (herr) return fail(RT3D_EINVAL, "spherical tracer error %d", herr);
     g->segments = tsg;
     g->tpl.kmax = bp.ncap;
+    // FP32 records and the ray order (decreasing length, then ray index) of
+    // the formal solution without Lambda*
+    if (tr > (long long)INT32_MAX) return fail(RT3D_EINVAL, "too many spherical rays");
+    TRY(g->alloc(&g->s_rec, tsg));
+    CKL(launch_sph_rec(tsg, g->s_crep, g->s_len64, g->s_cw64, g->s_rec, s));
+    {
+        std::vector<int> len(tr);
+        CK(cudaMemcpyAsync(len.data(), g->s_ray_len, sizeof(int) * tr, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        int maxlen = 0;
+        for (const int l : len) maxlen = std::max(maxlen, l);
+        std::vector<long long> start(maxlen + 2, 0);
+        for (const int l : len) ++start[maxlen - l + 1];
+        for (int i = 1; i <= maxlen + 1; ++i) start[i] += start[i - 1];
+        std::vector<int> perm(tr);
+        for (long long r = 0; r < tr; ++r) perm[start[maxlen - len[r]]++] = (int)r;
+        TRY(g->alloc(&g->s_perm, tr));
+        CK(cudaMemcpyAsync(g->s_perm, perm.data(), sizeof(int) * tr, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
     return alloc_work(g);
 }
 

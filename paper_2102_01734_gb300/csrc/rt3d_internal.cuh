@@ -306,6 +306,13 @@ struct SphFsParams {
 cudaError_t launch_sph_build(const SphBuildParams &p, cudaStream_t s);
 cudaError_t launch_sph_fs(const SphFsParams &p, bool fp64, bool parabolic, bool lstar,
                           cudaStream_t s);
+// FP32 formal solution without Lambda* over per-segment records, rays in the
+// order perm, into the replicated FP64 Jrep (zero on entry; fold afterwards)
+cudaError_t launch_sph_fs_fast(const SphFsParams &p, const float4 *rec, const int *perm,
+                               double *Jrep, bool parabolic, cudaStream_t s);
+// per-segment records (replicated index bits, l/2, J weight, 0)
+cudaError_t launch_sph_rec(long long nseg, const int *crep, const double *len64, const double *cw64,
+                           float4 *rec, cudaStream_t s);
 
 // Sets the message returned by rt3d_last_error() on this thread.
 void set_last_error(const char *msg);

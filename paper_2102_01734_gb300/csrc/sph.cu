@@ -15,7 +15,7 @@
 // its index in the 2 x 2-replicated packed (chi, S) array, the chord, the J
 // weight w l / (chord sum of the cell for this angle) and the Lambda* window
 // (neighbourhood in index space, periodic in phi only).
-#include "rt3d_internal.cuh"
+#include "fs_step.cuh"
 
 namespace rt3d {
 
@@ -630,6 +630,92 @@ cudaError_t launch_sph_build(const SphBuildParams &p, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     sph_build_kernel<<<p.nchunk, 32, shm, s>>>(p, npow);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// FP32 formal solution without Lambda* on the spherical cache: the
+// per-point step of the Cartesian kernel (fast_step, difference form) over
+// per-segment records (replicated index of the cell as int bits, l/2, J
+// weight), rays taken in order of decreasing length (perm) so that the
+// threads of a warp run similar trip counts, contributions reduced in FP64
+// at the replicated index (folded afterwards).
+template <bool PARAB>
+__global__ void __launch_bounds__(128) sph_fs_fast_kernel(SphFsParams p, const float4 *__restrict__ rec,
+                                                          const int *__restrict__ perm,
+                                                          double *__restrict__ Jrep) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= p.nrays) return;
+    const int ray = perm[idx];
+    const long long s0 = p.ray_off[ray];
+    const int K = p.ray_len[ray];
+    const int kind = p.ray_kind[ray];
+    const float4 *__restrict__ rr = rec + s0;
+    const float2 *__restrict__ chiS = static_cast<const float2 *>(p.chiS);
+    double I0 = 0.0;
+    if (!p.homogeneous) {
+        if (kind == 2) I0 = p.core_face ? p.core_face[p.ray_face[ray]] : p.I_core;
+        else if (kind == 1) I0 = p.I_irr;
+        else I0 = p.I_out;
+    }
+    RayF st;
+    st.live = true;
+    st.base = 0;
+    st.I = (float)I0;
+    const float4 r0 = __ldg(rr);
+    st.vc = __float_as_int(r0.x);
+    const float2 cs = chiS[st.vc];
+    st.hc = cs.x * r0.y;
+    st.u = st.hc;
+    st.Sc = cs.y;
+    st.Sp = cs.y;
+    st.dS = 0.0f;
+    st.ru = __fdividef(1.0f, fmaxf(st.hc, 1e-30f));
+    float cwc = r0.z;
+    int k = 1;
+    for (; k + 1 < K; k += 2) {
+        const float4 r1 = __ldg(rr + k), r2 = __ldg(rr + k + 1);
+        fast_step<PARAB, false, false>(st, chiS, Jrep, r1, cwc);
+        fast_step<PARAB, false, false>(st, chiS, Jrep, r2, r1.z);
+        cwc = r2.z;
+    }
+    if (k < K) {
+        const float4 r1 = __ldg(rr + k);
+        fast_step<PARAB, false, false>(st, chiS, Jrep, r1, cwc);
+        cwc = r1.z;
+    }
+    const IntervalE f = interval_fast(st.u, PARAB ? st.ru : __fdividef(1.0f, st.u));
+    st.I = fmaf(f.a, st.dS, fmaf(f.e0, st.Sp - st.I, st.I));
+    atomicAdd(Jrep + st.vc, (double)(cwc * st.I));
+    if (!(fabsf(st.I) <= 3.402823466e38f))  // non-finite: make J NaN
+        atomicAdd(Jrep + st.vc, __longlong_as_double(0x7ff8000000000000LL));
+}
+
+// per segment: (replicated index as int bits, l/2, J weight, 0)
+__global__ void sph_rec_kernel(long long nseg, const int *crep, const double *len64,
+                               const double *cw64, float4 *rec) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nseg;
+         i += (long long)gridDim.x * blockDim.x)
+        rec[i] = make_float4(__int_as_float(crep[i]), (float)(0.5 * len64[i]), (float)cw64[i], 0.0f);
+}
+
+}  // namespace
+
+cudaError_t launch_sph_rec(long long nseg, const int *crep, const double *len64, const double *cw64,
+                           float4 *rec, cudaStream_t s) {
+    long long b = (nseg + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    sph_rec_kernel<<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(nseg, crep, len64, cw64, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sph_fs_fast(const SphFsParams &p, const float4 *rec, const int *perm,
+                               double *Jrep, bool parabolic, cudaStream_t s) {
+    const int threads = 128;
+    const long long blocks = (p.nrays + threads - 1) / threads;
+    if (parabolic) sph_fs_fast_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(p, rec, perm, Jrep);
+    else sph_fs_fast_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(p, rec, perm, Jrep);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,11 @@ def test_sph_fs_parity(rt3d, parabolic):
         Lg = L.cpu().numpy().T
         lerr = np.max(np.abs(Lg - Lo) / np.max(np.abs(Lo), axis=1, keepdims=True))
         assert lerr < tol, (prec, lerr)
+        # without Lambda* (FP32: the record kernel over rays sorted by length)
+        for _ in range(2):
+            J2 = g.formal_solution(dev(chi), dev(S), dbc)
+            err = np.max(np.abs(J2.cpu().numpy() - Jo) / np.abs(Jo))
+            assert err < tol, (prec, err)
 
 
 def test_sph_solve_matches_direct_solution(rt3d):
