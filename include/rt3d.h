@@ -271,6 +271,11 @@ typedef struct {
     long long launches;
     long long fs_lambda_ff; /* single-wavelength float-float formal solutions done */
     double fsff_ms;
+    rt3d_fs_shape fs_shape; /* shape of the batched FP32 formal solution (autotuned
+                               on the grid's first batched call, one
+                               characteristic per thread) */
+    float fs_tune_ms[RT3D_FS_TUNE_SHAPES]; /* its candidates' times (0: not
+                               timed: two characteristics per thread) */
 } rt3d_batch_stats;
 
 /* Batched wavelengths (Sec. 4.1: the geometry is the same for all wavelength

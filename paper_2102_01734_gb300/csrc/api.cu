@@ -142,6 +142,8 @@ struct rt3d_grid {
     BatchState *bsd = nullptr;    // device copy
     cudaStream_t bstream = nullptr;
     cudaEvent_t bev0 = nullptr, bev1 = nullptr;
+    FsShape bfs_shape{0, 0, 0, 0};  // batched FS shape (block 0: not tuned)
+    float bfs_tune_ms[RT3D_FS_TUNE_SHAPES] = {};
 
     // instrumentation: formal-solution kernel time (CUDA events on the
     // grid's stream) and kernels launched
@@ -1560,6 +1562,42 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     bp.I_bot = bc ? bc->I_bottom : 0.0;
     bp.bs = g->bsd;
 
+    // Batched autotuner: every candidate shape with one characteristic per
+    // thread is timed once on this batch's first source (CUDA events on the
+    // batch stream), the fastest goes into the graph; kept for later calls.
+    if (g->bfs_shape.block == 0) {
+        CK(cudaEventRecord(g->bev0, s));
+        CK(cudaStreamWaitEvent(g->bstream, g->bev0, 0));
+        CKL(launch_b_source(bp, nl, g->bJ, g->beps, g->bB, g->bstream));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float best = 0.0f;
+        int pick = -1;
+        for (int i = 0; i < RT3D_FS_TUNE_SHAPES; ++i) {
+            if (kFsShapes[i].rays_per_thread != 1) continue;
+            CK(cudaEventRecord(e0, g->bstream));
+            CKL(launch_b_fs(bp, nl, kFsShapes[i], g->parab, g->bstream));
+            CK(cudaEventRecord(e1, g->bstream));
+            CK(cudaMemsetAsync(g->bJrep, 0, 4 * L * N * sizeof(double), g->bstream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            g->bfs_tune_ms[i] = ms;
+            if (pick < 0 || ms < best) {
+                best = ms;
+                pick = i;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CK(cudaStreamSynchronize(g->bstream));
+        g->bfs_shape = kFsShapes[pick];
+    }
+    bs.fs_shape = rt3d_fs_shape{g->bfs_shape.block, g->bfs_shape.rays_per_thread,
+                                g->bfs_shape.widen, g->bfs_shape.branchless};
+    for (int i = 0; i < RT3D_FS_TUNE_SHAPES; ++i) bs.fs_tune_ms[i] = g->bfs_tune_ms[i];
+
     // capture one iteration into a CUDA graph on the batch stream
     const int iter_cap = max_iter;
     const double switch_tol = g->fs64 ? tol : std::max(tol, 1e-6);
@@ -1568,7 +1606,8 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     CK(cudaStreamBeginCapture(g->bstream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = launch_batch_iteration(bp, nl, g->bJ, g->beps, g->bB, g->ba, g->binv, g->br,
                                             g->bbuf0, g->bbuf1, g->bb32_0, g->bb32_1, kBatchSweeps,
-                                            1e-3, switch_tol, iter_cap, g->parab, g->bstream);
+                                            1e-3, switch_tol, iter_cap, g->parab, g->bfs_shape,
+                                            g->bstream);
     cudaError_t ce = cudaStreamEndCapture(g->bstream, &graph);
     if (le != cudaSuccess || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);

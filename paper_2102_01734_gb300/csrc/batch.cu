@@ -66,10 +66,13 @@ __global__ void b_source(int nx, int ny, int nz, const double *J, const double *
 
 // FP32 formal solution (no Lambda*) of wavelength blockIdx.z into its
 // replicated FP64 J: the per-point step of the unbatched kernel (fast_step),
-// two points per trip, the FP64 widening alternating between the
-// conversion instruction and integer moves.
-template <bool PARAB>
-__global__ void __launch_bounds__(128) b_fs(BatchFsParams p) {
+// two points per trip, in the ray-bundle shape the batched autotuner chose
+// (threads per block from the launch; CONV as in fs_fast_kernel: 0 the
+// conversion instruction, 1 integer moves, 2 alternating; BL: parabolic
+// correction without a branch).
+template <bool PARAB, int CONV, bool BL>
+__global__ void __launch_bounds__(256) b_fs(BatchFsParams p) {
+    constexpr bool W0 = CONV == 1, W1 = CONV >= 1;
     const int l = blockIdx.z;
     if (!p.bs->active[l]) return;
     const int nray = p.nx * p.ny;
@@ -101,13 +104,13 @@ __global__ void __launch_bounds__(128) b_fs(BatchFsParams p) {
     int k = 1;
     for (; k + 1 < K; k += 2) {
         const float4 r1 = __ldg(rec + k), r2 = __ldg(rec + k + 1);
-        fast_step<PARAB, false, false>(s, chiS, J, r1, cwc);
-        fast_step<PARAB, true, false>(s, chiS, J, r2, r1.z);
+        fast_step<PARAB, W0, BL>(s, chiS, J, r1, cwc);
+        fast_step<PARAB, W1, BL>(s, chiS, J, r2, r1.z);
         cwc = r2.z;
     }
     if (k < K) {
         const float4 r1 = __ldg(rec + k);
-        fast_step<PARAB, false, false>(s, chiS, J, r1, cwc);
+        fast_step<PARAB, W0, BL>(s, chiS, J, r1, cwc);
         cwc = r1.z;
     }
     const IntervalE f = interval_fast(s.u, PARAB ? s.ru : __fdividef(1.0f, s.u));
@@ -262,19 +265,49 @@ int grid_x(long long n, int threads, int cap) {
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+template <bool PARAB, bool BL>
+void launch_b_fs_t(const BatchFsParams &p, dim3 grid, int block, int conv, cudaStream_t s) {
+    if (conv == 0) b_fs<PARAB, 0, BL><<<grid, block, 0, s>>>(p);
+    else if (conv == 1) b_fs<PARAB, 1, BL><<<grid, block, 0, s>>>(p);
+    else b_fs<PARAB, 2, BL><<<grid, block, 0, s>>>(p);
+}
+
 }  // namespace
+
+cudaError_t launch_b_source(const BatchFsParams &p, int nl, const double *J, const double *eps,
+                            const double *B, cudaStream_t s) {
+    const long long n = (long long)p.nx * p.ny * p.nz;
+    b_source<<<dim3(grid_x(n, 256, 152 * 2), nl), 256, 0, s>>>(p.nx, p.ny, p.nz, J, eps, B, p.chiS,
+                                                              p.bs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_b_fs(const BatchFsParams &p, int nl, const FsShape &sh, bool parabolic,
+                        cudaStream_t s) {
+    if (!fs_shape_valid(sh)) return cudaErrorInvalidValue;
+    const int block = sh.block;  // one characteristic per thread
+    dim3 grid((p.nx * p.ny + block - 1) / block, p.nangles, nl);
+    if (parabolic) {
+        if (sh.branchless) launch_b_fs_t<true, true>(p, grid, block, sh.widen, s);
+        else launch_b_fs_t<true, false>(p, grid, block, sh.widen, s);
+    } else {
+        if (sh.branchless) launch_b_fs_t<false, true>(p, grid, block, sh.widen, s);
+        else launch_b_fs_t<false, false>(p, grid, block, sh.widen, s);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, double *J, const double *eps,
                                    const double *B, const float *a, const double *inv_diag,
                                    double *r, double *buf0, double *buf1, float *b32_0,
                                    float *b32_1, int max_sweeps, double sweep_tol, double tol,
-                                   int max_iter, bool parabolic, cudaStream_t s) {
+                                   int max_iter, bool parabolic, const FsShape &shape,
+                                   cudaStream_t s) {
     const long long n = (long long)p.nx * p.ny * p.nz;
     const int gx = grid_x(n, 256, 152 * 2);
     b_source<<<dim3(gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, J, eps, B, p.chiS, p.bs);
-    dim3 gfs((p.nx * p.ny + 127) / 128, p.nangles, nl);
-    if (parabolic) b_fs<true><<<gfs, 128, 0, s>>>(p);
-    else b_fs<false><<<gfs, 128, 0, s>>>(p);
+    const cudaError_t fe = launch_b_fs(p, nl, shape, parabolic, s);
+    if (fe != cudaSuccess) return fe;
     b_fold_init<<<dim3(gx < 2 ? 2 : gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, p.Jrep, J, inv_diag,
                                                           r, buf0, b32_0, p.bs);
     for (int m = 1; m <= max_sweeps; ++m)

@@ -254,11 +254,19 @@ struct BatchFsParams {
 // One batched ALI iteration (source, formal solution, fold and OS right-hand
 // side, Jacobi sweeps, update, retirement, active count): a fixed launch
 // sequence, captured once into a CUDA graph.
+// S of every active wavelength into its packed (chi, S)
+cudaError_t launch_b_source(const BatchFsParams &p, int nl, const double *J, const double *eps,
+                            const double *B, cudaStream_t s);
+// batched FP32 formal solution into p.Jrep in the given shape (one
+// characteristic per thread; rays_per_thread is not used)
+cudaError_t launch_b_fs(const BatchFsParams &p, int nl, const FsShape &sh, bool parabolic,
+                        cudaStream_t s);
 cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, double *J, const double *eps,
                                    const double *B, const float *a, const double *inv_diag,
                                    double *r, double *buf0, double *buf1, float *b32_0,
                                    float *b32_1, int max_sweeps, double sweep_tol, double tol,
-                                   int max_iter, bool parabolic, cudaStream_t s);
+                                   int max_iter, bool parabolic, const FsShape &shape,
+                                   cudaStream_t s);
 
 // ---- spherical grid (sph.cu) ----
 struct SphTables {

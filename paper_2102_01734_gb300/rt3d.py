@@ -66,18 +66,6 @@ class SolveStats(ctypes.Structure):
         return out
 
 
-class BatchStats(ctypes.Structure):
-    _fields_ = [("nlambda", _c_int), ("converged", _c_int), ("iterations", _c_int),
-                ("graph_replays", _c_int), ("fs_lambda32", ctypes.c_longlong),
-                ("fs_lambda64", ctypes.c_longlong), ("max_est_error", _c_double),
-                ("max_residual64", _c_double), ("batch_ms", _c_double), ("fs32_ms", _c_double),
-                ("fs64_ms", _c_double), ("seconds", _c_double), ("launches", ctypes.c_longlong),
-                ("fs_lambda_ff", ctypes.c_longlong), ("fsff_ms", _c_double)]
-
-    def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
-
-
 class FsShape(ctypes.Structure):
     _fields_ = [("block", _c_int), ("rays_per_thread", _c_int), ("widen", _c_int),
                 ("branchless", _c_int)]
@@ -87,6 +75,24 @@ class FsShape(ctypes.Structure):
 
 
 FS_TUNE_SHAPES = 8
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("nlambda", _c_int), ("converged", _c_int), ("iterations", _c_int),
+                ("graph_replays", _c_int), ("fs_lambda32", ctypes.c_longlong),
+                ("fs_lambda64", ctypes.c_longlong), ("max_est_error", _c_double),
+                ("max_residual64", _c_double), ("batch_ms", _c_double), ("fs32_ms", _c_double),
+                ("fs64_ms", _c_double), ("seconds", _c_double), ("launches", ctypes.c_longlong),
+                ("fs_lambda_ff", ctypes.c_longlong), ("fsff_ms", _c_double),
+                ("fs_shape", FsShape), ("fs_tune_ms", ctypes.c_float * FS_TUNE_SHAPES)]
+
+    def as_dict(self):
+        out = {k: getattr(self, k) for k, _ in self._fields_}
+        out["fs_shape"] = self.fs_shape.as_tuple()
+        out["fs_tune_ms"] = list(self.fs_tune_ms)
+        return out
+
+
 
 
 class GridInfo(ctypes.Structure):

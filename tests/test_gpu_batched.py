@@ -66,6 +66,10 @@ def test_batched_equals_unbatched(rt3d):
     st = g.solve_batched(d(chis), d(epss), d(Bs), {"I_top": 0.0, "I_bottom": d(bots)}, J,
                          tol=1e-9, max_iter=3000)
     assert st["graph_replays"] > 0 and st["fs_lambda64"] >= 2 * nl
+    # the batched autotuner timed every one-characteristic-per-thread shape
+    cands = [rt3d.fs_tune_shape(i) for i in range(rt3d.FS_TUNE_SHAPES)]
+    assert st["fs_shape"] in [c for c in cands if c[1] == 1]
+    assert all((t > 0) == (c[1] == 1) for t, c in zip(st["fs_tune_ms"], cands))
     for l in range(nl):
         Jl = d(Bs[l]).clone()
         g.solve(d(chis[l]), d(epss[l]), d(Bs[l]), {"I_top": 0.0, "I_bottom": d(bots[l])}, Jl,
