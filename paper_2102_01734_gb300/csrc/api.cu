@@ -901,9 +901,18 @@ rt3d_status apply_A(rt3d_grid *g, const FsParams &fphom, bool fp64, const double
     return RT3D_OK;
 }
 
-// z = M^-1 v by Jacobi sweeps (the OS solve of Eq. alo)
+#ifndef RT3D_PRECOND_SWEEPS
+#define RT3D_PRECOND_SWEEPS 50
+#endif
+#ifndef RT3D_PRECOND_TOL
+#define RT3D_PRECOND_TOL 1e-3
+#endif
+
+// z = M^-1 v by Jacobi sweeps (the OS solve of Eq. alo): at most
+// RT3D_PRECOND_SWEEPS sweeps, stopped at a change of RT3D_PRECOND_TOL relative
+// to the iterate (the paper's OS solve; the same settings as the ALI step)
 rt3d_status precond(rt3d_grid *g, const double *v, double *z) {
-    TRY(os_solve_dev(g, nullptr, nullptr, v, 50, 1e-3));
+    TRY(os_solve_dev(g, nullptr, nullptr, v, RT3D_PRECOND_SWEEPS, RT3D_PRECOND_TOL));
     CKL(launch_copy_buf((int)g->N, g->dJ_dev, g->st, z, g->stream));
     return RT3D_OK;
 }
