@@ -2,17 +2,20 @@
 
 A step is one converged solve (all steps of the path: tracer cache reused,
 FP32 formal solutions with the Lambda* band built in the first iteration,
-FP64 Jacobi OS solves, FP64 defect correction and FP64 certification) of the
-box129_field workload: 129^3 periodic box, 32 x 64 solid angles, parabolic
-interpolation, eps = 1e-6, chi = vertical profile x lognormal k^-3 field
-(seed 1), B = 1 + 0.2 g, I_top = 0, I_bottom = B, from J = B to an estimated
-relative error of 1e-8 against FP64.
+FP64 Jacobi OS solves inside FGMRES, refinement residuals from float-float
+formal solutions (or FP64 with --precision mixed) and an FP64 formal solution
+certifying the result) of the box129_field workload: 129^3 periodic box,
+32 x 64 solid angles, parabolic interpolation, eps = 1e-6, chi = vertical
+profile x lognormal k^-3 field (seed 1), B = 1 + 0.2 g, I_top = 0,
+I_bottom = B, from J = B to an estimated relative error of 1e-8 against FP64.
 
 value = ray-segment updates (all formal solutions of the timed steps) per
 second of the timed region; solves_per_s is the second metric.
 
 --impl reference times the FP64 CPU oracle on a bounded angle sample of the
-same workload (the reference arm of this build: a plain CPU program).
+same workload (the reference arm: a plain CPU program). Clock samples taken
+during the timed region go to RT3D_CLOCKS_DIR (default: the system's
+temporary directory).
 """
 from __future__ import annotations
 
@@ -103,7 +106,9 @@ class ClockSampler:
     def __init__(self, index=0):
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        import tempfile
+        out = os.environ.get("RT3D_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out, f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -567,7 +572,7 @@ def run_spherical(args):
 
 
 def run_warmstart(args):
-    """Learned warm start (spec pattern, not in the paper): training data
+    """Learned warm start (not in the paper): training data
     are converged solutions the method produces on 32 x 32 x nz boxes (the
     vertical structure of the evaluation box), eps = 1e-6 and eps from the
     batched generator; evaluation: a held-out nz^3 box, eps = 1e-6, solve from

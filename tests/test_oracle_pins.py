@@ -167,7 +167,8 @@ def test_P9_polynomial_source_is_integrated_exactly(parabolic):
 
 
 def test_homogeneous_constant_source_closed_form():
-    """I = S (1 - e^-tau) + I0 e^-tau for constant S (north star pin)."""
+    """I = S (1 - e^-tau) + I0 e^-tau for constant S (the closed form of the
+    transfer equation in a homogeneous medium)."""
     chil = np.full(40, 0.37)
     S = np.full(40, 2.0)
     for parabolic in (False, True):
