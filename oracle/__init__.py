@@ -91,7 +91,7 @@ def default_threads() -> int:
 
 
 def directions(ntheta: int, nphi: int):
-    """A1 direction set: (mu, phi, dir (n,3), w), angle index o = i*nphi + j."""
+    """Direction set: (mu, phi, dir (n,3), w), angle index o = i*nphi + j."""
     lib = _load()
     n = ntheta * nphi
     mu, phi, w = np.zeros(n), np.zeros(n), np.zeros(n)
@@ -101,7 +101,7 @@ def directions(ntheta: int, nphi: int):
 
 
 def trace_cart(shape, d, x0: int = 0, y0: int = 0):
-    """A2: voxel indices and chords of the characteristic of direction d from
+    """Tracker: voxel indices and chords of the characteristic of direction d from
     the centre of inflow-face cell (x0, y0). shape = (nz, ny, nx)."""
     lib = _load()
     nz, ny, nx = shape
@@ -137,7 +137,7 @@ def parab_weight(u: float, w: float) -> float:
 
 
 def ray_fs(chil, S, I0: float, parabolic: bool):
-    """A4+A5 along one characteristic: returns (I, E, alpha, beta, gamma)."""
+    """Formal solution along one characteristic: returns (I, E, alpha, beta, gamma)."""
     lib = _load()
     chil, S = _f64(chil), _f64(S)
     K = chil.size
@@ -159,7 +159,7 @@ def _bc_args(shape, bc):
 
 def fs_cart(chi, S, ntheta: int, nphi: int, parabolic: bool = False, bc=None,
             lstar: bool = False, nthreads: int | None = None):
-    """A2-A7: J = Lambda S on the periodic box (and Lambda* as (N,27))."""
+    """J = Lambda S on the periodic box (and Lambda* as (N,27))."""
     lib = _load()
     chi, S = _f64(chi), _f64(S)
     nz, ny, nx = chi.shape
@@ -211,7 +211,7 @@ def fs_cart_voxel(chi, S, ntheta: int, nphi: int, v: int, parabolic: bool = Fals
 
 
 def os_jacobi(lstar, eps, r, max_sweeps: int = 50, tol: float = 1e-3):
-    """A8: Jacobi solve of [1 - L*(1-eps)] dJ = r. Returns (dJ, sweeps)."""
+    """Jacobi solve of [1 - L*(1-eps)] dJ = r. Returns (dJ, sweeps)."""
     lib = _load()
     eps, r = _f64(eps), _f64(r)
     nz, ny, nx = r.shape
@@ -224,7 +224,7 @@ def os_jacobi(lstar, eps, r, max_sweeps: int = 50, tol: float = 1e-3):
 def ali_solve(chi, eps, B, ntheta: int, nphi: int, parabolic: bool = False, bc=None, J0=None,
               tol: float = 1e-13, max_iter: int = 500, max_sweeps: int = 50,
               sweep_tol: float = 1e-3, nthreads: int | None = None):
-    """A8+A9: ALI iteration to rel dJ < tol. Returns (J, iterations, history, lstar)."""
+    """ALI iteration to rel dJ < tol. Returns (J, iterations, history, lstar)."""
     lib = _load()
     chi, eps, B = _f64(chi), _f64(eps), _f64(B)
     nz, ny, nx = chi.shape

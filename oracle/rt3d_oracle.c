@@ -43,7 +43,7 @@
 #endif
 
 /* ---------------------------------------------------------------------------
- * A1. Direction set: mu_i = -1 + (2i+1)/ntheta, phi_j = (2j+1) pi / nphi,
+ * Direction set: mu_i = -1 + (2i+1)/ntheta, phi_j = (2j+1) pi / nphi,
  * d = (sqrt((1-mu)(1+mu)) cos phi, sqrt((1-mu)(1+mu)) sin phi, mu),
  * w = 1/(ntheta nphi). "equally spaced in mu = cos(theta) and phi" (Sec. 3.1).
  * Angle index o = i * nphi + j.
@@ -67,7 +67,7 @@ void orc_directions(int nth, int nph, double *mu, double *phi, double *dir, doub
 }
 
 /* ---------------------------------------------------------------------------
- * A2. Tracker for the Cartesian box periodic in x and y (Sec. 4: "setting up
+ * Tracker for the Cartesian box periodic in x and y (Sec. 4: "setting up
  * the geometric paths through the grid for all solid angles").
  * Start at (x0+1/2, y0+1/2, z_in), z_in = nz if mu < 0 else 0. Crossing
  * parameters along the unit direction: the m-th x plane at (m - 1/2)/|d_x|,
@@ -135,7 +135,7 @@ int orc_kmax_cart(int nx, int ny, int nz, const double *d)
 }
 
 /* ---------------------------------------------------------------------------
- * A4. Exponential integrals of the interval of optical depth u:
+ * Exponential integrals of the interval of optical depth u:
  *   e0 = 1 - exp(-u), e1 = u - e0, e2 = u^2 - 2 e1
  * (Olson & Kunasz 1987; e_n = int_0^u t^n exp(-(u - t)) dt). For u < 1/2 the
  * three are summed from their Taylor series to full FP64 precision, otherwise
@@ -218,8 +218,8 @@ void orc_coef(int parabolic, double u, double w, double *E, double *al, double *
 }
 
 /* ---------------------------------------------------------------------------
- * A4 + A5. Formal solution along one characteristic of K points (Eq. 1
- * integrated along the ray; Listing 1 steps 2-5):
+ * Formal solution along one characteristic of K points (Eq. 1 integrated
+ * along the ray; the per-slot steps of Listing 1):
  *   I_k = E_k I_{k-1} + alpha_k S_{k-1} + beta_k S_k + gamma_k S_{k+1},
  * with u_k = 1/2 (chil[k-1] + chil[k]) (chil[-1] = 0), w_k = u_{k+1},
  * S_{-1} = S_0 (boundary entry point), linear form on the last interval.
@@ -297,7 +297,7 @@ static double orc_bc(int nx, double mu, int x0, int y0, double I_top, const doub
 }
 
 /* ---------------------------------------------------------------------------
- * A2-A7. Formal solution J = Lambda S (Eq. frmsol) on the periodic Cartesian
+ * Formal solution J = Lambda S (Eq. frmsol) on the periodic Cartesian
  * box for all solid angles, and optionally the 27-point Lambda* band:
  *   J_v = sum_Omega w (sum_{k in v} l_k I_k) / (sum_{k in v} l_k)
  *   L*[v][d] = sum_Omega w sum_{k in v} l_k/(sum l) sum_{j in window(k),
@@ -534,7 +534,7 @@ static long orc_nb(int nx, int ny, int nz, long v, int c)
 }
 
 /* ---------------------------------------------------------------------------
- * A8. Operator-splitting linear system of Eq. alo written for the correction
+ * Operator-splitting linear system of Eq. alo written for the correction
  * Delta J = J_new - J_old:  [1 - Lambda*(1 - eps)] Delta J = r, r = J_FS - J_old,
  * solved by Jacobi iteration (Sec. 4, "OS iteration"):
  *   dJ^0 = r / diag,  dJ^{m+1}_v = (r_v + sum_{d != 13} L*[v][d] (1 - eps_{v+d})
@@ -576,7 +576,7 @@ int orc_os_jacobi(int nx, int ny, int nz, const double *lstar, const double *eps
 }
 
 /* ---------------------------------------------------------------------------
- * A8 + A9. ALI iteration (Eqs. alisol, alodef, alo): from J,
+ * ALI iteration (Eqs. alisol, alodef, alo): from J,
  *   S = (1 - eps) J + eps B;  J_FS = Lambda S (Lambda* built in the first
  *   iteration);  r = J_FS - J;  Jacobi solve of [1 - L*(1-eps)] dJ = r;
  *   J += dJ;  rel = max_v |dJ_v| / |J_v|;

@@ -662,7 +662,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     g->sph = d.geometry == RT3D_SPHERICAL;
     if (g->sph) g->per = Periodic{false, false, true};
 
-    // A1: direction set in FP64 on the host (midpoints in mu and phi).
+    // Direction set in FP64 on the host (midpoints in mu and phi, Sec. 3.1).
     const int nO = g->nO;
     g->mu.resize(nO);
     g->wt.resize(nO);

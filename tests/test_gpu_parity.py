@@ -50,7 +50,7 @@ def lstar_err(Lg, Lo):
     return float(np.max(np.abs(Lg - Lo) / scale))
 
 
-# ------------------------------------------------------------ tracer (A2)
+# ------------------------------------------------------------------- tracer
 @pytest.mark.parametrize("n,nth,nph", [((13, 11, 9), 6, 10), ((4, 4, 1), 2, 4),
                                        ((40, 37, 23), 8, 16)])
 def test_template_bit_exact(rt3d, n, nth, nph):
@@ -77,7 +77,7 @@ def test_template_bit_exact_box129(rt3d):
     assert g.info()["segments"] > 2.5e10
 
 
-# ------------------------------------------------ formal solution (A4-A7)
+# ---------------------------------------------------------- formal solution
 CASES = [
     # (n, ntheta, nphi, seed) -- ragged tails: nx*ny not a multiple of 128
     ((17, 13, 11), 4, 8, 1),
@@ -254,7 +254,7 @@ def test_fs_box129_sampled(rt3d):
         assert abs(J[v] - Jv) / abs(Jv) < TOL32, v
 
 
-# ---------------------------------------------------------- OS solve (A8)
+# ----------------------------------------------------------------- OS solve
 def test_os_solve_parity(rt3d):
     rng = np.random.default_rng(2)
     n = (11, 9, 7)
@@ -303,7 +303,7 @@ def test_ali_step_parity(rt3d):
     assert abs(rel - np.max(np.abs(dJo) / np.abs(Jo))) < 1e-9 * rel
 
 
-# ------------------------------------------------- converged solve (A8-A10)
+# ---------------------------------------------------------- converged solve
 def _golden33():
     vals = [float(l) for l in open(os.path.join(HERE, "golden", "box33_fp64_J.txt"))
             if not l.startswith("#")]

@@ -21,7 +21,7 @@ from paper_2102_01734_gb300 import inputs
 mpmath.mp.dps = 40
 
 
-# ----------------------------------------------------------------- A1 angles
+# ------------------------------------------------------------ direction set
 def test_directions_midpoint_grid():
     mu, phi, d, w = oracle.directions(8, 16)
     assert abs(w.sum() - 1.0) < 1e-15
@@ -34,7 +34,7 @@ def test_directions_midpoint_grid():
     assert np.allclose(np.sort(mu), -np.sort(mu)[::-1])
 
 
-# ------------------------------------------------- A4 exponential integrals
+# ---------------------------------------------------- exponential integrals
 def _e012_exact(u):
     u = mpmath.mpf(u)
     e0 = -mpmath.expm1(-u)
@@ -132,7 +132,7 @@ def test_vacuum_interval():
     assert oracle.coef(True, 0.0, 1.0) == (1.0, 0.0, 0.0, 0.0)
 
 
-# --------------------------------------- P9: exactness along a characteristic
+# ------------------------------------------- exactness along a characteristic
 def _analytic_I(tau, I_start, k0, k1, Sfun):
     """I at tau[k1] from I_start at tau[k0]: I0 e^{-dt} + int S e^{-(t1-t)} dt."""
     t0, t1 = mpmath.mpf(tau[k0]), mpmath.mpf(tau[k1])
@@ -142,7 +142,7 @@ def _analytic_I(tau, I_start, k0, k1, Sfun):
 
 
 @pytest.mark.parametrize("parabolic", [False, True])
-def test_P9_polynomial_source_is_integrated_exactly(parabolic):
+def test_polynomial_source_is_integrated_exactly(parabolic):
     rng = np.random.default_rng(7)
     K = 14
     # chi*l per point; the parabolic case stays where the full parabola applies
@@ -178,7 +178,7 @@ def test_homogeneous_constant_source_closed_form():
         assert np.max(np.abs(I - ref) / ref) < 1e-14
 
 
-# ------------------------------------------------------------ A2 the tracer
+# --------------------------------------------------------------- the tracer
 def _brute_trace(shape, d, x0, y0):
     """All plane crossings enumerated and sorted; the cell of every interval
     found from the exact (rational) midpoint of the interval."""
@@ -226,7 +226,7 @@ def test_tracer_against_brute_force(nth, nph):
             assert np.all(ln > 0)
 
 
-def test_P4_chord_sum_per_voxel_is_one_over_mu():
+def test_chord_sum_per_voxel_is_one_over_mu():
     shape = (4, 5, 6)
     nz, ny, nx = shape
     mu, phi, d, w = oracle.directions(6, 8)
@@ -240,7 +240,7 @@ def test_P4_chord_sum_per_voxel_is_one_over_mu():
 
 
 # ----------------------------------------------------------- formal solution
-def test_P1_homogeneous_medium_constant_source():
+def test_homogeneous_medium_constant_source():
     shape = (6, 5, 7)
     chi = np.full(shape, 0.7)
     S = np.full(shape, 2.5)
@@ -249,7 +249,7 @@ def test_P1_homogeneous_medium_constant_source():
         assert np.max(np.abs(J - 2.5)) <= 2.5 * 2e-15
 
 
-def test_P2_lte_slab_closed_form():
+def test_lte_slab_closed_form():
     """S = B = 1, eps = 1, I_top = 0, I_bottom = B: along every point the
     intensity is B (1 - e^{-tau_top}) downwards and B upwards; J is the chord
     weighted average of these closed forms."""
@@ -281,7 +281,7 @@ def test_P2_lte_slab_closed_form():
     assert abs(J[-1].mean() - 0.5) < 0.05  # surface: only the upward half is bright
 
 
-def test_P3_translation_invariance():
+def test_translation_invariance():
     nz, ny, nx = 7, 5, 6
     chi = np.broadcast_to(inputs.vertical_chi(nz)[:, None, None], (nz, ny, nx)).copy()
     S = np.broadcast_to(np.linspace(0.3, 2.0, nz)[:, None, None], chi.shape).copy()
@@ -292,7 +292,7 @@ def test_P3_translation_invariance():
     assert np.max(np.ptp(Lr, axis=1)) < 1e-14
 
 
-def test_P8_linearity():
+def test_linearity():
     rng = np.random.default_rng(3)
     shape = (5, 4, 6)
     chi = 10 ** rng.uniform(-2, 1, shape)
@@ -317,7 +317,7 @@ def test_voxel_route_matches_full_solution():
         assert np.max(np.abs(row - L[v])) <= 1e-14 * np.max(np.abs(row))
 
 
-# ------------------------------------------------------------- A7 Lambda*
+# ---------------------------------------------------------------- Lambda*
 def _band_of(M, shape):
     nz, ny, nx = shape
     N = M.shape[0]
@@ -334,7 +334,7 @@ def _band_of(M, shape):
 
 
 @pytest.mark.parametrize("parabolic", [False, True])
-def test_P5_lstar_equals_band_of_brute_force_lambda(parabolic):
+def test_lstar_equals_band_of_brute_force_lambda(parabolic):
     """9x9x4 box, mu = +-1/2: a characteristic moves < 7 cells sideways, so it
     never re-enters a 3x3x3 neighbourhood and Lambda* is the exact band."""
     rng = np.random.default_rng(11)
@@ -352,7 +352,7 @@ def test_P5_lstar_equals_band_of_brute_force_lambda(parabolic):
     assert np.all(L[z == 0][:, :9] == 0) and np.all(L[z == 3][:, 18:] == 0)
 
 
-# ------------------------------------------------------------ A8 / A9 ALI
+# ----------------------------------------------------------------- the ALI
 def test_os_jacobi_solves_the_band_system():
     rng = np.random.default_rng(2)
     shape = (5, 4, 6)
@@ -383,7 +383,7 @@ def _dense_from_band(L, shape):
 
 
 @pytest.mark.parametrize("parabolic", [False, True])
-def test_P6_ali_converges_to_the_direct_solution(parabolic):
+def test_ali_converges_to_the_direct_solution(parabolic):
     rng = np.random.default_rng(4)
     shape = (5, 4, 4)
     chi = 10 ** rng.uniform(-1, 1.3, shape)
@@ -396,7 +396,7 @@ def test_P6_ali_converges_to_the_direct_solution(parabolic):
     assert np.max(np.abs(J - Jd) / np.abs(Jd)) < 1e-12
 
 
-def test_P6_lambda_iteration_fixed_point():
+def test_lambda_iteration_fixed_point():
     rng = np.random.default_rng(6)
     shape = (4, 3, 4)
     chi = 10 ** rng.uniform(-1, 0.5, shape)
@@ -410,7 +410,7 @@ def test_P6_lambda_iteration_fixed_point():
     assert np.max(np.abs(J - Jd) / Jd) < 1e-12
 
 
-def test_P8_spectral_radius_of_lambda_iteration():
+def test_spectral_radius_of_lambda_iteration():
     """Power iteration on Lambda(1-eps) for a homogeneous slab of vertical
     optical thickness T. Sec. 2.2 quotes lambda_max ~ (1-eps)(1-1/T), an
     estimate that tends to 1 for large T. The fundamental slab mode of the
