@@ -203,9 +203,11 @@ __global__ void __launch_bounds__(256) os_sweep_kernel(int nx, int ny, int nz, c
 }
 
 __global__ void os_finish_kernel(int max_sweeps, double tol, OsState *st) {
-    if (st->done) return;
-    st->done = 1;
-    st->count = max_sweeps;
+    if (!st->done) {
+        st->done = 1;
+        st->count = max_sweeps;
+    }
+    st->sweeps_total += (unsigned long long)st->count;
 }
 
 // J += dJ (dJ = the final sweep buffer); rel = max |dJ| / |J_new|.

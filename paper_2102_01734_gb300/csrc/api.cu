@@ -1352,6 +1352,7 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     rt3d_solve_stats s{};
     g->fs_ms[0] = g->fs_ms[1] = g->fs_ms[2] = 0.0;
     g->launches = 0;
+    TRY(reset_scalar(g, offsetof(OsState, sweeps_total), sizeof(unsigned long long)));
     TRY(load_problem(g, chi, eps, B));
     CK(cudaMemcpyAsync(g->J, J_inout, N * sizeof(double), cudaMemcpyDefault, g->stream));
     FsParams fp;
@@ -1370,6 +1371,12 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
         s.fs32_ms = g->fs_ms[0];
         s.fs64_ms = g->fs_ms[1];
         s.fsff_ms = g->fs_ms[2];
+        {
+            unsigned long long sw = 0;
+            CK(cudaMemcpyAsync(&sw, &g->st->sweeps_total, sizeof sw, cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            s.jacobi_sweeps = (int)std::min<unsigned long long>(sw, (unsigned long long)INT32_MAX);
+        }
         s.launches = g->launches;
         s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         if (stats) *stats = s;
@@ -1479,6 +1486,12 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     s.fs32_ms = g->fs_ms[0];
     s.fs64_ms = g->fs_ms[1];
     s.fsff_ms = g->fs_ms[2];
+    {
+        unsigned long long sw = 0;
+        CK(cudaMemcpyAsync(&sw, &g->st->sweeps_total, sizeof sw, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        s.jacobi_sweeps = (int)std::min<unsigned long long>(sw, (unsigned long long)INT32_MAX);
+    }
     s.launches = g->launches;
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = s;

@@ -139,6 +139,7 @@ struct OsState {
     unsigned long long res;        // max |r|/|J| of a residual
     unsigned long long amax;       // max |x| of a vector
     int changed;                   // content comparison flag
+    unsigned long long sweeps_total;  // sweeps of all OS solves since the last reset
 };
 
 cudaError_t launch_pack(int nx, int ny, int nz, const double *chi, double chi_scale,

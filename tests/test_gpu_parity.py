@@ -324,6 +324,7 @@ def test_solve_box33_matches_golden(rt3d, precision, accel):
     err = np.max(np.abs(J.cpu().numpy() - ref) / ref)
     assert err < 1e-8, (err, st)
     assert st["residual64"] < 1e-8
+    assert st["jacobi_sweeps"] > 0
 
 
 @pytest.mark.parametrize("accel", ["ali", "krylov"])
