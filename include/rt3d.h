@@ -66,10 +66,12 @@ enum {
 enum {
     RT3D_FP64 = 0,             /* formal solution and ALI in FP64 */
     RT3D_FP32_FS_FP64_ALI = 1, /* FP32 formal solution, FP64 ALI/residual, FP64 refinement */
-    RT3D_FP32_FS_FF_REFINE = 2 /* as RT3D_FP32_FS_FP64_ALI, but the refinement residuals
-                                  come from the float-float formal solution
-                                  (rt3d_formal_solution_ff) and only the residual
-                                  that certifies J from an FP64 formal solution */
+    RT3D_FP32_FS_FF_REFINE = 2 /* as RT3D_FP32_FS_FP64_ALI, but the Krylov solve's
+                                  refinement residuals come from the float-float
+                                  formal solution (rt3d_formal_solution_ff) and only
+                                  the residual that certifies J from an FP64 formal
+                                  solution (the plain ALI's defect correction keeps
+                                  FP64 residuals); Cartesian grids only */
 };
 
 typedef struct {
