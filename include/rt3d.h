@@ -75,9 +75,11 @@ enum {
 };
 
 typedef struct {
-    int geometry;     /* RT3D_CARTESIAN_PERIODIC_XY */
-    int n[3];         /* nx, ny, nz: 4 <= nx, ny <= 2047, 1 <= nz <= 1023,
-                         4 nx ny nz < 2^31 */
+    int geometry;     /* RT3D_CARTESIAN_PERIODIC_XY or RT3D_SPHERICAL */
+    int n[3];         /* Cartesian: nx, ny, nz with 4 <= nx, ny <= 2047,
+                         1 <= nz <= 1023; spherical: nr, ntheta, nphi with
+                         nr >= 1, ntheta >= 2, nphi >= 4, each <= 4096;
+                         always 4 n[0] n[1] n[2] < 2^31 */
     int ntheta, nphi; /* direction set: mu_i = -1 + (2i+1)/ntheta,
                          phi_j = (2j+1) pi / nphi, weight 1/(ntheta nphi) */
     int interp;       /* RT3D_LINEAR or RT3D_PARABOLIC source interpolation */
@@ -115,7 +117,9 @@ typedef struct {
     double rel_change;  /* last max_v |dJ_v| / |J_v| */
     double residual64;  /* max_v |J_FS64(S(J))_v - J_v| / |J_v| of the returned J
                            (FP64 formal solution; 0 if not computed) */
-    double est_error;   /* estimated max relative error of the returned J */
+    double est_error;   /* estimated max relative error of the returned J
+                           (-1: not estimated, e.g. the cap was reached before
+                           a refinement residual) */
     double seconds;     /* wall time of the call */
     double fs32_ms;     /* summed device time of the FP32 formal-solution kernels
                            (CUDA events on the grid's stream) */
@@ -206,8 +210,8 @@ rt3d_status rt3d_grid_sph_ray(const rt3d_grid *grid, int angle, int index, int *
                               double *len, int *launch, int *kind);
 
 /* Formal solution J = Lambda S (Eq. frmsol) over all solid angles, in the
- * grid's precision (FP64, or FP32 for RT3D_FP32_FS_FP64_ALI; results are
- * returned as double either way):
+ * grid's precision (FP64, or FP32 for RT3D_FP32_FS_FP64_ALI and
+ * RT3D_FP32_FS_FF_REFINE; results are returned as double either way):
  *   J_v = sum_Omega w (sum_{k in v} l_k I_k) / (sum_{k in v} l_k),
  *   I_k = exp(-dtau) I_{k-1} + alpha S_{k-1} + beta S_k + gamma S_{k+1}.
  * chi > 0 (per unit length) and S: double[N]. J_out: double[N] (written).
@@ -217,12 +221,6 @@ rt3d_status rt3d_grid_sph_ray(const rt3d_grid *grid, int angle, int index, int *
 rt3d_status rt3d_formal_solution(rt3d_grid *grid, const double *chi, const double *S,
                                  const rt3d_bc *bc, double *J_out, double *lstar_out);
 
-/* OS linear system of Eq. alo for the correction dJ = J_new - J_old:
- * [1 - Lambda*(1 - eps)] dJ = r, by Jacobi sweeps (Sec. 4, OS iteration):
- * dJ^0 = r / diag; stops when max|dJ^{m+1} - dJ^m| <= tol * max|dJ^{m+1}|
- * or after max_sweeps (1..256). lstar: double[27][N] as written by
- * rt3d_formal_solution; eps, r, dJ_out: double[N]. sweeps_out (nullable,
- * host) receives the number of sweeps. */
 /* The formal solution without Lambda* in float-float arithmetic (not in the
  * paper: FP64-class accuracy, about 1e-13 relative, on the FP32 pipe; GB300's
  * FP64 rate is about 1/64 of its FP32 rate). Same arguments, layouts and
@@ -233,6 +231,12 @@ rt3d_status rt3d_formal_solution(rt3d_grid *grid, const double *chi, const doubl
 rt3d_status rt3d_formal_solution_ff(rt3d_grid *grid, const double *chi, const double *S,
                                     const rt3d_bc *bc, double *J_out);
 
+/* OS linear system of Eq. alo for the correction dJ = J_new - J_old:
+ * [1 - Lambda*(1 - eps)] dJ = r, by Jacobi sweeps (Sec. 4, OS iteration):
+ * dJ^0 = r / diag; stops when max|dJ^{m+1} - dJ^m| <= tol * max|dJ^{m+1}|
+ * or after max_sweeps (1..256). lstar: double[27][N] as written by
+ * rt3d_formal_solution; eps, r, dJ_out: double[N]. sweeps_out (nullable,
+ * host) receives the number of sweeps. */
 rt3d_status rt3d_os_solve(rt3d_grid *grid, const double *lstar, const double *eps,
                           const double *r, double *dJ_out, int max_sweeps, double tol,
                           int *sweeps_out);
@@ -246,14 +250,23 @@ rt3d_status rt3d_ali_step(rt3d_grid *grid, const double *chi, const double *eps,
                           const double *B, const rt3d_bc *bc, double *J_inout,
                           double *rel_change_out);
 
-/* Iterates the ALI from J_inout until the estimated relative error of J is
- * below tol (the last change times rho/(1-rho), rho the observed contraction
- * of the changes). In RT3D_FP32_FS_FP64_ALI mode: FP32 iterations until the
- * change stagnates, then defect correction with FP64 formal solutions
- * (residual r64 = J_FS64(S(J)) - J, correction from the homogeneous FP32 ALI)
- * until the FP64 residual certifies the result. max_iter caps the ALI
- * iterations (FP32 and FP64 counted together). Returns RT3D_ENOTCONVERGED
- * with J_inout holding the last iterate when the cap is hit. stats: nullable. */
+/* Solves for J from J_inout until the estimated relative error of J is below
+ * tol. chi, eps, B: double[N]; J_inout: double[N] (start, then the result).
+ * RT3D_ACCEL_NONE (the paper's ALI, Eq. alo): iterations until the last
+ * change times rho/(1-rho) (rho the observed contraction) is below tol; in
+ * the mixed precisions FP32 iterations until the change stagnates, then
+ * defect correction with FP64 formal solutions (residual r64 =
+ * J_FS64(S(J)) - J, correction from the homogeneous FP32 ALI) until the FP64
+ * residual certifies the result. RT3D_ACCEL_KRYLOV: refinement rounds, each
+ * a residual r = J_FS(S(J)) - J and one FGMRES cycle on
+ * (1 - Lambda(1-eps)) delta = r preconditioned by the OS solve, J += delta;
+ * the error after a round is estimated as (|delta|/|r| of the previous round)
+ * times the residual, and an FP64 residual meeting tol certifies J (FP32
+ * residuals first in the mixed precisions; float-float ones with
+ * RT3D_FP32_FS_FF_REFINE; FP64 throughout in RT3D_FP64). max_iter caps the
+ * ALI iterations or the FGMRES steps. Returns RT3D_ENOTCONVERGED with
+ * J_inout holding the last iterate when the cap is hit, RT3D_ENUMERIC when a
+ * residual or change is not finite. stats: nullable (host). */
 rt3d_status rt3d_solve(rt3d_grid *grid, const double *chi, const double *eps, const double *B,
                        const rt3d_bc *bc, double *J_inout, double tol, int max_iter,
                        rt3d_solve_stats *stats);
@@ -287,7 +300,10 @@ typedef struct {
  * wavelengths together in FP32 (one captured CUDA graph per iteration,
  * replayed; a wavelength retires on the device when its estimated error is
  * below max(tol, 1e-6) or its changes stagnate); phase 2 refines and certifies
- * every wavelength with the FP64 residual of rt3d_solve's Krylov scheme.
+ * every wavelength with rt3d_solve's Krylov scheme (float-float refinement
+ * residuals with RT3D_FP32_FS_FF_REFINE, an FP64 residual certifying). The
+ * batched formal solution's shape is autotuned on the grid's first batched
+ * call (stats->fs_shape).
  * status_out (nullable, host int[n_lambda]) receives RT3D_OK,
  * RT3D_ENOTCONVERGED or RT3D_ENUMERIC per wavelength. Returns
  * RT3D_ENOTCONVERGED if any wavelength is not certified. Device memory grows
