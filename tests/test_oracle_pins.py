@@ -249,6 +249,18 @@ def test_homogeneous_medium_constant_source():
         assert np.max(np.abs(J - 2.5)) <= 2.5 * 2e-15
 
 
+def test_vacuum_carries_the_boundary_intensities():
+    """chi = 0 everywhere: intensities stay at their boundary values, so J is
+    the direction average 1/2 (I_top + I_bottom) whatever S is (half of the
+    midpoint directions enter at the top, half at the bottom)."""
+    rng = np.random.default_rng(4)
+    shape = (5, 6, 7)
+    S = rng.uniform(0.5, 2.0, shape)
+    for parabolic in (False, True):
+        J = oracle.fs_cart(np.zeros(shape), S, 4, 8, parabolic, bc={"I_top": 0.3, "I_bottom": 1.7})
+        assert np.max(np.abs(J - 1.0)) <= 1e-15
+
+
 def test_lte_slab_closed_form():
     """S = B = 1, eps = 1, I_top = 0, I_bottom = B: along every point the
     intensity is B (1 - e^{-tau_top}) downwards and B upwards; J is the chord
