@@ -216,10 +216,15 @@ __global__ void b_update(int n, double *J, const double *buf0, const double *buf
     bmax_atomic(bad ? __longlong_as_double(0x7ff8000000000000LL) : rel, &bs->rel[l]);
 }
 
+// Predicted further ALI iterations that retire a wavelength to the Krylov
+// refinement (contraction near 1, eps near 0).
+constexpr double kSlowIters = 300.0;
+
 // Per wavelength: record the change, estimate the error from the last kHist
 // changes, retire when converged (state 1), stagnated at the rounding floor
-// of the formal solution (state 2), failed (state 3: NaN) or out of
-// iterations (state 4).
+// of the formal solution or contracting so slowly that more than kSlowIters
+// further iterations are predicted (state 2: both go to the Krylov
+// refinement), failed (state 3: NaN) or out of iterations (state 4).
 __global__ void b_retire(int nl, double tol, int max_iter, BatchState *bs) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nl || !bs->active[l]) return;
@@ -246,6 +251,11 @@ __global__ void b_retire(int nl, double tol, int max_iter, BatchState *bs) {
         bs->state[l] = 1;
     } else if (it >= kHist && rel > 0.7 * h[it % kHist] && rel < 1e-2) {
         bs->active[l] = 0;  // no decrease over the window: rounding floor
+        bs->state[l] = 2;
+    } else if (it >= kHist && rho > 0.0 && log(tol / est) / log(rho) > kSlowIters) {
+        // slow contraction (eps near 0): more than kSlowIters further ALI
+        // iterations predicted; the Krylov refinement takes it from here
+        bs->active[l] = 0;
         bs->state[l] = 2;
     } else if (it >= max_iter) {
         bs->active[l] = 0;
