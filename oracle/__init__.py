@@ -57,6 +57,11 @@ def _load():
         lib.orc_fs_cart_voxel.restype = c_int
         lib.orc_os_jacobi.argtypes = [c_int, c_int, c_int, _dp, _dp, _dp, _dp, c_int, c_double]
         lib.orc_os_jacobi.restype = c_int
+        lib.orc_os_gauss_seidel.argtypes = [c_int, c_int, c_int, _dp, _dp, _dp, _dp, c_int,
+                                            c_double, c_int]
+        lib.orc_os_gauss_seidel.restype = c_int
+        lib.orc_os_bicgstab.argtypes = [c_int, c_int, c_int, _dp, _dp, _dp, _dp, c_int, c_double]
+        lib.orc_os_bicgstab.restype = c_int
         lib.orc_ali_solve.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp, _dp,
                                       c_double, _dp, c_double, _dp, _dp, c_double, c_int, c_int,
                                       c_double, c_int, _dp, _dp]
@@ -219,6 +224,32 @@ def os_jacobi(lstar, eps, r, max_sweeps: int = 50, tol: float = 1e-3):
     dJ = np.zeros(r.shape)
     m = lib.orc_os_jacobi(nx, ny, nz, _ptr(L), _ptr(eps), _ptr(r), _ptr(dJ), max_sweeps, tol)
     return dJ, m
+
+
+def os_gauss_seidel(lstar, eps, r, max_sweeps: int = 50, tol: float = 1e-3,
+                    colored: bool = False):
+    """Gauss-Seidel solve of [1 - L*(1-eps)] dJ = r (index order, or eight
+    parity colors). Returns (dJ, sweeps)."""
+    lib = _load()
+    eps, r = _f64(eps), _f64(r)
+    nz, ny, nx = r.shape
+    L = _f64(lstar)
+    dJ = np.zeros(r.shape)
+    m = lib.orc_os_gauss_seidel(nx, ny, nz, _ptr(L), _ptr(eps), _ptr(r), _ptr(dJ), max_sweeps,
+                                tol, int(colored))
+    return dJ, m
+
+
+def os_bicgstab(lstar, eps, r, max_iter: int = 200, tol: float = 1e-10):
+    """BiCGStab solve of [1 - L*(1-eps)] dJ = r from 0. Returns (dJ, iterations;
+    negative on a breakdown)."""
+    lib = _load()
+    eps, r = _f64(eps), _f64(r)
+    nz, ny, nx = r.shape
+    L = _f64(lstar)
+    dJ = np.zeros(r.shape)
+    k = lib.orc_os_bicgstab(nx, ny, nz, _ptr(L), _ptr(eps), _ptr(r), _ptr(dJ), max_iter, tol)
+    return dJ, k
 
 
 def ali_solve(chi, eps, B, ntheta: int, nphi: int, parabolic: bool = False, bc=None, J0=None,

@@ -576,6 +576,137 @@ int orc_os_jacobi(int nx, int ny, int nz, const double *lstar, const double *eps
 }
 
 /* ---------------------------------------------------------------------------
+ * Other solvers of the same OS system (the paper names Gauss-Seidel and
+ * BiCGStab OS solvers besides Jacobi, Sec. 4), with the matrix
+ *   A[v][v] = 1 - L*[v][13] (1 - eps_v),  A[v][u] = -L*[v][d] (1 - eps_u).
+ *
+ * Gauss-Seidel, colored = 0: voxels in index order, each update using the
+ * newest values. colored = 1: eight colors by the parities of (x, y, z),
+ * swept in order c = px + 2 py + 4 pz; within a color every update reads the
+ * values from before that color's sweep (on a 27-point stencil two voxels of
+ * one color are neighbours only across a periodic wrap of odd length).
+ * Starts from dJ^0 = r / diag; the stop test of orc_os_jacobi. Returns the
+ * sweeps done.
+ * ------------------------------------------------------------------------- */
+static double orc_os_row(int nx, int ny, int nz, const double *lstar, const double *eps,
+                         const double *r, const double *x, long v)
+{
+    double s = r[v];
+    for (int c = 0; c < 27; c++) {
+        if (c == 13) continue;
+        long u = orc_nb(nx, ny, nz, v, c);
+        if (u < 0) continue;
+        s += lstar[27 * v + c] * (1.0 - eps[u]) * x[u];
+    }
+    return s / (1.0 - lstar[27 * v + 13] * (1.0 - eps[v]));
+}
+
+int orc_os_gauss_seidel(int nx, int ny, int nz, const double *lstar, const double *eps,
+                        const double *r, double *dJ, int max_sweeps, double tol, int colored)
+{
+    const long N = (long)nx * ny * nz;
+    double *old = malloc(sizeof(double) * N);
+    double *snap = malloc(sizeof(double) * N);
+    for (long v = 0; v < N; v++) dJ[v] = r[v] / (1.0 - lstar[27 * v + 13] * (1.0 - eps[v]));
+    int m = 0;
+    while (m < max_sweeps) {
+        memcpy(old, dJ, sizeof(double) * N);
+        if (!colored) {
+            for (long v = 0; v < N; v++) dJ[v] = orc_os_row(nx, ny, nz, lstar, eps, r, dJ, v);
+        } else {
+            for (int col = 0; col < 8; col++) {
+                memcpy(snap, dJ, sizeof(double) * N);
+                for (long v = 0; v < N; v++) {
+                    int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long)nx * ny));
+                    if ((x & 1) + 2 * (y & 1) + 4 * (z & 1) != col) continue;
+                    dJ[v] = orc_os_row(nx, ny, nz, lstar, eps, r, snap, v);
+                }
+            }
+        }
+        double dmax = 0.0, jmax = 0.0;
+        for (long v = 0; v < N; v++) {
+            double df = fabs(dJ[v] - old[v]);
+            if (df > dmax) dmax = df;
+            if (fabs(dJ[v]) > jmax) jmax = fabs(dJ[v]);
+        }
+        m++;
+        if (dmax <= tol * jmax) break;
+    }
+    free(old);
+    free(snap);
+    return m;
+}
+
+/* A x for the OS matrix above. */
+static void orc_os_apply(int nx, int ny, int nz, const double *lstar, const double *eps,
+                         const double *x, double *y)
+{
+    const long N = (long)nx * ny * nz;
+    for (long v = 0; v < N; v++) {
+        double s = (1.0 - lstar[27 * v + 13] * (1.0 - eps[v])) * x[v];
+        for (int c = 0; c < 27; c++) {
+            if (c == 13) continue;
+            long u = orc_nb(nx, ny, nz, v, c);
+            if (u < 0) continue;
+            s -= lstar[27 * v + c] * (1.0 - eps[u]) * x[u];
+        }
+        y[v] = s;
+    }
+}
+
+static double orc_dot(long n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (long i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+/* BiCGStab (van der Vorst 1992) on A dJ = r from dJ = 0, without a
+ * preconditioner; stops when ||r_k||_2 <= tol ||r||_2 or after max_iter
+ * iterations (two products with A each). Returns the iterations done, or
+ * -(iterations) on a breakdown (rho or omega zero). */
+int orc_os_bicgstab(int nx, int ny, int nz, const double *lstar, const double *eps,
+                    const double *r, double *dJ, int max_iter, double tol)
+{
+    const long N = (long)nx * ny * nz;
+    double *res = malloc(sizeof(double) * N), *rh = malloc(sizeof(double) * N);
+    double *p = calloc(N, sizeof(double)), *vv = calloc(N, sizeof(double));
+    double *sv = malloc(sizeof(double) * N), *t = malloc(sizeof(double) * N);
+    for (long i = 0; i < N; i++) {
+        dJ[i] = 0.0;
+        res[i] = r[i];
+        rh[i] = r[i];
+    }
+    const double nr0 = sqrt(orc_dot(N, r, r));
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    int k = 0, status = 0;
+    if (!(nr0 > 0.0)) goto done;
+    while (k < max_iter) {
+        const double rho1 = orc_dot(N, rh, res);
+        if (rho1 == 0.0) { status = -1; break; }
+        const double beta = (rho1 / rho) * (alpha / omega);
+        for (long i = 0; i < N; i++) p[i] = res[i] + beta * (p[i] - omega * vv[i]);
+        orc_os_apply(nx, ny, nz, lstar, eps, p, vv);
+        alpha = rho1 / orc_dot(N, rh, vv);
+        for (long i = 0; i < N; i++) sv[i] = res[i] - alpha * vv[i];
+        orc_os_apply(nx, ny, nz, lstar, eps, sv, t);
+        const double tt = orc_dot(N, t, t);
+        omega = tt > 0.0 ? orc_dot(N, t, sv) / tt : 0.0;
+        for (long i = 0; i < N; i++) {
+            dJ[i] += alpha * p[i] + omega * sv[i];
+            res[i] = sv[i] - omega * t[i];
+        }
+        rho = rho1;
+        k++;
+        if (sqrt(orc_dot(N, res, res)) <= tol * nr0) break;
+        if (omega == 0.0) { status = -1; break; }
+    }
+done:
+    free(res); free(rh); free(p); free(vv); free(sv); free(t);
+    return status < 0 ? -k : k;
+}
+
+/* ---------------------------------------------------------------------------
  * ALI iteration (Eqs. alisol, alodef, alo): from J,
  *   S = (1 - eps) J + eps B;  J_FS = Lambda S (Lambda* built in the first
  *   iteration);  r = J_FS - J;  Jacobi solve of [1 - L*(1-eps)] dJ = r;

@@ -379,6 +379,74 @@ def test_os_jacobi_solves_the_band_system():
     assert np.max(np.abs(dJ.reshape(-1) - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
+def _os_band_system(seed, shape=(5, 4, 6), eps_range=(-4, -1)):
+    rng = np.random.default_rng(seed)
+    chi = 10 ** rng.uniform(-1, 1, shape)
+    _, L = oracle.fs_cart(chi, np.ones(shape), 4, 6, False, lstar=True)
+    eps = 10 ** rng.uniform(*eps_range, shape)
+    r = rng.standard_normal(shape)
+    A = np.eye(chi.size) - _dense_from_band(L, shape) * (1 - eps.reshape(-1))[None, :]
+    return L, eps, r, np.linalg.solve(A, r.reshape(-1))
+
+
+@pytest.mark.parametrize("colored", [False, True])
+def test_os_gauss_seidel_solves_the_band_system(colored):
+    L, eps, r, ref = _os_band_system(4)
+    dJ, m = oracle.os_gauss_seidel(L, eps, r, max_sweeps=5000, tol=1e-15, colored=colored)
+    assert 0 < m < 5000
+    assert np.max(np.abs(dJ.reshape(-1) - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_os_gauss_seidel_takes_fewer_sweeps_than_jacobi():
+    # For a diagonally dominant M-matrix-like system the Gauss-Seidel spectral
+    # radius is below the Jacobi one (Stein-Rosenberg), so at the same stop
+    # test it needs fewer sweeps; the eight-color order is a Gauss-Seidel
+    # order too.
+    L, eps, r, ref = _os_band_system(5)
+    _, mj = oracle.os_jacobi(L, eps, r, max_sweeps=5000, tol=1e-10)
+    _, mg = oracle.os_gauss_seidel(L, eps, r, max_sweeps=5000, tol=1e-10, colored=False)
+    _, mc = oracle.os_gauss_seidel(L, eps, r, max_sweeps=5000, tol=1e-10, colored=True)
+    assert mg < mj and mc < mj
+
+
+def test_os_gauss_seidel_one_sweep_by_hand():
+    # One lexicographic sweep on a tiny box, written out voxel by voxel from
+    # the definition dJ_v = (r_v + sum_{u != v} L*[v][u](1-eps_u) dJ_u) / A_vv
+    # with the voxels already visited taking their new values.
+    rng = np.random.default_rng(6)
+    shape = (3, 3, 3)
+    chi = 10 ** rng.uniform(-1, 1, shape)
+    _, L = oracle.fs_cart(chi, np.ones(shape), 2, 4, False, lstar=True)
+    eps = 10 ** rng.uniform(-3, -1, shape)
+    r = rng.standard_normal(shape)
+    M = _dense_from_band(L, shape) * (1 - eps.reshape(-1))[None, :]
+    n = M.shape[0]
+    diag = 1 - np.diag(M)
+    x = r.reshape(-1) / diag
+    for v in range(n):
+        x[v] = (r.reshape(-1)[v] + sum(M[v, u] * x[u] for u in range(n) if u != v)) / diag[v]
+    dJ, m = oracle.os_gauss_seidel(L, eps, r, max_sweeps=1, tol=0.0, colored=False)
+    assert m == 1
+    assert np.max(np.abs(dJ.reshape(-1) - x)) < 1e-14 * np.max(np.abs(x))
+
+
+def test_os_bicgstab_solves_the_band_system():
+    L, eps, r, ref = _os_band_system(7, eps_range=(-6, -3))
+    dJ, k = oracle.os_bicgstab(L, eps, r, max_iter=500, tol=1e-13)
+    assert 0 < k < 500
+    assert np.max(np.abs(dJ.reshape(-1) - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+def test_os_bicgstab_exact_on_a_diagonal_system():
+    # eps = 1 removes every coupling (A = I): the first step is exact and the
+    # stabilising half-step has nothing left to do.
+    L, _, r, _ = _os_band_system(8)
+    eps = np.ones(r.shape)
+    dJ, k = oracle.os_bicgstab(L, eps, r, max_iter=50, tol=1e-14)
+    assert k == 1
+    assert np.max(np.abs(dJ - r)) < 1e-14 * np.max(np.abs(r))
+
+
 def _dense_from_band(L, shape):
     nz, ny, nx = shape
     N = L.shape[0]
