@@ -8,7 +8,9 @@ The C library (``rt3d_oracle.c``) holds the arithmetic; this module only
 marshals numpy arrays, plus two plain linear-algebra helpers used as pins:
 the brute-force Lambda matrix built column by column from the formal solution
 (Eq. frmsol, J = Lambda S) and the direct dense solve of the scattering
-problem that the ALI iteration (Eqs. alisol, alo) converges to.
+problem that the ALI iteration (Eqs. alisol, alo) converges to. The line
+transfer functions (profile-averaged mean intensity, Sec. 2) compose the C
+routines per wavelength in plain numpy.
 
 Array convention: grids are numpy arrays of shape (nz, ny, nx), x fastest,
 so the flat index is v = x + nx (y + ny z). Lambda* is returned as (N, 27)
@@ -342,3 +344,82 @@ def fs_sph(chi, S, B, ntheta, nphi, parabolic=False, I_out=0.0, I_irr=0.0, lstar
     if err:
         raise RuntimeError(f"spherical formal solution failed ({err})")
     return (J, L) if lstar else J
+
+
+# ------------------------------------------------------------ line transfer
+# Sec. 2 (with Eq. alisol): for a spectral line the source function is shared
+# by the wavelengths l of the line, S = (1 - eps) Jbar + eps B, and couples to
+# the radiation field through the profile-averaged mean intensity
+# Jbar = int J_l phi_l dl, here the quadrature sum Jbar = sum_l wphi[l] J_l
+# (wphi: quadrature weight times profile, summing to 1). Wavelength l sees the
+# opacity scale[l] * chi. The OS step of Eq. alo then uses the profile-averaged
+# band Lbar* = sum_l wphi[l] Lambda*_l.
+
+def line_lambda_star(chi, scale, wphi, ntheta: int, nphi: int, parabolic: bool = False):
+    """Lbar* = sum_l wphi[l] Lambda*_l as (N, 27)."""
+    chi = _f64(chi)
+    L = np.zeros((chi.size, 27))
+    for s_l, w_l in zip(scale, wphi):
+        _, Ll = fs_cart(chi * float(s_l), np.ones(chi.shape), ntheta, nphi, parabolic,
+                        lstar=True)
+        L += float(w_l) * Ll
+    return L
+
+
+def line_fs(chi, scale, wphi, S, ntheta: int, nphi: int, parabolic: bool = False, bc=None):
+    """Jbar = sum_l wphi[l] Lambda_l S (+ the boundary terms of each wavelength)."""
+    chi = _f64(chi)
+    J = np.zeros(chi.shape)
+    for s_l, w_l in zip(scale, wphi):
+        J += float(w_l) * fs_cart(chi * float(s_l), S, ntheta, nphi, parabolic, bc)
+    return J
+
+
+def line_ali_step(chi, scale, wphi, eps, B, J, ntheta: int, nphi: int,
+                  parabolic: bool = False, bc=None, lbar=None, max_sweeps: int = 50,
+                  sweep_tol: float = 1e-3):
+    """One ALI iteration of the line problem: S from Jbar, Jbar_FS, the Jacobi
+    OS solve of [1 - Lbar*(1-eps)] dJ = Jbar_FS - Jbar, Jbar += dJ. Returns
+    (Jbar_new, rel, Lbar*) with rel = max |dJ| / |Jbar_new| over dJ != 0."""
+    eps, B, J = _f64(eps), _f64(B), _f64(J)
+    if lbar is None:
+        lbar = line_lambda_star(chi, scale, wphi, ntheta, nphi, parabolic)
+    S = (1.0 - eps) * J + eps * B
+    Jfs = line_fs(chi, scale, wphi, S, ntheta, nphi, parabolic, bc)
+    dJ, _ = os_jacobi(lbar, eps, Jfs - J, max_sweeps, sweep_tol)
+    Jn = J + dJ
+    nz = dJ != 0.0
+    rel = float(np.max(np.abs(dJ[nz]) / np.abs(Jn[nz]))) if nz.any() else 0.0
+    return Jn, rel, lbar
+
+
+def line_ali_solve(chi, scale, wphi, eps, B, ntheta: int, nphi: int, parabolic: bool = False,
+                   bc=None, J0=None, tol: float = 1e-13, max_iter: int = 500):
+    """Line ALI to rel < tol from J0 (default 0). Returns (Jbar, iterations;
+    negative if not converged)."""
+    J = np.zeros(np.shape(chi)) if J0 is None else _f64(J0).copy()
+    lbar = line_lambda_star(chi, scale, wphi, ntheta, nphi, parabolic)
+    for it in range(1, max_iter + 1):
+        J, rel, _ = line_ali_step(chi, scale, wphi, eps, B, J, ntheta, nphi, parabolic, bc,
+                                  lbar)
+        if not np.isfinite(rel):
+            raise RuntimeError("oracle line ALI: non-finite Jbar")
+        if rel < tol:
+            return J, it
+    return J, -max_iter
+
+
+def line_direct_solve(chi, scale, wphi, eps, B, ntheta: int, nphi: int,
+                      parabolic: bool = False, bc=None):
+    """Fixed point of the line problem by a dense solve of
+    (1 - Lbar (1-eps)) Jbar = Lbar(eps B) + Jbar_bc, Lbar = sum_l wphi[l] Lambda_l
+    built column by column."""
+    chi = _f64(chi)
+    eps_f, B_f = _f64(eps).reshape(-1), _f64(B).reshape(-1)
+    M = np.zeros((chi.size, chi.size))
+    for s_l, w_l in zip(scale, wphi):
+        M += float(w_l) * lambda_matrix(chi * float(s_l), ntheta, nphi, parabolic)
+    Jbc = line_fs(chi, scale, wphi, np.zeros(chi.shape), ntheta, nphi, parabolic, bc)
+    rhs = M @ (eps_f * B_f) + Jbc.reshape(-1)
+    A = np.eye(chi.size) - M * (1.0 - eps_f)[None, :]
+    return np.linalg.solve(A, rhs).reshape(chi.shape)

@@ -25,6 +25,13 @@ dataset is involved):
   boundary: I = B leaving the core, no incoming intensity at the outer sphere
   except an irradiation I_irr (in units of B) from the side x > 0.
 
+* ``line_profile(nl, ...)``: the wavelengths of one spectral line for the
+  line-transfer solve (profile-averaged mean intensity, Sec. 2): nl points
+  x_l equally spaced in [-xmax, xmax] Doppler widths, opacity scale
+  strength * exp(-x_l^2) (a Doppler profile, 1 at line centre), and
+  weights wphi_l = trapezoid weight * exp(-x_l^2) / sqrt(pi), normalised to
+  sum 1 (the quadrature of int phi dx = 1 on the sampled band).
+
 Cartesian arrays have shape (nz, ny, nx), x fastest; spherical ones
 (nphi, ntheta, nr), r fastest.
 """
@@ -107,3 +114,16 @@ def batched_wavelengths(nlambda: int, seed: int = 3):
     eps = 10.0 ** rng.uniform(-8.0, -1.0, nlambda)
     scale = 10.0 ** rng.uniform(-3.0, 3.0, nlambda)
     return eps, scale
+
+
+def line_profile(nl: int, xmax: float = 3.0, strength: float = 1.0):
+    """(scale, wphi) of nl wavelengths across a Doppler line profile."""
+    x = np.linspace(-xmax, xmax, nl) if nl > 1 else np.zeros(1)
+    phi = np.exp(-x * x) / np.sqrt(np.pi)
+    w = np.full(nl, 2.0 * xmax / max(nl - 1, 1))
+    if nl > 1:
+        w[0] *= 0.5
+        w[-1] *= 0.5
+    wphi = w * phi
+    wphi /= wphi.sum()
+    return strength * np.exp(-x * x), wphi

@@ -1,0 +1,87 @@
+"""Line transfer: the profile-averaged mean intensity of Sec. 2.
+
+The wavelengths of a line share S = (1 - eps) Jbar + eps B with
+Jbar = sum_l wphi[l] J_l; wavelength l sees the opacity scale[l] * chi.
+
+CPU tests pin the oracle (against the continuum ALI it must reduce to and
+against the dense solve of the line problem); GPU tests compare the C ABI's
+line solve with the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_01734_gb300 import inputs
+
+
+def _box(n, eps, seed):
+    chi, epsa, B, bc = inputs.cartesian_config(n, eps, seed=seed)
+    return chi, epsa, B, bc
+
+
+def test_line_profile_quadrature():
+    scale, wphi = inputs.line_profile(9, xmax=3.0, strength=2.0)
+    assert abs(wphi.sum() - 1.0) < 1e-15
+    assert np.allclose(wphi, wphi[::-1]) and np.allclose(scale, scale[::-1])
+    assert scale[4] == 2.0 and np.argmax(wphi) == 4
+    assert abs(scale[0] / 2.0 - np.exp(-9.0)) < 1e-18
+
+
+def test_line_single_wavelength_is_the_continuum_ali():
+    chi, eps, B, bc = _box((5, 4, 6), 1e-2, 2)
+    Jc, itc, _, _ = oracle.ali_solve(chi, eps, B, 2, 4, True, bc, tol=1e-12, max_iter=2000)
+    Jl, itl = oracle.line_ali_solve(chi, [1.0], [1.0], eps, B, 2, 4, True, bc, tol=1e-12,
+                                    max_iter=2000)
+    assert itc > 0 and itl == itc
+    assert np.max(np.abs(Jl - Jc) / np.abs(Jc)) < 1e-13
+
+
+def test_line_equal_opacities_reduce_to_the_continuum():
+    # all wavelengths see the same opacity: Jbar is the continuum J whatever
+    # the weights
+    chi, eps, B, bc = _box((5, 4, 6), 1e-2, 3)
+    Jc = oracle.direct_solve(chi, eps, B, 2, 4, False, bc)
+    Jl = oracle.line_direct_solve(chi, [1.0, 1.0, 1.0], [0.2, 0.5, 0.3], eps, B, 2, 4, False,
+                                  bc)
+    assert np.max(np.abs(Jl - Jc) / np.abs(Jc)) < 1e-12
+
+
+def test_line_duplicate_wavelengths_merge():
+    chi, eps, B, bc = _box((5, 4, 6), 1e-2, 4)
+    S = (1 - eps) * B + eps * B
+    a = oracle.line_fs(chi, [1.0, 0.1, 0.1], [0.5, 0.2, 0.3], S, 2, 4, True, bc)
+    b = oracle.line_fs(chi, [1.0, 0.1], [0.5, 0.5], S, 2, 4, True, bc)
+    assert np.max(np.abs(a - b) / np.abs(b)) < 1e-14
+
+
+@pytest.mark.parametrize("parabolic", [False, True])
+def test_line_ali_converges_to_the_dense_solve(parabolic):
+    chi, eps, B, bc = _box((5, 4, 6), 1e-2, 5)
+    scale, wphi = inputs.line_profile(5, xmax=2.5, strength=3.0)
+    Jx = oracle.line_direct_solve(chi, scale, wphi, eps, B, 2, 4, parabolic, bc)
+    Jl, it = oracle.line_ali_solve(chi, scale, wphi, eps, B, 2, 4, parabolic, bc, tol=1e-13,
+                                   max_iter=3000)
+    assert it > 0
+    assert np.max(np.abs(Jl - Jx) / np.abs(Jx)) < 1e-10
+    # the wings (optically thin) leave Jbar far from the continuum solution
+    Jc = oracle.direct_solve(chi * 3.0, eps, B, 2, 4, parabolic, bc)
+    assert np.max(np.abs(Jl - Jc) / np.abs(Jc)) > 1e-3
+
+
+def test_line_lambda_star_is_the_band_of_the_averaged_lambda():
+    chi, _, _, _ = _box((9, 9, 4), 1e-2, 6)
+    scale, wphi = inputs.line_profile(3, xmax=2.0)
+    Lb = oracle.line_lambda_star(chi, scale, wphi, 2, 4, False)
+    M = sum(w * oracle.lambda_matrix(chi * s, 2, 4, False) for s, w in zip(scale, wphi))
+    nz, ny, nx = chi.shape
+    for v in range(0, chi.size, 7):
+        z, rem = divmod(v, nx * ny)
+        y, x = divmod(rem, nx)
+        for d in range(27):
+            dz, dy, dx = d // 9 - 1, (d // 3) % 3 - 1, d % 3 - 1
+            zz = z + dz
+            if not 0 <= zz < nz:
+                assert Lb[v, d] == 0.0
+                continue
+            u = zz * nx * ny + ((y + dy) % ny) * nx + (x + dx) % nx
+            assert abs(Lb[v, d] - M[v, u]) < 1e-12 * np.max(np.abs(M[v]))
