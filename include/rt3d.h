@@ -313,6 +313,51 @@ rt3d_status rt3d_solve_batched(rt3d_grid *grid, int nlambda, const double *chi,
                                double *J_inout, double tol, int max_iter, int *status_out,
                                rt3d_batch_stats *stats);
 
+typedef struct {
+    int iterations;         /* line ALI iterations done */
+    int fs_lambda;          /* single-wavelength FP64 formal solutions done (those of
+                               the first iteration also build Lambda*) */
+    int jacobi_sweeps;      /* Jacobi sweeps of all OS solves */
+    double rel_change;      /* last max_v |dJbar_v| / |Jbar_v| */
+    double est_error;       /* rel_change * rho / (1 - rho), rho the observed
+                               contraction (-1 before the second iteration) */
+    double seconds;         /* wall time of the call */
+    double fs64_ms;         /* summed device time of the formal-solution kernels */
+    long long launches;     /* kernels launched by the call */
+} rt3d_line_stats;
+
+/* Line transfer (Sec. 2, with Eq. alisol: the mean intensity averaged over
+ * the line profile, Jbar = int J_lambda phi_lambda dlambda). nlambda
+ * wavelengths of one spectral line share the source function
+ *   S = (1 - eps) Jbar + eps B,   Jbar = sum_l wphi[l] J_l,
+ * where J_l is the formal solution (Eq. frmsol) with the opacity
+ * scale[l] * chi and the boundary intensities bc (the same at every
+ * wavelength). wphi[l] is the quadrature weight times the profile value
+ * (normally summing to 1). Iterates the ALI of Eq. alo with the
+ * profile-averaged band Lbar* = sum_l wphi[l] Lambda*_l, built in the call's
+ * first iteration:
+ *   Jbar_FS = sum_l wphi[l] Lambda_l S;  Jacobi solve (<= 50 sweeps,
+ *   relative tolerance 1e-3) of [1 - Lbar*(1 - eps)] dJ = Jbar_FS - Jbar;
+ *   Jbar += dJ,
+ * until the last change times rho/(1 - rho) (rho the observed contraction,
+ * from the second iteration on) is below tol, or for max_iter iterations
+ * (max_iter = 1: exactly one iteration, returning RT3D_ENOTCONVERGED). The
+ * formal solutions run in FP64 on every grid precision (the OS coefficients
+ * follow the grid's precision, which changes only the convergence rate).
+ * chi, eps, B: double[N] (host or device); scale, wphi: HOST double[nlambda]
+ * with scale[l] > 0 and wphi[l] >= 0, finite, sum of wphi > 0;
+ * 1 <= nlambda <= 65536;
+ * Jbar_inout: double[N] (start, then the result). Cartesian grids only
+ * (RT3D_EINVAL for a spherical grid). The call leaves the line's band in the
+ * grid: the next rt3d_ali_step or rt3d_solve rebuilds the continuum Lambda*.
+ * The first call allocates 28 N + 28 doubles. Returns RT3D_ENOTCONVERGED
+ * with Jbar_inout holding the last iterate when max_iter is reached,
+ * RT3D_ENUMERIC when a change is not finite. stats: nullable (host). */
+rt3d_status rt3d_line_solve(rt3d_grid *grid, int nlambda, const double *chi,
+                            const double *scale, const double *wphi, const double *eps,
+                            const double *B, const rt3d_bc *bc, double *Jbar_inout,
+                            double tol, int max_iter, rt3d_line_stats *stats);
+
 /* Allocation-free Jacobi OS solve. No counterpart in the paper: this is a
  * library service for callers that cannot allocate device memory, such as a
  * host application whose device memory is entirely pre-reserved by its own

@@ -145,6 +145,15 @@ struct rt3d_grid {
     FsShape bfs_shape{0, 0, 0, 0};  // batched FS shape (block 0: not tuned)
     float bfs_tune_ms[RT3D_FS_TUNE_SHAPES] = {};
 
+    // line-transfer workspace (allocated on first use): the profile-averaged
+    // Lambda* band [27][N] and formal solution [N], a device table of the
+    // vectors they accumulate ({Jfs, Lambda* plane 0..26}) and the negated
+    // profile weights (-wphi[l], for multi_axpy's w -= c V)
+    double *lbar = nullptr, *jbar_fs = nullptr;
+    double **lptr = nullptr;
+    double *lcoef = nullptr;
+    int lcoef_cap = 0;
+
     // instrumentation: formal-solution kernel time (CUDA events on the
     // grid's stream) and kernels launched
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1143,6 +1152,68 @@ rt3d_status batch_setup(rt3d_grid *g, int nl) {
     return RT3D_OK;
 }
 
+// Line-transfer workspace (allocated on first use; the weight buffer grows to
+// the largest nl seen, the smaller one staying allocated until destroy) and
+// the upload of the negated weights -wphi[l].
+rt3d_status line_setup(rt3d_grid *g, const std::vector<double> &negw) {
+    const size_t N = (size_t)g->N;
+    const int nl = (int)negw.size();
+    if (!g->lbar) {
+        TRY(g->alloc(&g->lbar, 27 * N));
+        TRY(g->alloc(&g->jbar_fs, N));
+        TRY(g->alloc(&g->lptr, 28));
+        std::vector<double *> tab(28);
+        tab[0] = g->Jfs;
+        for (int d = 0; d < 27; ++d) tab[1 + d] = g->lstar + (size_t)d * N;
+        CK(cudaMemcpyAsync(g->lptr, tab.data(), sizeof(double *) * 28, cudaMemcpyHostToDevice,
+                           g->stream));
+        CK(cudaStreamSynchronize(g->stream));  // tab is host memory of this frame
+    }
+    if (nl > g->lcoef_cap) {
+        TRY(g->alloc(&g->lcoef, (size_t)nl));
+        g->lcoef_cap = nl;
+    }
+    CK(cudaMemcpyAsync(g->lcoef, negw.data(), sizeof(double) * nl, cudaMemcpyHostToDevice,
+                       g->stream));
+    CK(cudaStreamSynchronize(g->stream));  // negw is the caller's host vector
+    return RT3D_OK;
+}
+
+// One ALI iteration of the line problem on g->J (= Jbar): for every
+// wavelength l, (chi scale[l], S) packed with S = (1 - eps) Jbar + eps B, its
+// FP64 formal solution added into jbar_fs with weight wphi[l] (and, when
+// build, its Lambda* band into lbar); then the OS solve with the averaged band
+// and Jbar += dJ. *rel = max |dJ| / |Jbar_new|.
+rt3d_status line_iteration(rt3d_grid *g, const FsParams &fp, const std::vector<double> &scale,
+                           bool build, double *rel, int *fs_count) {
+    const size_t N = (size_t)g->N;
+    const int n = (int)N;
+    CK(cudaMemsetAsync(g->jbar_fs, 0, sizeof(double) * N, g->stream));
+    if (build) CK(cudaMemsetAsync(g->lbar, 0, sizeof(double) * 27 * N, g->stream));
+    for (int l = 0; l < (int)scale.size(); ++l) {
+        CKL(launch_pack(g->nx, g->ny, g->nz, g->chi, scale[l], g->chi /*S placeholder*/,
+                        g->chiS64, true, g->stream));
+        CKL(launch_source(g->nx, g->ny, g->nz, g->J, g->eps, g->B, g->chiS64, true, false,
+                          g->stream));
+        TRY(run_fs(g, fp, true, build));
+        ++*fs_count;
+        // jbar_fs -= (-wphi[l]) Jfs
+        CKL(launch_multi_axpy(n, g->jbar_fs, g->lptr, g->lcoef + l, 1, g->stream));
+        if (build)
+            for (int d = 0; d < 27; ++d)
+                CKL(launch_multi_axpy(n, g->lbar + (size_t)d * N, g->lptr + 1 + d, g->lcoef + l,
+                                      1, g->stream));
+    }
+    if (build)
+        CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lbar, g->eps, g->a, g->a64, g->inv_diag,
+                           g->stream, g->per));
+    TRY(os_solve_dev(g, g->jbar_fs, g->J, nullptr, 50, 1e-3));
+    TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));
+    CKL(launch_ali_update(n, g->J, g->dJ_dev, g->st, nullptr, g->stream));
+    TRY(read_scalar_d(g, offsetof(OsState, rel), rel));
+    return RT3D_OK;
+}
+
 }  // namespace
 
 void rt3d::set_last_error(const char *msg) { g_err = msg; }
@@ -1496,6 +1567,80 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = s;
     if (!conv) return fail(RT3D_ENOTCONVERGED, "not converged after %d iterations (est %.3g)", it, est);
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_line_solve(rt3d_grid *g, int nl, const double *chi, const double *scale,
+                            const double *wphi, const double *eps, const double *B,
+                            const rt3d_bc *bc, double *Jbar_inout, double tol, int max_iter,
+                            rt3d_line_stats *stats) {
+    const auto t_start = std::chrono::steady_clock::now();
+    if (!g || !chi || !scale || !wphi || !eps || !B || !Jbar_inout)
+        return fail(RT3D_EINVAL, "NULL argument");
+    if (g->sph) return fail(RT3D_EINVAL, "line transfer needs the Cartesian grid");
+    if (nl < 1 || nl > 65536) return fail(RT3D_EINVAL, "nlambda %d", nl);
+    if (!(tol > 0.0) || max_iter < 1) return fail(RT3D_EINVAL, "bad tol or max_iter");
+    if (is_device_ptr(scale) || is_device_ptr(wphi))
+        return fail(RT3D_EINVAL, "scale and wphi must be host arrays");
+    std::vector<double> sc(nl), negw(nl);
+    double wsum = 0.0;
+    for (int l = 0; l < nl; ++l) {
+        if (!(scale[l] > 0.0) || !std::isfinite(scale[l]))
+            return fail(RT3D_EINVAL, "scale[%d] = %g", l, scale[l]);
+        if (!(wphi[l] >= 0.0) || !std::isfinite(wphi[l]))
+            return fail(RT3D_EINVAL, "wphi[%d] = %g", l, wphi[l]);
+        sc[l] = scale[l];
+        negw[l] = -wphi[l];
+        wsum += wphi[l];
+    }
+    if (!(wsum > 0.0)) return fail(RT3D_EINVAL, "the profile weights sum to zero");
+    const size_t N = (size_t)g->N;
+    rt3d_line_stats s{};
+    s.est_error = -1.0;
+    g->fs_ms[0] = g->fs_ms[1] = g->fs_ms[2] = 0.0;
+    g->launches = 0;
+    TRY(reset_scalar(g, offsetof(OsState, sweeps_total), sizeof(unsigned long long)));
+    TRY(line_setup(g, negw));
+    g->lstar_valid = false;  // the grid's Lambda* and OS coefficients become the line's
+    TRY(load_problem(g, chi, eps, B));
+    CK(cudaMemcpyAsync(g->J, Jbar_inout, N * sizeof(double), cudaMemcpyDefault, g->stream));
+    FsParams fp;
+    TRY(fs_params(g, bc, true, false, &fp));
+    Progress prog;
+    double rel = 1.0;
+    bool conv = false;
+    int it = 0;
+    while (it < max_iter) {
+        TRY(line_iteration(g, fp, sc, it == 0, &rel, &s.fs_lambda));
+        ++it;
+        if (!(rel == rel)) return fail(RT3D_ENUMERIC, "NaN in the line ALI change at iteration %d", it);
+        prog.add(rel);
+        if (it >= 2) {
+            s.est_error = prog.error_estimate();
+            if (s.est_error <= tol) {
+                conv = true;
+                break;
+            }
+        }
+    }
+    s.iterations = it;
+    s.rel_change = rel;
+    TRY(deliver(g, Jbar_inout, g->J, N));
+    CK(cudaStreamSynchronize(g->stream));
+    TRY(collect_events(g));
+    s.fs64_ms = g->fs_ms[1];
+    {
+        unsigned long long sw = 0;
+        CK(cudaMemcpyAsync(&sw, &g->st->sweeps_total, sizeof sw, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        s.jacobi_sweeps = (int)std::min<unsigned long long>(sw, (unsigned long long)INT32_MAX);
+    }
+    s.launches = g->launches;
+    s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (stats) *stats = s;
+    if (!conv)
+        return fail(RT3D_ENOTCONVERGED, "line ALI not converged after %d iterations (est %.3g)",
+                    it, s.est_error);
     return RT3D_OK;
 }
 

@@ -66,6 +66,15 @@ class SolveStats(ctypes.Structure):
         return out
 
 
+class LineStats(ctypes.Structure):
+    _fields_ = [("iterations", _c_int), ("fs_lambda", _c_int), ("jacobi_sweeps", _c_int),
+                ("rel_change", _c_double), ("est_error", _c_double), ("seconds", _c_double),
+                ("fs64_ms", _c_double), ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class FsShape(ctypes.Structure):
     _fields_ = [("block", _c_int), ("rays_per_thread", _c_int), ("widen", _c_int),
                 ("branchless", _c_int)]
@@ -136,6 +145,8 @@ def load(path: str | None = None):
                                           _c_double, P(_c_int), _vp]
     lib.rt3d_solve_batched.argtypes = [_vp, _c_int, _vp, _vp, _vp, P(BC), _vp, _c_double, _c_int,
                                        _vp, P(BatchStats)]
+    lib.rt3d_line_solve.argtypes = [_vp, _c_int, _vp, _vp, _vp, _vp, _vp, P(BC), _vp,
+                                    _c_double, _c_int, P(LineStats)]
     lib.rt3d_grid_sph_ray.argtypes = [_vp, _c_int, _c_int, P(_c_int), _vp, _vp, P(_c_int),
                                       P(_c_int)]
     lib.rt3d_last_error.restype = ctypes.c_char_p
@@ -379,6 +390,27 @@ def solve_batched(h, chi, eps, B, bc, J_inout, tol: float = 1e-8, max_iter: int 
     return out
 
 
+def line_solve(h, chi, scale, wphi, eps, B, bc, Jbar_inout, tol: float = 1e-8,
+               max_iter: int = 2000, raise_on_nonconv: bool = True) -> dict:
+    """Line transfer: Jbar of nl wavelengths with opacities scale[l] * chi and
+    profile weights wphi[l] (host sequences of length nl)."""
+    keep = []
+    b = _bc(bc, keep)
+    sc = np.ascontiguousarray(scale, dtype=np.float64).reshape(-1)
+    wp = np.ascontiguousarray(wphi, dtype=np.float64).reshape(-1)
+    if sc.size != wp.size:
+        raise ValueError("scale and wphi differ in length")
+    st = LineStats()
+    status = load().rt3d_line_solve(h, int(sc.size), _ptr(chi), sc.ctypes.data, wp.ctypes.data,
+                                    _ptr(eps), _ptr(B), ctypes.byref(b) if b else None,
+                                    _ptr(Jbar_inout), tol, max_iter, ctypes.byref(st))
+    out = st.as_dict()
+    out["status"] = status
+    if status != OK and (raise_on_nonconv or status != ENOTCONVERGED):
+        raise RT3DError(status, last_error())
+    return out
+
+
 class Grid:
     """Owning wrapper of an rt3d_grid handle."""
 
@@ -441,3 +473,8 @@ class Grid:
 
     def solve_batched(self, chi, eps, B, bc, J, tol=1e-8, max_iter=4000, raise_on_nonconv=True):
         return solve_batched(self.handle, chi, eps, B, bc, J, tol, max_iter, raise_on_nonconv)
+
+    def line_solve(self, chi, scale, wphi, eps, B, bc, J, tol=1e-8, max_iter=2000,
+                   raise_on_nonconv=True):
+        return line_solve(self.handle, chi, scale, wphi, eps, B, bc, J, tol, max_iter,
+                          raise_on_nonconv)

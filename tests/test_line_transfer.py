@@ -85,3 +85,99 @@ def test_line_lambda_star_is_the_band_of_the_averaged_lambda():
                 continue
             u = zz * nx * ny + ((y + dy) % ny) * nx + (x + dx) % nx
             assert abs(Lb[v, d] - M[v, u]) < 1e-12 * np.max(np.abs(M[v]))
+
+
+# ------------------------------------------------------------ GPU parity
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_01734_gb300 import build, rt3d
+    build.build()
+    rt3d.load()
+    return torch, rt3d
+
+
+def _dev(torch, x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def _dev_bc(torch, bc):
+    return {k: (_dev(torch, v) if isinstance(v, np.ndarray) else v) for k, v in bc.items()}
+
+
+def _relerr(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+@pytest.mark.gpu
+def test_gpu_line_step_parity():
+    torch, rt3d = _gpu()
+    n = (13, 11, 9)
+    chi, eps, B, bc = _box(n, 1e-3, 7)
+    scale, wphi = inputs.line_profile(5, xmax=2.5, strength=3.0)
+    J0 = np.full(chi.shape, 0.5)
+    Jo, relo, _ = oracle.line_ali_step(chi, scale, wphi, eps, B, J0, 4, 8, True, bc)
+    g = rt3d.Grid(n, 4, 8, rt3d.PARABOLIC, rt3d.FP64)
+    J = _dev(torch, J0)
+    st = g.line_solve(_dev(torch, chi), scale, wphi, _dev(torch, eps), _dev(torch, B),
+                      _dev_bc(torch, bc), J, tol=1e-9, max_iter=1, raise_on_nonconv=False)
+    assert st["status"] == rt3d.ENOTCONVERGED
+    assert st["iterations"] == 1 and st["fs_lambda"] == 5 and st["jacobi_sweeps"] > 0
+    assert _relerr(J.cpu().numpy(), Jo) < 1e-11
+    assert abs(st["rel_change"] - relo) < 1e-9 * relo
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gpu_line_solve_matches_oracle(precision):
+    torch, rt3d = _gpu()
+    n = (13, 11, 9)
+    chi, eps, B, bc = _box(n, 1e-2, 8)
+    scale, wphi = inputs.line_profile(5, xmax=2.5, strength=3.0)
+    Jo, it = oracle.line_ali_solve(chi, scale, wphi, eps, B, 4, 8, True, bc, tol=1e-13,
+                                   max_iter=3000)
+    assert it > 0
+    prec = rt3d.FP64 if precision == "fp64" else rt3d.FP32_FS_FP64_ALI
+    g = rt3d.Grid(n, 4, 8, rt3d.PARABOLIC, prec)
+    J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
+    st = g.line_solve(_dev(torch, chi), scale, wphi, _dev(torch, eps), _dev(torch, B),
+                      _dev_bc(torch, bc), J, tol=1e-9, max_iter=3000)
+    assert _relerr(J.cpu().numpy(), Jo) < 1e-8, st
+    assert st["fs_lambda"] == 5 * st["iterations"]
+    assert 0 <= st["est_error"] <= 1e-9
+
+
+@pytest.mark.gpu
+def test_gpu_line_with_equal_opacities_is_the_continuum_solve():
+    torch, rt3d = _gpu()
+    n = (12, 10, 8)
+    chi, eps, B, bc = _box(n, 1e-2, 9)
+    Jo, it, _, _ = oracle.ali_solve(chi, eps, B, 4, 8, False, bc, tol=1e-13, max_iter=3000)
+    assert it > 0
+    g = rt3d.Grid(n, 4, 8, rt3d.LINEAR, rt3d.FP64)
+    J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
+    g.line_solve(_dev(torch, chi), [1.0, 1.0, 1.0], [0.2, 0.5, 0.3], _dev(torch, eps),
+                 _dev(torch, B), _dev_bc(torch, bc), J, tol=1e-9, max_iter=3000)
+    assert _relerr(J.cpu().numpy(), Jo) < 1e-8
+    # the grid's continuum solve afterwards rebuilds its own Lambda*
+    J2 = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
+    g.solve(_dev(torch, chi), _dev(torch, eps), _dev(torch, B), _dev_bc(torch, bc), J2,
+            tol=1e-9, max_iter=3000)
+    assert _relerr(J2.cpu().numpy(), Jo) < 1e-8
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("scale,wphi", [([1.0, 0.0], [0.5, 0.5]), ([1.0, -1.0], [0.5, 0.5]),
+                                        ([1.0, 1.0], [0.5, -0.1]), ([1.0, 1.0], [0.0, 0.0]),
+                                        ([1.0, float("nan")], [0.5, 0.5])])
+def test_gpu_line_bad_profile_is_einval(scale, wphi):
+    torch, rt3d = _gpu()
+    n = (6, 6, 4)
+    chi, eps, B, bc = _box(n, 1e-2, 1)
+    g = rt3d.Grid(n, 2, 4, rt3d.LINEAR, rt3d.FP64)
+    J = torch.zeros(chi.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(rt3d.RT3DError) as ei:
+        g.line_solve(_dev(torch, chi), scale, wphi, _dev(torch, eps), _dev(torch, B), None, J,
+                     tol=1e-8, max_iter=10)
+    assert ei.value.status == rt3d.EINVAL
