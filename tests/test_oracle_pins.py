@@ -364,6 +364,24 @@ def test_lstar_equals_band_of_brute_force_lambda(parabolic):
     assert np.all(L[z == 0][:, :9] == 0) and np.all(L[z == 3][:, 18:] == 0)
 
 
+@pytest.mark.parametrize("n,nth,nph", [((4, 4, 5), 4, 6), ((5, 4, 6), 4, 4)])
+def test_lstar_on_wrapping_characteristics(n, nth, nph):
+    """Small periodic boxes with shallow directions: characteristics wrap
+    around x, y and re-enter a voxel's 3x3x3 neighbourhood, and the
+    passage-local window leaves the later passage out. With the linear
+    weights (all contributions non-negative) no band entry then exceeds the
+    brute-force Lambda's, and some fall measurably below it."""
+    nx, ny, nz = n
+    shape = (nz, ny, nx)
+    rng = np.random.default_rng(3)
+    chi = 10 ** rng.uniform(-1, 0, shape)
+    _, L = oracle.fs_cart(chi, np.ones(shape), nth, nph, False, lstar=True)
+    M = oracle.lambda_matrix(chi, nth, nph, False)
+    diff = (_band_of(M, shape) - L) / np.max(np.abs(M), axis=1, keepdims=True)
+    assert np.min(diff) > -1e-14
+    assert np.max(diff) > 0.05
+
+
 # ----------------------------------------------------------------- the ALI
 def test_os_jacobi_solves_the_band_system():
     rng = np.random.default_rng(2)
