@@ -571,6 +571,40 @@ def run_spherical(args):
     return 0
 
 
+def run_line(args):
+    """Line transfer (wavelengths of one line coupled through the
+    profile-averaged mean intensity): one converged line solve on the box
+    workload's structure at a reduced size (FP64 formal solutions)."""
+    import torch
+
+    from paper_2102_01734_gb300 import build, inputs, rt3d
+
+    build.build()
+    n = args.line_n
+    nth, nph = args.line_angles
+    chi, eps, B, bc = inputs.cartesian_config(n, args.line_eps, seed=1)
+    scale, wphi = inputs.line_profile(args.line_lambdas, xmax=3.0, strength=1.0)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    tchi, teps, tB = d(chi), d(eps), d(B)
+    tbc = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}
+    g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, rt3d.FP64)
+    seg = g.info()["segments"]
+    J = tB.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = g.line_solve(tchi, scale, wphi, teps, tB, tbc, J, tol=args.tol, max_iter=args.max_iter)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"mode": "line", "grid": [n] * 3, "angles": [nth, nph], "eps": args.line_eps,
+           "nlambda": args.line_lambdas, "seconds": dt, "iterations": st["iterations"],
+           "fs_lambda": st["fs_lambda"], "est_error": st["est_error"],
+           "segments_per_s": st["fs_lambda"] * seg / dt,
+           "fs_kernel_segments_per_s": st["fs_lambda"] * seg / (st["fs64_ms"] / 1e3),
+           "note": "FP64 formal solutions; the first iteration builds the averaged Lambda*"}
+    print(json.dumps(out))
+    return 0
+
+
 def run_warmstart(args):
     """Learned warm start (not in the paper): training data
     are converged solutions the method produces on 32 x 32 x nz boxes (the
@@ -707,6 +741,12 @@ def main():
     ap.add_argument("--sph-n", type=int, nargs=3, default=[65, 33, 65])
     ap.add_argument("--sph-angles", type=int, nargs=2, default=[32, 64])
     ap.add_argument("--sph-eps", type=float, default=1e-4)
+    ap.add_argument("--line", action="store_true",
+                    help="line transfer: wavelengths coupled through the profile-averaged J")
+    ap.add_argument("--line-n", type=int, default=65)
+    ap.add_argument("--line-angles", type=int, nargs=2, default=[16, 32])
+    ap.add_argument("--line-lambdas", type=int, default=9)
+    ap.add_argument("--line-eps", type=float, default=1e-2)
     ap.add_argument("--warmstart", action="store_true",
                     help="train the learned warm start and evaluate it")
     ap.add_argument("--ws-n", type=int, default=193)
@@ -722,6 +762,8 @@ def main():
         return run_precisions(args)
     if args.spherical:
         return run_spherical(args)
+    if args.line:
+        return run_line(args)
     if args.batched:
         return run_batched(args)
     if args.impl == "reference":
