@@ -52,9 +52,10 @@ struct IntervalFF {
 
 // e0, a, d of the interval of optical depth u (the quantities of
 // interval_fast). u < 1/2: p(u) = e2/u^3 as the degree-9 polynomial fitted to
-// it on [0, 1/2] (approximation error 1.6e-18 relative), levels 9..6 of its
-// Horner scheme in FP32 (their share of p is below 2.6e-7), 5..0 in
-// float-float; b = u p, a = u/2 (1 - b), e0 = u (1 - a), d = a - b. Otherwise
+// it on [0, 1/2] (approximation error 1.6e-18 relative with exact
+// coefficients), levels 9..6 of its Horner scheme in FP32 (their share of p
+// is below 2.6e-7; their coefficients rounded to FP32 make the polynomial's
+// error 9.3e-15 relative), 5..0 in float-float; b = u p, a = u/2 (1 - b), e0 = u (1 - a), d = a - b. Otherwise
 // E = e^-u, e0 = 1 - E, a = 1 - e0/u, d = (2a - e0)/u with ru = 1/u.
 __device__ __forceinline__ IntervalFF interval_ff(ff u, ff ru, const float2 *tab) {
     IntervalFF r;
