@@ -97,3 +97,40 @@ def test_float_float_fit_on_half_interval():
     # 8.6e-8 of p at u = 1/2) to 24 bits dominates, about 1e-14 relative; far
     # below the float-float formal solution's per-step error budget (2e-12)
     assert worst < 1.5e-14
+
+
+def _constexpr_floats(path):
+    src = open(os.path.join(CSRC, path)).read()
+    return {k: np.float32(float(v)) for k, v in
+            re.findall(r"\b(k[A-Z]\w*) = " + NUM, src)}
+
+
+def _significant_bits(x):
+    m, _ = np.frexp(np.float64(x))  # exact for an FP32 value
+    m = abs(int(np.ldexp(m, 24)))
+    return 24 - (len(bin(m)) - len(bin(m).rstrip("0")))
+
+
+def test_float_float_exponential_constants():
+    """Cody-Waite split of ln2/32 and 32/ln2 of the float-float exponential:
+    c1, c2 short enough that n c1, n c2 are exact for every n the kernel
+    forms (u <= 87), and c1 + c2 + c3 + c4 = ln2/32 to far below float-float
+    precision."""
+    c = _constexpr_floats("fsff.cu")
+    c1, c2, c3, c4, inv = c["kC1"], c["kC2"], c["kC3"], c["kC4"], c["kInvL"]
+    with mpmath.workdps(50):
+        l32 = mpmath.log(2) / 32
+        total = sum(mpmath.mpf(float(v)) for v in (c1, c2, c3, c4))
+        assert abs(total / l32 - 1) < 1e-22  # 4.4e-24: the FP32 rounding of c4
+        assert abs(mpmath.mpf(float(inv)) * l32 - 1) < 2 ** -24
+    n_max = int(np.ceil(87.0 * float(inv)))
+    assert n_max < 2 ** 13
+    for v in (c1, c2):
+        # n (< 2^13) times an 11-bit significand fits the 24-bit significand
+        assert _significant_bits(v) <= 11
+        for n in (1, 3, 4095, n_max):
+            assert float(np.float32(n) * v) == n * float(v)
+    # e^-r series cut after r^5: the remainder at |r| = ln2/64 (plus the
+    # rounding of n) is below 2e-15 relative
+    r = float(mpmath.log(2) / 64) * 1.001
+    assert r ** 6 / 720 < 2e-15
