@@ -131,6 +131,7 @@ def test_float_float_exponential_constants():
         for n in (1, 3, 4095, n_max):
             assert float(np.float32(n) * v) == n * float(v)
     # e^-r series cut after r^5: the remainder at |r| = ln2/64 (plus the
-    # rounding of n) is below 2e-15 relative
+    # rounding of n) is 2.2e-15 relative, below the float-float precision
+    # 2^-48 = 3.6e-15
     r = float(mpmath.log(2) / 64) * 1.001
-    assert r ** 6 / 720 < 2e-15
+    assert r ** 6 / 720 < 2 ** -48
