@@ -46,7 +46,8 @@ typedef enum {
     RT3D_ENOMEM = 2,         /* device or host allocation failed */
     RT3D_ECUDA = 3,          /* a CUDA call failed */
     RT3D_ENOTCONVERGED = 4,  /* iteration cap reached; J holds the last iterate */
-    RT3D_ETIMEOUT = 5,       /* a bounded device-side wait ran out */
+    RT3D_ETIMEOUT = 5,       /* reserved for a bounded device-side wait that ran out;
+                                no kernel of this library spins on the device */
     RT3D_ENUMERIC = 6        /* NaN/Inf met in a residual or change */
 } rt3d_status;
 
