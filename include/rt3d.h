@@ -327,8 +327,8 @@ typedef struct {
     long long launches;     /* kernels launched by the call */
 } rt3d_line_stats;
 
-/* Line transfer (Sec. 2, with Eq. alisol: the mean intensity averaged over
- * the line profile, Jbar = int J_lambda phi_lambda dlambda). nlambda
+/* Line transfer (Sec. 2, with Eq. alisol: J weighted by the line profile
+ * phi across the line, Jbar = int J_lambda phi_lambda dlambda). nlambda
  * wavelengths of one spectral line share the source function
  *   S = (1 - eps) Jbar + eps B,   Jbar = sum_l wphi[l] J_l,
  * where J_l is the formal solution (Eq. frmsol) with the opacity
