@@ -142,13 +142,24 @@ typedef struct {
  * paper, which maps characteristics to OpenACC gangs and vectors, Sec. 5). */
 typedef struct {
     int block;            /* threads per block: 64, 128 or 256 */
-    int rays_per_thread;  /* characteristics per thread: 1 or 2 */
+    int rays_per_thread;  /* characteristics per thread: 1; 2 (face cells
+                             (x, y) and (x, y + 1), y even, integrated together
+                             in packed FP32x2 arithmetic); or 4 (face cells
+                             (x, y .. y + 3), y a multiple of 4, two packed
+                             pairs, the J contributions of successive points
+                             summed in FP32 per voxel while the voxel stays
+                             inside the block of voxels a warp's
+                             characteristics occupy, then reduced in FP64;
+                             FP32 grids of at most 2^27 voxels) */
     int widen;            /* FP32 contribution to FP64 for the reduction: 0 the
-                             conversion instruction, 1 integer moves, 2 both,
-                             alternating from point to point */
+                             conversion instruction, 1 integer moves, 2 both
+                             (one characteristic per thread: alternating from
+                             point to point; two: the second by integer
+                             moves; four: as 0) */
     int branchless;       /* 1: the parabolic correction is evaluated without
                              a branch (multiplied by its blend weight 0 where
-                             the linear form applies) */
+                             the linear form applies); two characteristics
+                             per thread always evaluate it so */
 } rt3d_fs_shape;
 
 #define RT3D_FS_TUNE_SHAPES 8
@@ -185,13 +196,15 @@ rt3d_status rt3d_fs_tune_shape(int i, rt3d_fs_shape *out);
 
 /* Sets the grid's ray-bundle shape of the FP32 formal solution without
  * Lambda*. shape = NULL: autotune at the next such formal solution (the
- * default for a new grid): every candidate of rt3d_fs_tune_shape is launched
- * once on that call's input, timed with CUDA events on the grid's stream,
- * and the fastest is kept. The result does not depend on the shape beyond
+ * default for a new grid): every candidate of rt3d_fs_tune_shape that the
+ * grid supports is launched once on that call's input, timed with CUDA
+ * events on the grid's stream, and the fastest is kept (an unsupported
+ * candidate records 0 ms in rt3d_grid_info). The result does not depend on the shape beyond
  * FP64 reduction order (both widenings are exact for normal FP32 values;
  * integer widening maps an FP32 zero or subnormal contribution to at most
  * 1.2e-38 in magnitude). RT3D_EINVAL for a shape outside the ranges of
- * rt3d_fs_shape. */
+ * rt3d_fs_shape, or four characteristics per thread on a grid that does
+ * not support them. */
 rt3d_status rt3d_grid_set_fs_shape(rt3d_grid *grid, const rt3d_fs_shape *shape);
 
 /* The traced characteristic of solid angle `angle` from face cell (0,0):

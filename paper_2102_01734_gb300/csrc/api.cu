@@ -98,6 +98,7 @@ struct rt3d_grid {
     // FP32 formal solution without Lambda*: replicated FP64 accumulation
     // (zero between launches) and the kernel shape chosen by fs_tune
     double *Jrep = nullptr;  // [4N]
+    float4 *pairs = nullptr;  // [4N] pair-packed FP32 (chi, S) of the two-characteristic kernel
     FsShape fs_shape{0, 0, 0, 0};  // block 0: not chosen yet
     float fs_tune_ms[RT3D_FS_TUNE_SHAPES] = {};  // last tuning: time of each shape
     void *a = nullptr;  // 26 OS off-diagonal planes, os_coef_index layout (f64 in FP64 mode, f32 otherwise)
@@ -127,7 +128,7 @@ struct rt3d_grid {
     double *s_len64 = nullptr, *s_cw64 = nullptr;
     float *s_len32 = nullptr, *s_cw32 = nullptr;
     uint64_t *s_win = nullptr;
-    float4 *s_rec = nullptr;  // [segments] (replicated index bits, l/2, J weight, 0)
+    float4 *s_rec = nullptr;  // [segments] (replicated index bits, J weight, l/2, l/2)
     int *s_perm = nullptr;    // [rays] by decreasing length
 
     // batched-wavelength workspace (allocated for the largest n_lambda seen)
@@ -220,6 +221,8 @@ rt3d_status fs_params(rt3d_grid *g, const rt3d_bc *bc, bool fp64, bool homogeneo
     q.rec32 = g->tpl.rec32;
     q.rec64 = g->tpl.rec64;
     q.Jrep = g->Jrep;
+    q.pairs = g->pairs;
+    q.rec4 = g->tpl.rec4;
     q.chiS = fp64 ? g->chiS64 : g->chiS32;
     q.homogeneous = homogeneous ? 1 : 0;
     if (bc && !homogeneous) {
@@ -251,10 +254,14 @@ rt3d_status collect_events(rt3d_grid *g) {
 
 // Candidate shapes of the FP32 formal-solution kernel without Lambda* that
 // fs_tune times: (threads per block, characteristics per thread, widening,
-// branchless parabolic correction).
+// branchless parabolic correction). Two characteristics per thread is the
+// packed FP32x2 kernel, four the packed kernel that sums J contributions in
+// registers before the FP64 reduction (both always branchless; widening 2 of
+// the four-characteristic kernel is the conversion, as 0). A grid where a
+// candidate cannot run records 0 for it.
 constexpr FsShape kFsShapes[RT3D_FS_TUNE_SHAPES] = {
-    {256, 1, 0, 0}, {256, 1, 1, 0}, {256, 1, 2, 0}, {256, 1, 0, 1},
-    {256, 1, 2, 1}, {128, 1, 0, 0}, {128, 2, 0, 0}, {128, 1, 2, 1}};
+    {256, 1, 0, 1}, {128, 2, 1, 1}, {256, 2, 2, 1}, {256, 4, 1, 1},
+    {128, 4, 1, 1}, {64, 4, 1, 1},  {256, 4, 0, 1}, {128, 4, 0, 1}};
 
 // Autotuner of the FP32 formal solution's ray-bundle shape: times one launch
 // of every shape on the grid's current (chi, S) (CUDA events on the grid's
@@ -266,6 +273,10 @@ rt3d_status fs_tune(rt3d_grid *g, const FsParams &p) {
     int pick = 0;
     for (int i = -1; i < RT3D_FS_TUNE_SHAPES; ++i) {
         const int c = i < 0 ? 0 : i;
+        if (kFsShapes[c].rays_per_thread == 4 && !quad_applicable(p)) {
+            g->fs_tune_ms[c] = 0.0f;  // not available on this grid
+            continue;
+        }
         CK(cudaEventRecord(g->ev0, g->stream));
         CK(launch_fs_fast(p, g->parab, kFsShapes[c], g->stream));
         CK(cudaEventRecord(g->ev1, g->stream));
@@ -434,6 +445,7 @@ rt3d_status alloc_work(rt3d_grid *g) {
     TRY(g->alloc(reinterpret_cast<float2 **>(&g->chiS32), 4 * N));
     TRY(g->alloc(&g->Jrep, 4 * N));
     CK(cudaMemsetAsync(g->Jrep, 0, sizeof(double) * 4 * N, s));
+    if (!g->sph && !g->fs64) TRY(g->alloc(&g->pairs, 4 * N));
     if (g->a64) TRY(g->alloc(reinterpret_cast<double **>(&g->a), os_coef_count(N)));
     else TRY(g->alloc(reinterpret_cast<float **>(&g->a), os_coef_count(N)));
     TRY(g->alloc(&g->st, 1));
@@ -720,6 +732,8 @@ rt3d_status grid_build(rt3d_grid *g) {
     TRY(g->alloc(&t.win, total));
     TRY(g->alloc(&t.rec32, total));
     TRY(g->alloc(&t.rec64, total));
+    const bool quad = !g->fs64 && 4LL * g->nx * g->ny * g->nz <= (1LL << 29) - 1;
+    if (quad) TRY(g->alloc(&t.rec4, total));
     double *d_dir = nullptr, *d_wt = nullptr, *d_ls = nullptr;
     int *d_cap = nullptr, *d_err = nullptr;
     TRY(g->alloc(&d_dir, 3 * nO));
@@ -757,6 +771,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     tp.layer_sum = d_ls;
     tp.err = d_err;
     CK(launch_trace(tp, s));
+    if (quad) CK(launch_quad_rec(t, g->nx, g->ny, t.rec4, s));
     int herr = 0;
     g->K.resize(nO);
     CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1279,6 +1294,9 @@ rt3d_status rt3d_grid_set_fs_shape(rt3d_grid *g, const rt3d_fs_shape *shape) {
     if (!fs_shape_valid(sh))
         return fail(RT3D_EINVAL, "shape (%d, %d, %d, %d) not available", sh.block, sh.rays_per_thread,
                     sh.widen, sh.branchless);
+    if (sh.rays_per_thread == 4 && !g->tpl.rec4)
+        return fail(RT3D_EINVAL, "four characteristics per thread need an FP32 Cartesian grid of "
+                                 "at most 2^27 voxels");
     g->fs_shape = sh;
     return RT3D_OK;
 }

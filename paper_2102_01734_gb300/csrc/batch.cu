@@ -94,24 +94,24 @@ __global__ void __launch_bounds__(256) b_fs(BatchFsParams p) {
     const float4 r = __ldg(rec);
     s.vc = s.base + __float_as_int(r.x);
     const float2 cs = chiS[s.vc];
-    s.hc = cs.x * r.y;
+    s.hc = cs.x * r.z;
     s.u = s.hc;
     s.Sc = cs.y;
     s.Sp = cs.y;
     s.dS = 0.0f;
     s.ru = __fdividef(1.0f, s.hc);
-    float cwc = r.z;
+    float cwc = r.y;
     int k = 1;
     for (; k + 1 < K; k += 2) {
         const float4 r1 = __ldg(rec + k), r2 = __ldg(rec + k + 1);
         fast_step<PARAB, W0, BL>(s, chiS, J, r1, cwc);
-        fast_step<PARAB, W1, BL>(s, chiS, J, r2, r1.z);
-        cwc = r2.z;
+        fast_step<PARAB, W1, BL>(s, chiS, J, r2, r1.y);
+        cwc = r2.y;
     }
     if (k < K) {
         const float4 r1 = __ldg(rec + k);
         fast_step<PARAB, W0, BL>(s, chiS, J, r1, cwc);
-        cwc = r1.z;
+        cwc = r1.y;
     }
     const IntervalE f = interval_fast(s.u, PARAB ? s.ru : __fdividef(1.0f, s.u));
     s.I = fmaf(f.a, s.dS, fmaf(f.e0, s.Sp - s.I, s.I));

@@ -237,30 +237,27 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
     }
 }
 
-// FP32 formal solution without Lambda* (every iteration after the first).
-// A thread integrates RPT characteristics of one solid angle (face cells
-// ray, ray + blockDim.x, ...), sharing the 16-byte broadcast load of each
-// step record (replicated offset, l/2, J weight). Per point and
-// characteristic: one integer add for the replicated address, one 8-byte
-// (chi, S) gather, the interval arithmetic, and one FP64 reduction
-// (red.global.add.f64) into the replicated J, folded afterwards; the FP32
-// contribution is widened by integer moves, by the conversion instruction
-// (which runs on the FP64 pipe), or alternately by both (the autotuner
-// picks, see fast_step and fs_fast_kernel). FP64 accumulation keeps the operator's error at the
-// level of its FP32 arithmetic (an FP32 reduction over ~10^3 contributions
-// per voxel and angle group was measured to cost the refinement a fourth
-// FP64 formal solution and 60 more FP32 ones at 129^3). The reciprocal of
-// the next interval is carried into the next step. The last point (linear
-// form) is peeled off; the loop takes two points per trip so that the
-// carried values rotate through registers without moves.
+// FP32 formal solution without Lambda* (every iteration after the first),
+// one characteristic per thread. Per point: one integer add for the
+// replicated address, one 8-byte (chi, S) gather, the interval arithmetic,
+// and one FP64 reduction (red.global.add.f64) into the replicated J, folded
+// afterwards; the FP32 contribution is widened by integer moves, by the
+// conversion instruction (which runs on the FP64 pipe), or alternately by
+// both (the autotuner picks, see fast_step). FP64 accumulation keeps the
+// operator's error at the level of its FP32 arithmetic (an FP32 reduction
+// over ~10^3 contributions per voxel and angle group was measured to cost
+// the refinement a fourth FP64 formal solution and 60 more FP32 ones at
+// 129^3). The reciprocal of the next interval is carried into the next step.
+// The last point (linear form) is peeled off; the loop takes two points per
+// trip so that the carried values rotate through registers without moves.
 // CONV: how FP32 contributions become FP64 for the reduction: 0 the
 // conversion instruction (FP64 pipe), 1 integer moves, 2 alternating between
 // the two from point to point (both pipes half loaded).
-template <bool PARAB, int RPT, int CONV, bool BRANCHLESS>
+template <bool PARAB, int CONV, bool BRANCHLESS>
 __global__ void __launch_bounds__(256) fs_fast_kernel(FsParams p) {
     const int nray = p.nx * p.ny;
-    const int ray0 = blockIdx.x * (blockDim.x * RPT) + threadIdx.x;
-    if (ray0 >= nray) return;
+    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ray >= nray) return;
     const int o = p.order[blockIdx.y];
     const int K = p.tlen[o];
     const float4 *__restrict__ rec = p.rec32 + p.toff[o];
@@ -268,57 +265,351 @@ __global__ void __launch_bounds__(256) fs_fast_kernel(FsParams p) {
     double *__restrict__ Jd = p.Jrep;
     constexpr bool W0 = CONV == 1, W1 = CONV >= 1;
 
-    RayF ray[RPT];
+    RayF s;
     const float4 r = __ldg(rec);
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-        RayF &s = ray[j];
-        const int rj = ray0 + j * blockDim.x;
-        s.live = rj < nray;
-        const int rr = s.live ? rj : ray0;
-        const int x0 = rr % p.nx, y0 = rr / p.nx;
-        s.base = x0 + 2 * p.nx * y0;
-        double I0 = 0.0;
-        if (!p.homogeneous) {
-            if (p.up[o]) I0 = p.bot_face ? p.bot_face[rr] : p.I_bot;
-            else I0 = p.top_face ? p.top_face[rr] : p.I_top;
-        }
-        s.I = (float)I0;
-        s.vc = s.base + __float_as_int(r.x);
-        const float2 cs = chiS[s.vc];
-        s.hc = cs.x * r.y;  // half the optical depth of the chord of the point
-        s.u = s.hc;         // the entry interval: chi_{-1} l_{-1} = 0
-        s.Sc = cs.y;
-        s.Sp = cs.y;        // S_{-1} = S_0
-        s.dS = 0.0f;
-        s.ru = __fdividef(1.0f, s.hc);
+    s.live = true;
+    const int x0 = ray % p.nx, y0 = ray / p.nx;
+    s.base = x0 + 2 * p.nx * y0;
+    double I0 = 0.0;
+    if (!p.homogeneous) {
+        if (p.up[o]) I0 = p.bot_face ? p.bot_face[ray] : p.I_bot;
+        else I0 = p.top_face ? p.top_face[ray] : p.I_top;
     }
-    float cwc = r.z;
+    s.I = (float)I0;
+    s.vc = s.base + __float_as_int(r.x);
+    const float2 cs = chiS[s.vc];
+    s.hc = cs.x * r.z;  // half the optical depth of the chord of the point
+    s.u = s.hc;         // the entry interval: chi_{-1} l_{-1} = 0
+    s.Sc = cs.y;
+    s.Sp = cs.y;        // S_{-1} = S_0
+    s.dS = 0.0f;
+    s.ru = __fdividef(1.0f, s.hc);
+    float cwc = r.y;
     int k = 1;
     // two points per trip: the carried values rotate through registers
     for (; k + 1 < K; k += 2) {
         const float4 r1 = __ldg(rec + k), r2 = __ldg(rec + k + 1);
-#pragma unroll
-        for (int j = 0; j < RPT; ++j) fast_step<PARAB, W0, BRANCHLESS>(ray[j], chiS, Jd, r1, cwc);
-#pragma unroll
-        for (int j = 0; j < RPT; ++j) fast_step<PARAB, W1, BRANCHLESS>(ray[j], chiS, Jd, r2, r1.z);
-        cwc = r2.z;
+        fast_step<PARAB, W0, BRANCHLESS>(s, chiS, Jd, r1, cwc);
+        fast_step<PARAB, W1, BRANCHLESS>(s, chiS, Jd, r2, r1.y);
+        cwc = r2.y;
     }
     if (k < K) {
         const float4 r1 = __ldg(rec + k);
-#pragma unroll
-        for (int j = 0; j < RPT; ++j) fast_step<PARAB, W0, BRANCHLESS>(ray[j], chiS, Jd, r1, cwc);
-        cwc = r1.z;
+        fast_step<PARAB, W0, BRANCHLESS>(s, chiS, Jd, r1, cwc);
+        cwc = r1.y;
     }
+    const IntervalE f = interval_fast(s.u, PARAB ? s.ru : __fdividef(1.0f, s.u));
+    s.I = fmaf(f.a, s.dS, fmaf(f.e0, s.Sp - s.I, s.I));
+    atomicAdd(Jd + s.vc, to_f64<W1>(cwc * s.I));
+    if (!(fabsf(s.I) <= 3.402823466e38f))  // non-finite: make J NaN
+        atomicAdd(Jd + s.vc, __longlong_as_double(0x7ff8000000000000LL));
+}
+
+// FP32 formal solution without Lambda*, two characteristics per thread in
+// packed FP32x2 arithmetic (pair_advance): face cells (x0, y0) and
+// (x0, y0 + 1) with y0 even. Both sit at the same offset of the cached
+// characteristic, so one 16-byte load of the pair-packed (chi, S) (p.pairs)
+// serves both, and the step record (one 16-byte broadcast load per point) is
+// shared. Lanes of a warp take consecutive x0 of one row pair: the gathers of
+// a warp cover one contiguous run of 16-byte elements. Per point and
+// characteristic one FP64 reduction into the replicated J, as in
+// fs_fast_kernel (CONV: 0 both contributions widened by the conversion
+// instruction, 1 both by integer moves, 2 the first by conversion and the
+// second by integer moves).
+template <bool PARAB, int CONV>
+__global__ void __launch_bounds__(256) fs_pair_kernel(FsParams p) {
+    const int nyh = (p.ny + 1) >> 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.nx * nyh) return;
+    const int o = p.order[blockIdx.y];
+    const int K = p.tlen[o];
+    const float4 *__restrict__ rec = p.rec32 + p.toff[o];
+    const int x0 = t % p.nx, y0 = 2 * (t / p.nx);
+    const bool lb = y0 + 1 < p.ny;  // row y0 + 1 exists (ny odd: not in the last pair)
+    const int base = x0 + 2 * p.nx * y0;
+    const float4 *__restrict__ P = p.pairs + base;
+    double *__restrict__ Ja = p.Jrep + base;
+    double *__restrict__ Jb = Ja + 2 * p.nx;
+    constexpr int CA = CONV == 1 ? 1 : 0, CB = CONV >= 1 ? 1 : 0;
+
+    float Ia = 0.0f, Ib = 0.0f;
+    if (!p.homogeneous) {
+        const double *face = p.up[o] ? p.bot_face : p.top_face;
+        const double I1 = p.up[o] ? p.I_bot : p.I_top;
+        const int fa = y0 * p.nx + x0;
+        Ia = (float)(face ? face[fa] : I1);
+        if (lb) Ib = (float)(face ? face[fa + p.nx] : I1);
+    }
+    RayP s;
+    const float4 r0 = __ldg(rec);
+    int vc = __float_as_int(r0.x);
+    pair_init(s, __ldg(P + vc), pk(r0.z, r0.w), Ia, Ib);
+    float cwc = r0.y;
+#pragma unroll 2
+    for (int k = 1; k < K; ++k) {
+        const float4 rn = __ldg(rec + k);
+        const int vn = __float_as_int(rn.x);
+        const float2 cI = mul2(pair_advance<PARAB>(s, P, vn, pk(rn.z, rn.w)), pk1(cwc));
+        atomicAdd(Ja + vc, pair_widen<CA>(cI.x));
+        if (lb) atomicAdd(Jb + vc, pair_widen<CB>(cI.y));
+        vc = vn;
+        cwc = rn.y;
+    }
+    // the last point: linear form
+    const float2 In = pair_last(s);
+    const float2 cI = mul2(In, pk1(cwc));
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    atomicAdd(Ja + vc, pair_widen<CA>(cI.x));
+    if (!(fabsf(In.x) <= 3.402823466e38f)) atomicAdd(Ja + vc, nan);  // non-finite: make J NaN
+    if (lb) {
+        atomicAdd(Jb + vc, pair_widen<CB>(cI.y));
+        if (!(fabsf(In.y) <= 3.402823466e38f)) atomicAdd(Jb + vc, nan);
+    }
+}
+
+// ---- Four characteristics per thread with the J contributions summed
+// across points before the FP64 reduction.
+//
+// Lane t of the angle's launch integrates face cells (x0, y0 + r), r = 0..3,
+// x0 = t mod nx, y0 = 4 (t div nx) (two packed pairs). All characteristics
+// of an angle are translates, so at every point the 32 lanes x 4 rays of a
+// warp occupy a block of voxels that moves by one voxel in x, in y or in z
+// from point to point (the step type is stored with the point's record).
+// Each lane keeps four FP32 sums, one per row, for the voxels its rays
+// currently occupy, and adds the contribution (J weight x I) of every point.
+// When the block moves in x the sums move one lane over with warp shuffles
+// (the voxel a lane's rays enter was its neighbour's); in y they move one
+// row over inside the lane; a sum whose voxel leaves the block is reduced
+// into the replicated FP64 J: after an x-step through a per-warp list in
+// shared memory that is drained 32 entries at a time by all lanes, after a
+// y-step directly (one row of the block), after a z-step or a diagonal step
+// all four. Lanes of one face row (quad of rows) form a segment: the sums
+// move only between lanes of the same segment, and only between rows that
+// exist (a y-step towards the face's last row reduces the sum of the last
+// existing row instead of moving it on). A sum holds the contributions
+// of one voxel from successive rays, at most ~(points per layer) of them,
+// before its FP64 reduction.
+constexpr int kQuadOffBits = 29;
+constexpr unsigned kQuadOffMask = (1u << kQuadOffBits) - 1u;
+constexpr int kQuadSpill = 64;  // spill list entries per warp
+
+// Reduces a warp's spill list into J (all lanes; entries with index < 0 are
+// empty) and empties it. An entry holds the four row sums of a lane, the
+// replicated index of its row-0 voxel (low 29 bits) and its last existing
+// row (bits 29-30).
+template <int CONV>
+__device__ __forceinline__ void quad_drain(const float2 *sa, const float2 *sb, int *si,
+                                           double *__restrict__ Jrep, int rowp, int lane) {
+    __syncwarp();
+    for (int e = lane; e < kQuadSpill; e += 32) {
+        const int code = si[e];
+        if (code >= 0) {
+            const float2 va = sa[e], vb = sb[e];
+            const int rtop = code >> kQuadOffBits;
+            double *j = Jrep + (code & (int)kQuadOffMask);
+            atomicAdd(j, pair_widen<CONV>(va.x));
+            if (rtop >= 1) atomicAdd(j + rowp, pair_widen<CONV>(va.y));
+            if (rtop >= 2) atomicAdd(j + 2 * rowp, pair_widen<CONV>(vb.x));
+            if (rtop >= 3) atomicAdd(j + 3 * rowp, pair_widen<CONV>(vb.y));
+            si[e] = -1;
+        }
+    }
+    __syncwarp();
+}
+
+template <bool PARAB, int CONV>
+__global__ void __launch_bounds__(256, 3) fs_quad_kernel(FsParams p) {
+    __shared__ float2 sp_a[8][kQuadSpill], sp_b[8][kQuadSpill];
+    __shared__ int sp_idx[8][kQuadSpill];
+    constexpr unsigned FULL = 0xffffffffu;
+    const int nq = (p.ny + 3) >> 2;
+    const int nlive = p.nx * nq;
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t - lane >= nlive) return;  // the whole warp is past the face (warp-uniform)
+    const bool live = t < nlive;
+    const int tt = live ? t : nlive - 1;
+    const int o = p.order[blockIdx.y];
+    const int K = p.tlen[o];
+    const float4 *__restrict__ rec = p.rec4 + p.toff[o];
+    const int x0 = tt % p.nx, q = tt / p.nx, y0 = 4 * q;
+    const int base = x0 + 2 * p.nx * y0;
+    const int rowp = 2 * p.nx;  // one replicated row
+    const float4 *__restrict__ PA = p.pairs + base;
+    // rows y0 + 2, y0 + 3 (a quad without them reads pair A's data, unused)
+    const float4 *__restrict__ PB = (y0 + 2 < p.ny) ? PA + 2 * rowp : PA;
+    double *__restrict__ J0 = p.Jrep + base;
+    // the quad's last existing row (-1: a lane past the face). Rows past it
+    // (the face's last quad when ny is not a multiple of 4) are integrated
+    // and summed like the others, but their sums are never reduced and never
+    // move into an existing row.
+    const int rtop = live ? min(3, p.ny - 1 - y0) : -1;
+    // segments: the lanes of one quad of rows (consecutive x0); lane 0 is live
+    const int seg = live ? q : -1;
+    const int segL = __shfl_up_sync(FULL, seg, 1), segR = __shfl_down_sync(FULL, seg, 1);
+    const bool hasL = lane > 0 && live && segL == seg;
+    const bool hasR = lane < 31 && live && segR == seg;
+    const float2 takeP = pk1(hasR ? 1.0f : 0.0f), takeM = pk1(hasL ? 1.0f : 0.0f);
+    const int nsub = 31 / p.nx + 2;           // segments a warp can span
+    const int per_drain = kQuadSpill / nsub;  // x-steps between drains of the spill list
+    const int slot0 = seg - __shfl_sync(FULL, seg, 0);
+    const int spill_tag = (rtop < 0 ? 0 : rtop) << kQuadOffBits;
+    float2 *sa = sp_a[wb];
+    float2 *sb = sp_b[wb];
+    int *si = sp_idx[wb];
+    for (int e = lane; e < kQuadSpill; e += 32) si[e] = -1;
+    __syncwarp();
+
+    float Iv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (!p.homogeneous) {
+        const double *face = p.up[o] ? p.bot_face : p.top_face;
+        const double I1 = p.up[o] ? p.I_bot : p.I_top;
 #pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-        RayF &s = ray[j];
-        const IntervalE f = interval_fast(s.u, PARAB ? s.ru : __fdividef(1.0f, s.u));
-        s.I = fmaf(f.a, s.dS, fmaf(f.e0, s.Sp - s.I, s.I));
-        if (s.live) {
-            atomicAdd(Jd + s.vc, to_f64<W1>(cwc * s.I));
-            if (!(fabsf(s.I) <= 3.402823466e38f))  // non-finite: make J NaN
-                atomicAdd(Jd + s.vc, __longlong_as_double(0x7ff8000000000000LL));
+        for (int r = 0; r < 4; ++r)
+            if (y0 + r < p.ny) Iv[r] = (float)(face ? face[(y0 + r) * p.nx + x0] : I1);
+    }
+    RayP a, b;
+    const float4 r0 = __ldg(rec);
+    int vc = (int)(__float_as_uint(r0.x) & kQuadOffMask);
+    pair_init(a, __ldg(PA + vc), pk(r0.z, r0.w), Iv[0], Iv[1]);
+    pair_init(b, __ldg(PB + vc), pk(r0.z, r0.w), Iv[2], Iv[3]);
+    float2 A01 = pk1(0.0f), A23 = pk1(0.0f);  // sums of rows y0 .. y0 + 3 at the current voxels
+    float cwc = r0.y;
+    int cnt = 0;
+    // the next point's record and data are loaded one point ahead
+    float4 rn = __ldg(rec + (K > 1 ? 1 : 0));
+    unsigned bits = __float_as_uint(rn.x);
+    float4 cA = __ldg(PA + (bits & kQuadOffMask)), cB = __ldg(PB + (bits & kQuadOffMask));
+#pragma unroll 2
+    for (int k = 1; k < K; ++k) {
+        const float4 rq = __ldg(rec + (k + 1 < K ? k + 1 : k));
+        const unsigned bq = __float_as_uint(rq.x);
+        const float4 qA = __ldg(PA + (bq & kQuadOffMask)), qB = __ldg(PB + (bq & kQuadOffMask));
+        const int vn = (int)(bits & kQuadOffMask);
+        const float2 hl = pk(rn.z, rn.w);
+        const float2 Ia = pair_advance_c<PARAB>(a, cA, hl);
+        const float2 Ib = pair_advance_c<PARAB>(b, cB, hl);
+        A01 = fma2(Ia, pk1(cwc), A01);
+        A23 = fma2(Ib, pk1(cwc), A23);
+        // the block moves from the current points (offset vc) to the next
+        const unsigned type = bits >> kQuadOffBits;
+        if (type <= 1u) {  // x-step: +1 (type 0) or -1 (type 1)
+            const bool plus = type == 0u;
+            if (live && (plus ? !hasL : !hasR)) {  // no lane takes this voxel over
+                const int e = cnt * nsub + slot0;
+                sa[e] = A01;
+                sb[e] = A23;
+                si[e] = (base + vc) | spill_tag;
+            }
+            float s0, s1, s2, s3;
+            if (plus) {
+                s0 = __shfl_down_sync(FULL, A01.x, 1);
+                s1 = __shfl_down_sync(FULL, A01.y, 1);
+                s2 = __shfl_down_sync(FULL, A23.x, 1);
+                s3 = __shfl_down_sync(FULL, A23.y, 1);
+            } else {
+                s0 = __shfl_up_sync(FULL, A01.x, 1);
+                s1 = __shfl_up_sync(FULL, A01.y, 1);
+                s2 = __shfl_up_sync(FULL, A23.x, 1);
+                s3 = __shfl_up_sync(FULL, A23.y, 1);
+            }
+            const float2 take = plus ? takeP : takeM;
+            A01 = mul2(pk(s0, s1), take);
+            A23 = mul2(pk(s2, s3), take);
+            if (++cnt == per_drain) {
+                quad_drain<CONV>(sa, sb, si, p.Jrep, rowp, lane);
+                cnt = 0;
+            }
+        } else if (type == 2u) {  // y-step +1: row y0's voxel leaves
+            if (rtop >= 0) atomicAdd(J0 + vc, pair_widen<CONV>(A01.x));
+            A01 = pk(A01.y, A23.x);
+            A23 = pk(A23.y, 0.0f);
+            if (rtop < 3) {  // the last existing row enters a voxel no sum of this lane holds
+                if (rtop == 2) A23.x = 0.0f;
+                else if (rtop == 1) A01.y = 0.0f;
+                else A01.x = 0.0f;
+            }
+        } else if (type == 3u) {  // y-step -1: the voxel of the last existing row leaves
+            const float v = rtop == 3 ? A23.y : (rtop == 2 ? A23.x : (rtop == 1 ? A01.y : A01.x));
+            if (rtop >= 0) atomicAdd(J0 + rtop * rowp + vc, pair_widen<CONV>(v));
+            A23 = pk(A01.y, A23.x);
+            A01 = pk(0.0f, A01.x);
+        } else {  // z-step or diagonal step: all four leave
+            double *j = J0 + vc;
+            if (rtop >= 0) atomicAdd(j, pair_widen<CONV>(A01.x));
+            if (rtop >= 1) atomicAdd(j + rowp, pair_widen<CONV>(A01.y));
+            if (rtop >= 2) atomicAdd(j + 2 * rowp, pair_widen<CONV>(A23.x));
+            if (rtop >= 3) atomicAdd(j + 3 * rowp, pair_widen<CONV>(A23.y));
+            A01 = pk1(0.0f);
+            A23 = pk1(0.0f);
+        }
+        vc = vn;
+        cwc = rn.y;
+        rn = rq;
+        bits = bq;
+        cA = qA;
+        cB = qB;
+    }
+    // the last point: linear form
+    const float2 Ia = pair_last(a), Ib = pair_last(b);
+    A01 = fma2(Ia, pk1(cwc), A01);
+    A23 = fma2(Ib, pk1(cwc), A23);
+    double *j = J0 + vc;
+    if (rtop >= 0) atomicAdd(j, pair_widen<CONV>(A01.x));
+    if (rtop >= 1) atomicAdd(j + rowp, pair_widen<CONV>(A01.y));
+    if (rtop >= 2) atomicAdd(j + 2 * rowp, pair_widen<CONV>(A23.x));
+    if (rtop >= 3) atomicAdd(j + 3 * rowp, pair_widen<CONV>(A23.y));
+    quad_drain<CONV>(sa, sb, si, p.Jrep, rowp, lane);
+    // a non-finite intensity persists along the recurrence: make J NaN
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (rtop >= 0 && !(fabsf(Ia.x) <= 3.402823466e38f)) atomicAdd(j, nan);
+    if (rtop >= 1 && !(fabsf(Ia.y) <= 3.402823466e38f)) atomicAdd(j + rowp, nan);
+    if (rtop >= 2 && !(fabsf(Ib.x) <= 3.402823466e38f)) atomicAdd(j + 2 * rowp, nan);
+    if (rtop >= 3 && !(fabsf(Ib.y) <= 3.402823466e38f)) atomicAdd(j + 3 * rowp, nan);
+}
+
+// Records of the four-characteristic kernel: (offset | step type << 29,
+// J weight, l/2, l/2), the step type of the move from the previous point:
+// 0 x + 1, 1 x - 1, 2 y + 1, 3 y - 1, 4 anything else (z, diagonal, first).
+__global__ void quad_rec_kernel(int nx, int ny, const long long *__restrict__ toff,
+                                const int *__restrict__ tlen, const uint32_t *__restrict__ code,
+                                const float4 *__restrict__ rec32, float4 *__restrict__ rec4) {
+    const int o = blockIdx.x;
+    const long long t0 = toff[o];
+    const int K = tlen[o];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        unsigned type = 4u;
+        if (k > 0) {
+            const uint32_t c1 = code[t0 + k], c0 = code[t0 + k - 1];
+            int ddx = (int)(c1 & 0x7ffu) - (int)(c0 & 0x7ffu);
+            int ddy = (int)((c1 >> 11) & 0x7ffu) - (int)((c0 >> 11) & 0x7ffu);
+            const int ddz = (int)(c1 >> 22) - (int)(c0 >> 22);
+            if (ddx == nx - 1) ddx = -1;  // wrapped offsets: a step across the
+            if (ddx == 1 - nx) ddx = 1;   // periodic boundary
+            if (ddy == ny - 1) ddy = -1;
+            if (ddy == 1 - ny) ddy = 1;
+            if (ddz == 0 && ddy == 0 && (ddx == 1 || ddx == -1)) type = ddx == 1 ? 0u : 1u;
+            if (ddz == 0 && ddx == 0 && (ddy == 1 || ddy == -1)) type = ddy == 1 ? 2u : 3u;
+        }
+        const float4 r = rec32[t0 + k];
+        const unsigned off = __float_as_uint(r.x);
+        rec4[t0 + k] = make_float4(__uint_as_float(off | (type << kQuadOffBits)), r.y, r.z, r.w);
+    }
+}
+
+// p.pairs from the replicated FP32 (chi, S): at every replicated index the
+// values of that row and the next one, (chi(y), chi(y+1), S(y), S(y+1)); the
+// last replicated row of a layer pairs with the layer's first (never read by
+// an existing characteristic: the pair kernel reads rows <= 2 ny - 2).
+__global__ void pair_pack_kernel(int nx, int ny, int nz, const float2 *__restrict__ chiS,
+                                 float4 *__restrict__ P) {
+    const int rows = 2 * ny * nz, w = 2 * nx;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const long long i0 = (long long)row * w;
+        const long long next = (row % (2 * ny) + 1 < 2 * ny) ? w : w - 2LL * ny * w;
+        for (int x = threadIdx.x; x < w; x += blockDim.x) {
+            const float2 a = chiS[i0 + x], b = chiS[i0 + next + x];
+            P[i0 + x] = make_float4(a.x, b.x, a.y, b.y);
         }
     }
 }
@@ -492,38 +783,71 @@ cudaError_t launch_t(const FsParams &p, cudaStream_t s) {
 
 }  // namespace
 
-template <bool PARAB, int CONV, bool BL>
-void launch_fast_t(const FsParams &p, dim3 grid, int block, int rpt, cudaStream_t s) {
-    if (rpt == 2) fs_fast_kernel<PARAB, 2, CONV, BL><<<grid, block, 0, s>>>(p);
-    else fs_fast_kernel<PARAB, 1, CONV, BL><<<grid, block, 0, s>>>(p);
+template <bool PARAB, bool BL>
+void launch_fast_w(const FsParams &p, dim3 grid, int block, int widen, cudaStream_t s) {
+    if (widen == 0) fs_fast_kernel<PARAB, 0, BL><<<grid, block, 0, s>>>(p);
+    else if (widen == 1) fs_fast_kernel<PARAB, 1, BL><<<grid, block, 0, s>>>(p);
+    else fs_fast_kernel<PARAB, 2, BL><<<grid, block, 0, s>>>(p);
 }
 
 template <bool PARAB>
-void launch_fast_p(const FsParams &p, dim3 grid, const FsShape &sh, cudaStream_t s) {
-    const int b = sh.block, r = sh.rays_per_thread;
-    if (sh.branchless) {
-        if (sh.widen == 0) launch_fast_t<PARAB, 0, true>(p, grid, b, r, s);
-        else if (sh.widen == 1) launch_fast_t<PARAB, 1, true>(p, grid, b, r, s);
-        else launch_fast_t<PARAB, 2, true>(p, grid, b, r, s);
-    } else {
-        if (sh.widen == 0) launch_fast_t<PARAB, 0, false>(p, grid, b, r, s);
-        else if (sh.widen == 1) launch_fast_t<PARAB, 1, false>(p, grid, b, r, s);
-        else launch_fast_t<PARAB, 2, false>(p, grid, b, r, s);
-    }
+void launch_quad_w(const FsParams &p, dim3 grid, int block, int widen, cudaStream_t s) {
+    if (widen == 1) fs_quad_kernel<PARAB, 1><<<grid, block, 0, s>>>(p);
+    else fs_quad_kernel<PARAB, 0><<<grid, block, 0, s>>>(p);
+}
+
+template <bool PARAB>
+void launch_pair_w(const FsParams &p, dim3 grid, int block, int widen, cudaStream_t s) {
+    if (widen == 0) fs_pair_kernel<PARAB, 0><<<grid, block, 0, s>>>(p);
+    else if (widen == 1) fs_pair_kernel<PARAB, 1><<<grid, block, 0, s>>>(p);
+    else fs_pair_kernel<PARAB, 2><<<grid, block, 0, s>>>(p);
+}
+
+bool quad_applicable(const FsParams &p) {
+    return p.rec4 != nullptr && 4LL * p.nx * p.ny * p.nz <= (long long)kQuadOffMask;
+}
+
+cudaError_t launch_quad_rec(const Template &t, int nx, int ny, float4 *rec4, cudaStream_t s) {
+    quad_rec_kernel<<<t.nangles, 256, 0, s>>>(nx, ny, t.toff, t.tlen, t.code, t.rec32, rec4);
+    return cudaGetLastError();
 }
 
 bool fs_shape_valid(const FsShape &sh) {
     return (sh.block == 64 || sh.block == 128 || sh.block == 256) &&
-           (sh.rays_per_thread == 1 || sh.rays_per_thread == 2) && sh.widen >= 0 && sh.widen <= 2 &&
+           (sh.rays_per_thread == 1 || sh.rays_per_thread == 2 || sh.rays_per_thread == 4) &&
+           sh.widen >= 0 && sh.widen <= 2 &&
            (sh.branchless == 0 || sh.branchless == 1);
 }
 
 cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, const FsShape &sh, cudaStream_t s) {
     if (!fs_shape_valid(sh)) return cudaErrorInvalidValue;
-    const int per = sh.block * sh.rays_per_thread;
-    dim3 grid((p.nx * p.ny + per - 1) / per, p.nangles);
-    if (parabolic) launch_fast_p<true>(p, grid, sh, s);
-    else launch_fast_p<false>(p, grid, sh, s);
+    if (sh.rays_per_thread >= 2) {
+        if (!p.pairs) return cudaErrorInvalidValue;
+        if (sh.rays_per_thread == 4 && !quad_applicable(p)) return cudaErrorInvalidValue;
+        const int rows = 2 * p.ny * p.nz;
+        pair_pack_kernel<<<rows < 65536 ? rows : 65536, 256, 0, s>>>(
+            p.nx, p.ny, p.nz, static_cast<const float2 *>(p.chiS), p.pairs);
+        if (sh.rays_per_thread == 4) {
+            const int nlanes = p.nx * ((p.ny + 3) / 4);
+            dim3 grid((nlanes + sh.block - 1) / sh.block, p.nangles);
+            if (parabolic) launch_quad_w<true>(p, grid, sh.block, sh.widen, s);
+            else launch_quad_w<false>(p, grid, sh.block, sh.widen, s);
+            return cudaGetLastError();
+        }
+        const int npair = p.nx * ((p.ny + 1) / 2);
+        dim3 grid((npair + sh.block - 1) / sh.block, p.nangles);
+        if (parabolic) launch_pair_w<true>(p, grid, sh.block, sh.widen, s);
+        else launch_pair_w<false>(p, grid, sh.block, sh.widen, s);
+        return cudaGetLastError();
+    }
+    dim3 grid((p.nx * p.ny + sh.block - 1) / sh.block, p.nangles);
+    if (parabolic) {
+        if (sh.branchless) launch_fast_w<true, true>(p, grid, sh.block, sh.widen, s);
+        else launch_fast_w<true, false>(p, grid, sh.block, sh.widen, s);
+    } else {
+        if (sh.branchless) launch_fast_w<false, true>(p, grid, sh.block, sh.widen, s);
+        else launch_fast_w<false, false>(p, grid, sh.block, sh.widen, s);
+    }
     return cudaGetLastError();
 }
 

@@ -40,10 +40,15 @@ struct Template {
     float *cw32 = nullptr;
     uint64_t *win = nullptr;    // [total] Lambda* window: 9 x 5-bit neighbour codes
     // [total] FP32 step record for the formal solution without Lambda*:
-    // (offset in the 2x2-replicated grid as int bits, l/2, J weight, 0)
+    // (offset in the 2x2-replicated grid as int bits, J weight, l/2, l/2:
+    // the last two form the aligned pair of the packed two-characteristic kernel)
     float4 *rec32 = nullptr;
     // [total] FP64 step record of the same: (l/2, J weight)
     double2 *rec64 = nullptr;
+    // [total] FP32 step record of the four-characteristic kernel (FP32
+    // grids of at most 2^27 voxels): rec32 with the step type in the top
+    // three bits of the offset
+    float4 *rec4 = nullptr;
 };
 
 // The packed (chi, S) arrays are replicated 2 x 2 in x and y: element
@@ -72,6 +77,11 @@ struct FsParams {
     const float4 *rec32;  // FP32 step records (fast path)
     const double2 *rec64; // FP64 (l/2, J weight) records (FP64 path without Lambda*)
     double *Jrep;      // [4N] replicated accumulation target of the fast path
+    // [4N] pair-packed FP32 (chi, S) of the two-characteristic kernel: at the
+    // replicated index of (x, y, z) the values of rows y and y + 1,
+    // (chi(y), chi(y+1), S(y), S(y+1)); written from chiS by launch_fs_fast
+    float4 *pairs;
+    const float4 *rec4;  // nullable: step records of the four-characteristic kernel
     double *lstar;     // nullable [27][N], accumulated into
     const double *top_face;  // nullable [ny*nx]
     const double *bot_face;  // nullable [ny*nx]
@@ -106,11 +116,19 @@ cudaError_t launch_fs(const FsParams &p, bool fp64, bool parabolic, bool lstar, 
 // fields as the public rt3d_fs_shape).
 struct FsShape {
     int block;            // 64, 128 or 256 threads
-    int rays_per_thread;  // 1 or 2
+    int rays_per_thread;  // 1; 2: face rows y and y + 1 in packed FP32x2 arithmetic;
+                          // 4: rows y .. y + 3, J summed across points in registers
     int widen;            // FP32 -> FP64: 0 conversion, 1 integer moves, 2 alternating
+                          // (two per thread: the second characteristic by integer moves)
     int branchless;       // 1: parabolic correction evaluated without a branch
+                          // (two per thread: always without)
 };
 bool fs_shape_valid(const FsShape &sh);
+// whether the four-characteristic kernel can run on these parameters (its
+// records exist and the replicated grid's offsets fit in 29 bits)
+bool quad_applicable(const FsParams &p);
+// the four-characteristic kernel's step records from the template
+cudaError_t launch_quad_rec(const Template &t, int nx, int ny, float4 *rec4, cudaStream_t s);
 // FP32 formal solution without Lambda* into p.Jrep (zero on entry; the fold
 // zeroes it again).
 cudaError_t launch_fs_fast(const FsParams &p, bool parabolic, const FsShape &sh, cudaStream_t s);
@@ -319,7 +337,7 @@ cudaError_t launch_sph_fs(const SphFsParams &p, bool fp64, bool parabolic, bool 
 // order perm, into the replicated FP64 Jrep (zero on entry; fold afterwards)
 cudaError_t launch_sph_fs_fast(const SphFsParams &p, const float4 *rec, const int *perm,
                                double *Jrep, bool parabolic, cudaStream_t s);
-// per-segment records (replicated index bits, l/2, J weight, 0)
+// per-segment records (replicated index bits, J weight, l/2, l/2)
 cudaError_t launch_sph_rec(long long nseg, const int *crep, const double *len64, const double *cw64,
                            float4 *rec, cudaStream_t s);
 

@@ -637,7 +637,7 @@ namespace {
 
 // FP32 formal solution without Lambda* on the spherical cache: the
 // per-point step of the Cartesian kernel (fast_step, difference form) over
-// per-segment records (replicated index of the cell as int bits, l/2, J
+// per-segment records (replicated index of the cell as int bits, J weight, l/2,
 // weight), rays taken in order of decreasing length (perm) so that the
 // threads of a warp run similar trip counts, contributions reduced in FP64
 // at the replicated index (folded afterwards).
@@ -666,24 +666,24 @@ __global__ void __launch_bounds__(128) sph_fs_fast_kernel(SphFsParams p, const f
     const float4 r0 = __ldg(rr);
     st.vc = __float_as_int(r0.x);
     const float2 cs = chiS[st.vc];
-    st.hc = cs.x * r0.y;
+    st.hc = cs.x * r0.z;
     st.u = st.hc;
     st.Sc = cs.y;
     st.Sp = cs.y;
     st.dS = 0.0f;
     st.ru = __fdividef(1.0f, fmaxf(st.hc, 1e-30f));
-    float cwc = r0.z;
+    float cwc = r0.y;
     int k = 1;
     for (; k + 1 < K; k += 2) {
         const float4 r1 = __ldg(rr + k), r2 = __ldg(rr + k + 1);
         fast_step<PARAB, false, false>(st, chiS, Jrep, r1, cwc);
-        fast_step<PARAB, false, false>(st, chiS, Jrep, r2, r1.z);
-        cwc = r2.z;
+        fast_step<PARAB, false, false>(st, chiS, Jrep, r2, r1.y);
+        cwc = r2.y;
     }
     if (k < K) {
         const float4 r1 = __ldg(rr + k);
         fast_step<PARAB, false, false>(st, chiS, Jrep, r1, cwc);
-        cwc = r1.z;
+        cwc = r1.y;
     }
     const IntervalE f = interval_fast(st.u, PARAB ? st.ru : __fdividef(1.0f, st.u));
     st.I = fmaf(f.a, st.dS, fmaf(f.e0, st.Sp - st.I, st.I));
@@ -692,12 +692,12 @@ __global__ void __launch_bounds__(128) sph_fs_fast_kernel(SphFsParams p, const f
         atomicAdd(Jrep + st.vc, __longlong_as_double(0x7ff8000000000000LL));
 }
 
-// per segment: (replicated index as int bits, l/2, J weight, 0)
+// per segment: (replicated index as int bits, J weight, l/2, l/2)
 __global__ void sph_rec_kernel(long long nseg, const int *crep, const double *len64,
                                const double *cw64, float4 *rec) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nseg;
          i += (long long)gridDim.x * blockDim.x)
-        rec[i] = make_float4(__int_as_float(crep[i]), (float)(0.5 * len64[i]), (float)cw64[i], 0.0f);
+        rec[i] = make_float4(__int_as_float(crep[i]), (float)cw64[i], (float)(0.5 * len64[i]), (float)(0.5 * len64[i]));
 }
 
 }  // namespace

@@ -100,7 +100,7 @@ __global__ void trace_kernel(TraceParams p) {
         p.len32[base + i] = (float)l;
         const uint32_t ci = p.code[base + i];
         const long long orep = rep_index(ci & 0x7ff, (ci >> 11) & 0x7ff, ci >> 22, p.nx, p.ny);
-        p.rec32[base + i] = make_float4(__int_as_float((int)orep), (float)(0.5 * l), (float)c, 0.0f);
+        p.rec32[base + i] = make_float4(__int_as_float((int)orep), (float)c, (float)(0.5 * l), (float)(0.5 * l));
         p.rec64[base + i] = make_double2(0.5 * l, c);
     }
 

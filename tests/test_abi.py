@@ -63,6 +63,6 @@ def test_fs_tune_shapes_are_valid(lib):
     shapes = [rt3d.fs_tune_shape(i) for i in range(rt3d.FS_TUNE_SHAPES)]
     assert len(set(shapes)) == rt3d.FS_TUNE_SHAPES
     for block, rpt, widen, bl in shapes:
-        assert block in (64, 128, 256) and rpt in (1, 2) and widen in (0, 1, 2) and bl in (0, 1)
+        assert block in (64, 128, 256) and rpt in (1, 2, 4) and widen in (0, 1, 2) and bl in (0, 1)
     with pytest.raises(rt3d.RT3DError):
         rt3d.fs_tune_shape(rt3d.FS_TUNE_SHAPES)

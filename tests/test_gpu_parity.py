@@ -123,10 +123,11 @@ def test_fs_fp32_parity(rt3d, n, nth, nph, seed, parabolic):
     assert relerr(J2.cpu().numpy(), Jo) < TOL32
 
 
-SHAPES = [(b, r, w, bl) for b in (64, 128, 256) for r in (1, 2) for w in (0, 1, 2) for bl in (0, 1)]
+SHAPES = [(b, r, w, bl) for b in (64, 128, 256) for r in (1, 2, 4) for w in (0, 1, 2) for bl in (0, 1)]
 
 
-@pytest.mark.parametrize("n,nth,nph,seed", [((17, 13, 11), 12, 16, 5), ((4, 5, 3), 2, 6, 6)])
+@pytest.mark.parametrize("n,nth,nph,seed", [((17, 13, 11), 12, 16, 5), ((4, 5, 3), 2, 6, 6),
+                                          ((37, 14, 9), 8, 16, 7)])
 def test_fs_fast_every_shape(rt3d, n, nth, nph, seed):
     """The FP32 formal solution without Lambda* in every ray-bundle shape,
     widening and branch form (ragged bundles; odd and even point counts
