@@ -1,7 +1,8 @@
 """Benchmark of the long-characteristics formal solution + ALI on one GB300.
 
 A step is one converged solve (all steps of the path: tracer cache reused,
-FP32 formal solutions with the Lambda* band built in the first iteration,
+FP32 formal solutions with the Lambda* band built in the first iteration (the
+band is dropped before every step, so each step builds it),
 FP64 Jacobi OS solves inside FGMRES, refinement residuals from float-float
 formal solutions (or FP64 with --precision mixed) and an FP64 formal solution
 certifying the result) of the box129_field workload: 129^3 periodic box,
@@ -53,15 +54,17 @@ OPS_PER_SEGMENT = 28
 # 1/diag and r (FP64), the FP32 copy of the previous sweep (one pass; the
 # neighbours come from cache), the FP64 iterate and its FP32 copy written
 SWEEP_BYTES_F32 = 26 * 4 + 8 + 8 + 4 + 8 + 4
-SMS = 152
 LANES = 128
+# kernel names of the FP32 formal solution by characteristics per thread
+FS_KERNEL = {1: "fs_fast_kernel", 2: "fs_pair_kernel", 4: "fs_quad_kernel"}
 
 
 # The FP32 formal-solution kernel's sources: the DRAM traffic recorded in
 # its profile summary applies only while they are unchanged.
 FS_SOURCES = ("paper_2102_01734_gb300/csrc/fs.cu", "paper_2102_01734_gb300/csrc/fs_step.cuh",
               "paper_2102_01734_gb300/csrc/rt3d_internal.cuh")
-FS_PROFILE = "profiles/fs_fast_kernel_box129_field.md"
+FS_PROFILE = "profiles/fs_pair_kernel_box129_field.md"
+FS_PROFILE_KERNEL = "fs_pair_kernel"
 
 
 def fs_source_hash() -> str:
@@ -268,6 +271,7 @@ def run_ours(args):
 
     def one(timed_stats):
         J.copy_(tB)
+        g.invalidate_lstar()  # every step builds the Lambda* band (Sec. 4)
         st = g.solve(tchi, teps, tB, tbc, J, tol=args.tol, max_iter=args.max_iter)
         timed_stats.append(st)
 
@@ -297,12 +301,18 @@ def run_ours(args):
         torch.distributed.barrier()
     value = segs / total
     solves_per_s = solves / total
-    fs32_ms = sum(s["fs32_ms"] for s in stats)
-    n32 = sum(s["fs_fp32"] for s in stats)
+    # the roofline's kernel: the FP32 formal solutions without Lambda* (the one
+    # per solve that builds Lambda* runs another kernel and is left out)
+    fs32_ms = sum(s["fs32_ms"] - s["fs32_lstar_ms"] for s in stats)
+    n32 = sum(s["fs_fp32"] - s["fs_lstar"] for s in stats)
     fs_rate = n32 * seg_per_fs / (fs32_ms / 1e3) if fs32_ms > 0 else 0.0
+    lstar_ms = sum(s["fs32_lstar_ms"] for s in stats) / max(1, sum(s["fs_lstar"] for s in stats))
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = SMS * LANES * sm_max * 1e6
+    info = g.info()
+    sms = int(info["sm_count"])  # cudaDevAttrMultiProcessorCount, queried by the library
+    peak_ops = sms * LANES * sm_max * 1e6
+    fs_kernel = FS_KERNEL.get(info["fs_shape"][1], "fs_fast_kernel")
     achieved = OPS_PER_SEGMENT * fs_rate
     launches = int(sum(s["launches"] for s in stats))
 
@@ -312,7 +322,7 @@ def run_ours(args):
     hB = torch.from_numpy(B).pin_memory()
     hbot = torch.from_numpy(bc["I_bottom"]).pin_memory()
     hJ = torch.empty(chi.shape, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    e2e_steps = max(1, args.e2e_steps)
     e2e_segs = 0
     if world > 1:
         torch.distributed.barrier()
@@ -320,6 +330,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         hJ.copy_(hB)
+        g.invalidate_lstar()
         st = g.solve(hchi, heps, hB, {"I_top": 0.0, "I_bottom": hbot}, hJ, tol=args.tol,
                      max_iter=args.max_iter)
         e2e_segs += (st["fs_fp32"] + st["fs_fp64"] + st["fs_ff"]) * seg_per_fs
@@ -353,18 +364,21 @@ def run_ours(args):
         "solve": {"iterations": last["iterations"], "fs_fp32": last["fs_fp32"],
                   "fs_fp64": last["fs_fp64"], "fs_ff": last["fs_ff"],
                   "fs_ms": {"fp32": last["fs32_ms"], "fp64": last["fs64_ms"],
-                            "ff": last["fsff_ms"]},
+                            "ff": last["fsff_ms"], "fp32_lstar": last["fs32_lstar_ms"]},
+                  "fs_lstar": last["fs_lstar"],
                   "residual64": last["residual64"],
                   "est_error": last["est_error"],
                   "rounds": [[r64, nfs, res, est] for r64, nfs, res, est in
                              zip(last["round_fp64"], last["round_fs"], last["round_res"],
                                  last["round_est"])]},
         "fs_kernel_segments_per_s": fs_rate,
+        "fs_lstar_ms_per_launch": lstar_ms,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops,
-                     "traffic": recorded_traffic(), "kernel": "fs_fast_kernel<parabolic>",
-                     "peak_source": f"{SMS} SMs x {LANES} FP32 lanes x {sm_max:.0f} MHz "
-                                    f"(sm_max_mhz, {peak_kind})",
+                     "traffic": recorded_traffic() if fs_kernel == FS_PROFILE_KERNEL else None,
+                     "kernel": f"{fs_kernel}<parabolic>", "fs_shape": list(info["fs_shape"]),
+                     "peak_source": f"{sms} SMs (cudaDevAttrMultiProcessorCount) x {LANES} FP32 "
+                                    f"lanes x {sm_max:.0f} MHz (sm_max_mhz, {peak_kind})",
                      "ops_per_segment": OPS_PER_SEGMENT},
         "e2e": {"value": e2e_segs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
@@ -721,7 +735,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--max-iter", type=int, default=4000)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-angles", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels", action="store_true",

@@ -136,6 +136,9 @@ typedef struct {
     int round_fs[16];      /* formal solutions of the round's FGMRES cycle */
     double round_res[16];  /* the round's residual max_v |r_v| / |J_v| */
     double round_est[16];  /* estimated error at that residual (-1: none) */
+    int fs_lstar;          /* FP32 formal solutions that built Lambda* (counted
+                              in fs_fp32) */
+    double fs32_lstar_ms;  /* their summed device time (included in fs32_ms) */
 } rt3d_solve_stats;
 
 /* Ray-bundle shape of the FP32 formal solution without Lambda* (not in the
@@ -175,6 +178,9 @@ typedef struct {
     float fs_tune_ms[RT3D_FS_TUNE_SHAPES]; /* kernel time of each candidate
                                  shape (rt3d_fs_tune_shape order) at the last
                                  autotuning; 0 if not tuned */
+    int sm_count;             /* streaming multiprocessors of the grid's device
+                                 (cudaDevAttrMultiProcessorCount), which sizes the
+                                 library's capped launches */
 } rt3d_grid_info;
 
 /* Creates a grid: builds the direction set (host, FP64) and traces one
@@ -187,6 +193,32 @@ rt3d_status rt3d_grid_create(const rt3d_grid_desc *desc, rt3d_grid **out);
 
 /* Releases the grid and all device memory it holds. NULL is ignored. */
 void rt3d_grid_destroy(rt3d_grid *grid);
+
+/* Solver of the OS step [1 - Lambda*(1 - eps)] dJ = r (Sec. 4: the OS
+ * iteration by Jacobi, Gauss-Seidel or BiCGStab) used by every call of the
+ * grid that solves it: rt3d_os_solve, rt3d_ali_step, rt3d_solve (its ALI, and
+ * its Krylov preconditioner), rt3d_line_solve.
+ *   RT3D_OS_JACOBI (default): Jacobi sweeps from dJ = r/diag.
+ *   RT3D_OS_GAUSS_SEIDEL: eight-colour Gauss-Seidel sweeps from dJ = r/diag,
+ *     colours c = (x&1) + 2(y&1) + 4(z&1) in order, every voxel of a colour
+ *     from the values its neighbours hold before that colour's update; the
+ *     same stop test as Jacobi, once per sweep of all colours.
+ *   RT3D_OS_BICGSTAB: BiCGStab (van der Vorst 1992) from dJ = 0, stopped when
+ *     ||A dJ - r||_2 <= tol ||r||_2, at a breakdown (omega = 0), or after the
+ *     cap; its iterations are counted as sweeps, and a cap given in sweeps by
+ *     the library (50 for the ALI and the preconditioner) allows half as
+ *     many iterations (two matrix products each).
+ * The batched solve (rt3d_solve_batched) and rt3d_os_solve_noalloc always use
+ * Jacobi. RT3D_EINVAL for NULL or another value. */
+#define RT3D_OS_JACOBI 0
+#define RT3D_OS_GAUSS_SEIDEL 1
+#define RT3D_OS_BICGSTAB 2
+rt3d_status rt3d_grid_set_os_solver(rt3d_grid *grid, int solver);
+
+/* Drops the grid's Lambda* band (Sec. 4: built in the first iteration of a
+ * solve and kept while chi and eps are unchanged), so that the next solve or
+ * ALI step builds it again from its own chi and eps. RT3D_EINVAL for NULL. */
+rt3d_status rt3d_grid_invalidate_lstar(rt3d_grid *grid);
 
 rt3d_status rt3d_grid_get_info(const rt3d_grid *grid, rt3d_grid_info *info);
 
@@ -246,11 +278,13 @@ rt3d_status rt3d_formal_solution_ff(rt3d_grid *grid, const double *chi, const do
                                     const rt3d_bc *bc, double *J_out);
 
 /* OS linear system of Eq. alo for the correction dJ = J_new - J_old:
- * [1 - Lambda*(1 - eps)] dJ = r, by Jacobi sweeps (Sec. 4, OS iteration):
- * dJ^0 = r / diag; stops when max|dJ^{m+1} - dJ^m| <= tol * max|dJ^{m+1}|
- * or after max_sweeps (1..256). lstar: double[27][N] as written by
- * rt3d_formal_solution; eps, r, dJ_out: double[N]. sweeps_out (nullable,
- * host) receives the number of sweeps. */
+ * [1 - Lambda*(1 - eps)] dJ = r, by the grid's OS solver (Sec. 4, OS
+ * iteration; rt3d_grid_set_os_solver). Jacobi and Gauss-Seidel: dJ^0 = r /
+ * diag; stop when max|dJ^{m+1} - dJ^m| <= tol * max|dJ^{m+1}| or after
+ * max_sweeps (1..256) sweeps. BiCGStab: from dJ = 0, stop when
+ * ||A dJ - r||_2 <= tol ||r||_2 or after max_sweeps iterations. lstar:
+ * double[27][N] as written by rt3d_formal_solution; eps, r, dJ_out:
+ * double[N]. sweeps_out (nullable, host) receives the sweeps (iterations). */
 rt3d_status rt3d_os_solve(rt3d_grid *grid, const double *lstar, const double *eps,
                           const double *r, double *dJ_out, int max_sweeps, double tol,
                           int *sweeps_out);
@@ -387,12 +421,18 @@ rt3d_status rt3d_line_solve(rt3d_grid *grid, int nlambda, const double *chi,
  * grids or nx, ny < 4 return RT3D_EINVAL). The only scratch is a fixed
  * file-scope device array of 2 * RT3D_NOALLOC_MAX_VOXELS doubles (1 MiB,
  * held by every GPU that loads the library until the process exits).
- * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture. All calls share the array: calls whose work
- * overlaps on the GPU race and must be serialised. Work runs on cuda_stream
- * (NULL: legacy stream); the call returns after it completes. sweeps_out
- * (nullable, host) receives the number of sweeps. */
+ * The arrays must be device memory of the current device (or managed
+ * memory); another device's arrays return RT3D_EINVAL. The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current and keeps it for the process; make that first call
+ * before any stream capture. A cudaDeviceReset (or another destruction of
+ * the device's primary context) while the library is loaded is not
+ * supported. All calls share the array: calls whose work overlaps on the
+ * GPU race and must be serialised. Work runs on cuda_stream (NULL: legacy
+ * stream); every call synchronises that stream before it returns (it reads
+ * the sweep count back), and returns RT3D_EINVAL without launching anything
+ * while the stream is being captured. sweeps_out (nullable, host) receives
+ * the number of sweeps. */
 #define RT3D_NOALLOC_MAX_VOXELS 65536
 rt3d_status rt3d_os_solve_noalloc(int nx, int ny, int nz, const double *lstar,
                                   const double *eps, const double *r, double *dJ_out,

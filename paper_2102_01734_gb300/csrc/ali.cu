@@ -111,22 +111,224 @@ __device__ __forceinline__ long long nb_index(int x, int y, int z, int dx, int d
 
 template <typename A>
 __global__ void os_prep_kernel(int nx, int ny, int nz, const double *L, const double *eps, A *a,
-                               double *inv_diag, Periodic per) {
+                               double *inv_diag, Periodic per, bool colour, ColourGeo cg,
+                               double *diag) {
     const long long N = (long long)nx * ny * nz;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
          v += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
-        inv_diag[v] = 1.0 / (1.0 - L[13 * N + v] * (1.0 - eps[v]));
+        const double dg = 1.0 - L[13 * N + v] * (1.0 - eps[v]);
+        inv_diag[v] = 1.0 / dg;
+        if (diag) diag[v] = dg;
+        const int c = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+        const long long k = (x >> 1) + (long long)cg.nxc[c] * ((y >> 1) + (long long)cg.nyc[c] * (z >> 1));
         int plane = 0;
         for (int d = 0; d < 27; ++d) {
             if (d == 13) continue;
             const long long u = nb_index(x, y, z, d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1, nx, ny, nz, per);
             double val = 0.0;
             if (u >= 0) val = L[(long long)d * N + v] * (1.0 - eps[u]);
-            a[os_coef_index(plane, v)] = (A)val;
+            a[colour ? os_colour_index(plane, cg.blk[c], k) : os_coef_index(plane, v)] = (A)val;
             ++plane;
         }
     }
+}
+
+// Colour c of the eight-colour sweep: every voxel of the colour from its
+// neighbours' values of this sweep where their colour comes earlier (in dst,
+// already final) and of the last sweep otherwise (in src: later colours, and
+// the same colour, which a periodic axis of odd length makes a neighbour
+// across the seam); Jacobi inside a colour, as the oracle's sweep defines it.
+template <typename A>
+__global__ void __launch_bounds__(256) gs_colour_kernel(int nx, int ny, int nz, ColourGeo cg, int c,
+                                                        const A *__restrict__ a,
+                                                        const double *__restrict__ inv_diag,
+                                                        const double *__restrict__ r,
+                                                        const double *__restrict__ src,
+                                                        double *__restrict__ dst, int m, double tol,
+                                                        OsState *st, Periodic per) {
+    if (st->done) return;
+    if (c == 0 && m >= 2) {
+        const double dm = bitsd(st->dmax[m - 1]), jm = bitsd(st->jmax[m - 1]);
+        if (dm <= tol * jm) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                st->done = 1;
+                st->count = m - 1;
+            }
+            return;
+        }
+    }
+    const int px = c & 1, py = (c >> 1) & 1, pz = c >> 2;
+    const int nxc = cg.nxc[c], nyc = cg.nyc[c];
+    const long long cnt = cg.cnt[c], blk0 = cg.blk[c];
+    const int nxy = nx * ny;
+    double dmax = 0.0, jmax = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < cnt;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long kxy = (long long)nxc * nyc;
+        const int zi = (int)(k / kxy), rem = (int)(k - zi * kxy), yi = rem / nxc, xi = rem - yi * nxc;
+        const int x = 2 * xi + px, y = 2 * yi + py, z = 2 * zi + pz;
+        const int v = x + nx * (y + ny * z);
+        const int X[3] = {os_nb_lo(x, nx, per.x), x, os_nb_hi(x, nx, per.x)};
+        const int Y[3] = {os_nb_lo(y, ny, per.y), y, os_nb_hi(y, ny, per.y)};
+        const int Z[3] = {os_nb_lo(z, nz, per.z), z, os_nb_hi(z, nz, per.z)};
+        const A *__restrict__ ab = a + os_colour_index(0, blk0, k);
+        A acc = A(0);
+#pragma unroll
+        for (int d = 0, pl = 0; d < 27; ++d) {
+            if (d == 13) continue;
+            const int xn = X[d % 3], yn = Y[(d / 3) % 3], zn = Z[d / 9];
+            const int cn = (xn & 1) + 2 * (yn & 1) + 4 * (zn & 1);
+            const int u = xn + nx * yn + nxy * zn;
+            const double xv = cn < c ? dst[u] : src[u];
+            acc += ab[pl * 32] * (A)xv;
+            ++pl;
+        }
+        const double nv = (r[v] + (double)acc) * inv_diag[v];
+        dst[v] = nv;
+        dmax = fmax(dmax, fabs(nv - src[v]));
+        jmax = fmax(jmax, fabs(nv));
+    }
+    block_max_atomic(dmax, &st->dmax[m]);
+    block_max_atomic(jmax, &st->jmax[m]);
+}
+
+// ---- BiCGStab (van der Vorst 1992) on A x = r, A = [1 - Lambda*(1 - eps)],
+// from x = 0, as the oracle's orc_os_bicgstab: scalars on the device, dot
+// products accumulated by the kernels that produce their operands.
+
+// block sum of v (all threads), added to *out by thread 0 of each block
+__device__ __forceinline__ void block_sum_atomic(double v, double *out) {
+    __shared__ double part[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) atomicAdd(out, v);
+    }
+}
+
+// (A x)_v = diag_v x_v - sum_d a_d(v) x_{v+d}
+template <typename A>
+__device__ __forceinline__ double os_apply(const A *a, const double *diag, const double *x, int v,
+                                           int nx, int ny, int nz, Periodic per) {
+    return diag[v] * x[v] - (double)os_stencil(a, x, v, nx, ny, nz, per);
+}
+
+__global__ void bicg_init_kernel(int n, const double *r, BicgVecs vv, BicgState *bs) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        bs->rho = bs->alpha = bs->omega = 1.0;
+        bs->rhv = bs->tt = bs->ts = bs->rr = 0.0;
+    }
+    double acc = 0.0;
+    for (int i = tid; i < n; i += gridDim.x * blockDim.x) {
+        const double ri = r[i];
+        vv.x[i] = 0.0;
+        vv.res[i] = ri;
+        vv.rh[i] = ri;
+        vv.p[i] = 0.0;
+        vv.vv[i] = 0.0;
+        acc += ri * ri;
+    }
+    block_sum_atomic(acc, &bs->rr0);
+}
+
+// rho1 = rh . res
+__global__ void bicg_rho_kernel(int n, BicgVecs v, BicgState *bs) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        acc += v.rh[i] * v.res[i];
+    block_sum_atomic(acc, &bs->rho1);
+}
+
+// p = res + beta (p - omega vv), beta = (rho1/rho)(alpha/omega)
+__global__ void bicg_p_kernel(int n, BicgVecs v, BicgState *bs) {
+    const double beta = (bs->rho1 / bs->rho) * (bs->alpha / bs->omega), om = bs->omega;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        v.p[i] = v.res[i] + beta * (v.p[i] - om * v.vv[i]);
+}
+
+// vv = A p; rhv = rh . vv
+template <typename A>
+__global__ void __launch_bounds__(256) bicg_vv_kernel(int nx, int ny, int nz, const A *__restrict__ a,
+                                                      const double *__restrict__ diag, BicgVecs v,
+                                                      BicgState *bs, Periodic per) {
+    const int n = nx * ny * nz;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double y = os_apply(a, diag, v.p, i, nx, ny, nz, per);
+        v.vv[i] = y;
+        acc += v.rh[i] * y;
+    }
+    block_sum_atomic(acc, &bs->rhv);
+}
+
+// alpha = rho1 / rhv; sv = res - alpha vv
+__global__ void bicg_s_kernel(int n, BicgVecs v, BicgState *bs) {
+    const double alpha = bs->rho1 / bs->rhv;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        v.sv[i] = v.res[i] - alpha * v.vv[i];
+}
+
+// t = A sv; tt = t . t; ts = t . sv
+template <typename A>
+__global__ void __launch_bounds__(256) bicg_t_kernel(int nx, int ny, int nz, const A *__restrict__ a,
+                                                     const double *__restrict__ diag, BicgVecs v,
+                                                     BicgState *bs, Periodic per) {
+    const int n = nx * ny * nz;
+    double att = 0.0, ats = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double y = os_apply(a, diag, v.sv, i, nx, ny, nz, per);
+        v.t[i] = y;
+        att += y * y;
+        ats += y * v.sv[i];
+    }
+    block_sum_atomic(att, &bs->tt);
+    block_sum_atomic(ats, &bs->ts);
+}
+
+// omega = ts / tt (0 if tt = 0); x += alpha p + omega sv; res = sv - omega t;
+// rr = res . res
+__global__ void bicg_x_kernel(int n, BicgVecs v, BicgState *bs) {
+    const double alpha = bs->rho1 / bs->rhv;
+    const double om = bs->tt > 0.0 ? bs->ts / bs->tt : 0.0;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        v.x[i] += alpha * v.p[i] + om * v.sv[i];
+        const double ri = v.sv[i] - om * v.t[i];
+        v.res[i] = ri;
+        acc += ri * ri;
+    }
+    block_sum_atomic(acc, &bs->rr);
+}
+
+// end of an iteration: rho = rho1, alpha and omega kept; accumulators of the
+// next iteration zeroed (rr stays for the host's stop test)
+__global__ void bicg_next_kernel(BicgState *bs) {
+    bs->alpha = bs->rho1 / bs->rhv;
+    bs->omega = bs->tt > 0.0 ? bs->ts / bs->tt : 0.0;
+    bs->rho = bs->rho1;
+    bs->rho1 = 0.0;
+    bs->rhv = 0.0;
+    bs->tt = 0.0;
+    bs->ts = 0.0;
+}
+
+__global__ void bicg_zero_rr_kernel(BicgState *bs) { bs->rr = 0.0; }
+
+__global__ void os_set_result_kernel(int n, const double *src, double *dst, int k, OsState *st) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        st->done = 1;
+        st->count = k;
+        st->sweeps_total += (unsigned long long)k;
+    }
+    if (dst != src)
+        for (int i = tid; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
 
 // r = Jfs - J (+ extra); dJ0 = r / diag; resets the sweep state.
@@ -272,7 +474,7 @@ __global__ void compare_kernel(long long n, const double *a, const double *b, Os
 
 int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
-    const long long cap = 152LL * 16;
+    const long long cap = 16LL * device_sm_count();
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
@@ -295,15 +497,84 @@ cudaError_t launch_source(int nx, int ny, int nz, const double *J, const double 
     return cudaGetLastError();
 }
 
+ColourGeo colour_geo(int nx, int ny, int nz) {
+    ColourGeo cg{};
+    long long blk = 0;
+    for (int c = 0; c < 8; ++c) {
+        const int px = c & 1, py = (c >> 1) & 1, pz = c >> 2;
+        cg.nxc[c] = (nx - px + 1) / 2;
+        cg.nyc[c] = (ny - py + 1) / 2;
+        const long long nzc = (nz - pz + 1) / 2;
+        cg.cnt[c] = (long long)cg.nxc[c] * cg.nyc[c] * nzc;
+        cg.blk[c] = blk;
+        blk += (cg.cnt[c] + 31) >> 5;
+    }
+    return cg;
+}
+
+cudaError_t launch_gs_sweep(int nx, int ny, int nz, const ColourGeo &cg, const void *a, bool a64,
+                            const double *inv_diag, const double *r, const double *src,
+                            double *dst, int m, double tol, OsState *st, cudaStream_t s,
+                            Periodic per) {
+    for (int c = 0; c < 8; ++c) {
+        const int blocks = grid_for(cg.cnt[c] > 0 ? cg.cnt[c] : 1, 256);
+        if (a64)
+            gs_colour_kernel<double><<<blocks, 256, 0, s>>>(nx, ny, nz, cg, c,
+                                                            static_cast<const double *>(a), inv_diag,
+                                                            r, src, dst, m, tol, st, per);
+        else
+            gs_colour_kernel<float><<<blocks, 256, 0, s>>>(nx, ny, nz, cg, c,
+                                                           static_cast<const float *>(a), inv_diag, r,
+                                                           src, dst, m, tol, st, per);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_init(int n, const double *r, const BicgVecs &v, BicgState *bs,
+                             cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&bs->rr0, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&bs->rho1, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    bicg_init_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, r, v, bs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_iteration(int nx, int ny, int nz, const void *a, bool a64,
+                                  const double *diag, const BicgVecs &v, BicgState *bs,
+                                  cudaStream_t s, Periodic per) {
+    const int n = nx * ny * nz;
+    const int b = grid_for(n, 256);
+    bicg_rho_kernel<<<b, 256, 0, s>>>(n, v, bs);
+    bicg_p_kernel<<<b, 256, 0, s>>>(n, v, bs);
+    if (a64) bicg_vv_kernel<double><<<b, 256, 0, s>>>(nx, ny, nz, static_cast<const double *>(a), diag, v, bs, per);
+    else bicg_vv_kernel<float><<<b, 256, 0, s>>>(nx, ny, nz, static_cast<const float *>(a), diag, v, bs, per);
+    bicg_s_kernel<<<b, 256, 0, s>>>(n, v, bs);
+    if (a64) bicg_t_kernel<double><<<b, 256, 0, s>>>(nx, ny, nz, static_cast<const double *>(a), diag, v, bs, per);
+    else bicg_t_kernel<float><<<b, 256, 0, s>>>(nx, ny, nz, static_cast<const float *>(a), diag, v, bs, per);
+    bicg_zero_rr_kernel<<<1, 1, 0, s>>>(bs);
+    bicg_x_kernel<<<b, 256, 0, s>>>(n, v, bs);
+    bicg_next_kernel<<<1, 1, 0, s>>>(bs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_os_set_result(int n, const double *src, double *dst, int k, OsState *st,
+                                 cudaStream_t s) {
+    os_set_result_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, src, dst, k, st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_os_prep(int nx, int ny, int nz, const double *lstar, const double *eps,
-                           void *a, bool a64, double *inv_diag, cudaStream_t s, Periodic per) {
+                           void *a, bool a64, double *inv_diag, cudaStream_t s, Periodic per,
+                           bool colour, double *diag) {
     const long long N = (long long)nx * ny * nz;
+    const ColourGeo cg = colour_geo(nx, ny, nz);
     if (a64)
-        os_prep_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(nx, ny, nz, lstar, eps,
-                                                                static_cast<double *>(a), inv_diag, per);
+        os_prep_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(
+            nx, ny, nz, lstar, eps, static_cast<double *>(a), inv_diag, per, colour, cg, diag);
     else
-        os_prep_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(nx, ny, nz, lstar, eps,
-                                                               static_cast<float *>(a), inv_diag, per);
+        os_prep_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(
+            nx, ny, nz, lstar, eps, static_cast<float *>(a), inv_diag, per, colour, cg, diag);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,23 @@
 
 using namespace rt3d;
 
+int rt3d::device_sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (dev < 64 && cached[dev] > 0) return cached[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    if (dev < 64) cached[dev] = n;
+    return n;
+}
+
 namespace {
 
 thread_local std::string g_err;
@@ -54,16 +71,28 @@ rt3d_status fail(rt3d_status st, const char *fmt, ...) {
         if (s_ != RT3D_OK) return s_;          \
     } while (0)
 
-bool is_device_ptr(const void *p) {
-    if (!p) return false;
+// Where p points: 0 host memory (pageable or pinned) or unknown, 1 device
+// memory of the current device or managed memory (usable by the library's
+// kernels as is), 2 device memory of another device.
+int ptr_kind(const void *p) {
+    if (!p) return 0;
     cudaPointerAttributes at;
     cudaError_t e = cudaPointerGetAttributes(&at, p);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return 1;
+    if (at.type != cudaMemoryTypeDevice) return 0;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 2;
+    }
+    return at.device == dev ? 1 : 2;
 }
+
+bool is_device_ptr(const void *p) { return ptr_kind(p) == 1; }
 
 }  // namespace
 
@@ -103,6 +132,14 @@ struct rt3d_grid {
     float fs_tune_ms[RT3D_FS_TUNE_SHAPES] = {};  // last tuning: time of each shape
     void *a = nullptr;  // 26 OS off-diagonal planes, os_coef_index layout (f64 in FP64 mode, f32 otherwise)
     bool a64 = true;
+    // OS solver (rt3d_grid_set_os_solver): the coefficients use the colour
+    // layout under Gauss-Seidel; diag = 1 - Lambda*_0 (1 - eps) for BiCGStab's
+    // products; BiCGStab's vectors and scalars allocated on first use
+    int os_kind = kOsJacobi;
+    double *diag = nullptr;
+    double *bres = nullptr, *brh = nullptr, *bp = nullptr, *bvv = nullptr, *bsv = nullptr,
+           *bt = nullptr;
+    BicgState *bicg = nullptr;
     OsState *st = nullptr;
     bool lstar_valid = false;
 
@@ -158,8 +195,9 @@ struct rt3d_grid {
     // instrumentation: formal-solution kernel time (CUDA events on the
     // grid's stream) and kernels launched
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    int ev_pending = -1;  // -1 none, 0 FP32, 1 FP64, 2 float-float
-    double fs_ms[3] = {0.0, 0.0, 0.0};
+    int ev_pending = -1;  // -1 none, 0 FP32, 1 FP64, 2 float-float, 3 FP32 with Lambda*
+    double fs_ms[4] = {0.0, 0.0, 0.0, 0.0};
+    int fs_lstar32 = 0;   // FP32 formal solutions with Lambda* since the last reset
     long long launches = 0;
 
     template <typename T>
@@ -188,7 +226,8 @@ struct rt3d_grid {
 
 namespace {
 
-// Input: a device pointer as is, or a host array copied into `stage`.
+// Input: a pointer to the grid's device memory (or managed memory) as is;
+// a host array, or another device's array, copied into `stage`.
 rt3d_status stage_in(rt3d_grid *g, const double *p, size_t n, double *stage, const double **out) {
     if (!p) {
         *out = nullptr;
@@ -198,7 +237,7 @@ rt3d_status stage_in(rt3d_grid *g, const double *p, size_t n, double *stage, con
         *out = p;
         return RT3D_OK;
     }
-    CK(cudaMemcpyAsync(stage, p, n * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemcpyAsync(stage, p, n * sizeof(double), cudaMemcpyDefault, g->stream));
     *out = stage;
     return RT3D_OK;
 }
@@ -333,7 +372,8 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         if (sfast) CK(launch_sph_fs_fast(sp, g->s_rec, g->s_perm, g->Jrep, g->parab, g->stream));
         else CK(launch_sph_fs(sp, fp64, g->parab, with_lstar, g->stream));
         CK(cudaEventRecord(g->ev1, g->stream));
-        g->ev_pending = fp64 ? 1 : 0;
+        g->ev_pending = fp64 ? 1 : (with_lstar ? 3 : 0);
+        if (!fp64 && with_lstar) ++g->fs_lstar32;
         ++g->launches;
         if (sfast) {
             CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
@@ -352,7 +392,8 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
     else if (fast) CK(launch_fs_fast(p, g->parab, g->fs_shape, g->stream));
     else CK(launch_fs(p, fp64, g->parab, with_lstar, g->stream));
     CK(cudaEventRecord(g->ev1, g->stream));
-    g->ev_pending = fp64 ? 1 : 0;
+    g->ev_pending = fp64 ? 1 : (with_lstar ? 3 : 0);
+    if (!fp64 && with_lstar) ++g->fs_lstar32;
     ++g->launches;
     if (fast) {
         CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
@@ -406,12 +447,76 @@ rt3d_status os_solve_dev(rt3d_grid *g, const double *Jfs, const double *J, const
                          int max_sweeps, double tol) {
     CK(launch_os_init((int)g->N, Jfs, J, extra, g->inv_diag, g->r, g->dJ[0],
                       g->a64 ? nullptr : g->dJ32[0], g->st, g->stream));
-    for (int m = 1; m <= max_sweeps; ++m)
-        CK(launch_os_sweep(g->nx, g->ny, g->nz, g->a, g->a64, g->inv_diag, g->r, g->dJ,
-                           g->a64 ? nullptr : g->dJ32, m, tol, g->st, g->stream, g->per));
-    CK(launch_os_finish(max_sweeps, tol, g->st, g->stream));
-    g->launches += max_sweeps + 2;
+    ++g->launches;
+    if (g->os_kind == kOsJacobi) {
+        for (int m = 1; m <= max_sweeps; ++m)
+            CK(launch_os_sweep(g->nx, g->ny, g->nz, g->a, g->a64, g->inv_diag, g->r, g->dJ,
+                               g->a64 ? nullptr : g->dJ32, m, tol, g->st, g->stream, g->per));
+        CK(launch_os_finish(max_sweeps, tol, g->st, g->stream));
+        g->launches += max_sweeps + 1;
+        return RT3D_OK;
+    }
+    if (g->os_kind == kOsGaussSeidel) {
+        // eight launches per sweep; the stop flag is read every fourth sweep
+        const ColourGeo cg = colour_geo(g->nx, g->ny, g->nz);
+        for (int m = 1; m <= max_sweeps; ++m) {
+            CK(launch_gs_sweep(g->nx, g->ny, g->nz, cg, g->a, g->a64, g->inv_diag, g->r,
+                               g->dJ[(m - 1) & 1], g->dJ[m & 1], m, tol, g->st, g->stream, g->per));
+            g->launches += 8;
+            if ((m & 3) == 0 && m < max_sweeps) {
+                int done = 0;
+                CK(cudaMemcpyAsync(&done, &g->st->done, sizeof done, cudaMemcpyDeviceToHost,
+                                   g->stream));
+                CK(cudaStreamSynchronize(g->stream));
+                if (done) break;
+            }
+        }
+        CK(launch_os_finish(max_sweeps, tol, g->st, g->stream));
+        ++g->launches;
+        return RT3D_OK;
+    }
+    // BiCGStab from dJ = 0 (dJ[0] holds the iterate), stop on ||res||_2 <=
+    // tol ||r||_2 or after max_sweeps iterations, or at a breakdown (omega = 0)
+    const int n = (int)g->N;
+    if (!g->bicg) {
+        TRY(g->alloc(&g->bres, (size_t)n));
+        TRY(g->alloc(&g->brh, (size_t)n));
+        TRY(g->alloc(&g->bp, (size_t)n));
+        TRY(g->alloc(&g->bvv, (size_t)n));
+        TRY(g->alloc(&g->bsv, (size_t)n));
+        TRY(g->alloc(&g->bt, (size_t)n));
+        TRY(g->alloc(&g->bicg, 1));
+    }
+    const BicgVecs v{g->dJ[0], g->bres, g->brh, g->bp, g->bvv, g->bsv, g->bt};
+    CK(launch_bicg_init(n, g->r, v, g->bicg, g->stream));
+    ++g->launches;
+    BicgState hs{};
+    CK(cudaMemcpyAsync(&hs, g->bicg, sizeof hs, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    const double nr0 = std::sqrt(hs.rr0);
+    int k = 0;
+    if (nr0 > 0.0) {
+        while (k < max_sweeps) {
+            CK(launch_bicg_iteration(g->nx, g->ny, g->nz, g->a, g->a64, g->diag, v, g->bicg,
+                                     g->stream, g->per));
+            g->launches += 9;
+            ++k;
+            CK(cudaMemcpyAsync(&hs, g->bicg, sizeof hs, cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            if (!(hs.rr == hs.rr)) return fail(RT3D_ENUMERIC, "NaN in the BiCGStab residual");
+            if (std::sqrt(hs.rr) <= tol * nr0) break;
+            if (hs.omega == 0.0) break;
+        }
+    }
+    CK(launch_os_set_result(n, g->dJ[0], g->dJ[k & 1], k, g->st, g->stream));
+    ++g->launches;
     return RT3D_OK;
+}
+
+// OS solve caps of the solver's own unit: a BiCGStab iteration applies the
+// matrix twice, so it counts as two sweeps of a cap given in sweeps.
+int os_cap(const rt3d_grid *g, int sweeps) {
+    return g->os_kind == kOsBicgstab ? std::max(1, sweeps / 2) : sweeps;
 }
 
 // Work buffers of the formal solution and the solvers.
@@ -446,8 +551,9 @@ rt3d_status alloc_work(rt3d_grid *g) {
     TRY(g->alloc(&g->Jrep, 4 * N));
     CK(cudaMemsetAsync(g->Jrep, 0, sizeof(double) * 4 * N, s));
     if (!g->sph && !g->fs64) TRY(g->alloc(&g->pairs, 4 * N));
-    if (g->a64) TRY(g->alloc(reinterpret_cast<double **>(&g->a), os_coef_count(N)));
-    else TRY(g->alloc(reinterpret_cast<float **>(&g->a), os_coef_count(N)));
+    if (g->a64) TRY(g->alloc(reinterpret_cast<double **>(&g->a), os_coef_alloc(N)));
+    else TRY(g->alloc(reinterpret_cast<float **>(&g->a), os_coef_alloc(N)));
+    TRY(g->alloc(&g->diag, N));
     TRY(g->alloc(&g->st, 1));
     CK(cudaMemcpyAsync(g->dJ_dev, g->dJ, sizeof(double *) * 2, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(g->st, 0, sizeof(OsState), s));
@@ -859,14 +965,14 @@ rt3d_status ali_iteration(rt3d_grid *g, const FsParams &fp, bool fp64, int max_s
     TRY(run_fs(g, fp, fp64, build));
     if (build) {
         CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag,
-                          g->stream, g->per));
+                          g->stream, g->per, g->os_kind == kOsGaussSeidel, g->diag));
         CK(cudaMemcpyAsync(g->chi_ref, g->chi, sizeof(double) * N, cudaMemcpyDeviceToDevice,
                            g->stream));
         CK(cudaMemcpyAsync(g->eps_ref, g->eps, sizeof(double) * N, cudaMemcpyDeviceToDevice,
                            g->stream));
         g->lstar_valid = true;
     }
-    TRY(os_solve_dev(g, g->Jfs, g->J, nullptr, max_sweeps, sweep_tol));
+    TRY(os_solve_dev(g, g->Jfs, g->J, nullptr, os_cap(g, max_sweeps), sweep_tol));
     TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));
     CKL(launch_ali_update(N, g->J, g->dJ_dev, g->st, nullptr, g->stream));
     TRY(read_scalar_d(g, offsetof(OsState, rel), rel));
@@ -936,7 +1042,7 @@ rt3d_status apply_A(rt3d_grid *g, const FsParams &fphom, bool fp64, const double
 // RT3D_PRECOND_SWEEPS sweeps, stopped at a change of RT3D_PRECOND_TOL relative
 // to the iterate (the paper's OS solve; the same settings as the ALI step)
 rt3d_status precond(rt3d_grid *g, const double *v, double *z) {
-    TRY(os_solve_dev(g, nullptr, nullptr, v, RT3D_PRECOND_SWEEPS, RT3D_PRECOND_TOL));
+    TRY(os_solve_dev(g, nullptr, nullptr, v, os_cap(g, RT3D_PRECOND_SWEEPS), RT3D_PRECOND_TOL));
     CKL(launch_copy_buf((int)g->N, g->dJ_dev, g->st, z, g->stream));
     return RT3D_OK;
 }
@@ -1055,7 +1161,7 @@ rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p
             else ++s.fs_fp32;
             if (build) {
                 CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag,
-                                   g->stream, g->per));
+                                   g->stream, g->per, g->os_kind == kOsGaussSeidel, g->diag));
                 CK(cudaMemcpyAsync(g->chi_ref, g->chi, sizeof(double) * n, cudaMemcpyDeviceToDevice,
                                    g->stream));
                 CK(cudaMemcpyAsync(g->eps_ref, g->eps, sizeof(double) * n, cudaMemcpyDeviceToDevice,
@@ -1080,13 +1186,30 @@ rt3d_status krylov_solve(rt3d_grid *g, const FsParams &fp, const FsParams &fp64p
         }
         return ri;
     };
+    // Float-float residuals are accurate to about 1e-12 of J; where the
+    // problem amplifies that floor above tol (eps near 1e-8 in optically
+    // thick media) a float-float residual stops falling between rounds, and
+    // the refinement then takes its residuals from the FP64 formal solution.
+    bool ff_ok = true;
+    double res_ff_prev = -1.0;
     for (int round = 0; round < 60 && it < max_iter; ++round) {
         // the first residual also builds Lambda* (FP32 or FP64 kind)
-        int kind = res64 ? ((g->ff_refine && g->lstar_valid) ? 2 : 1) : 0;
+        int kind = res64 ? ((g->ff_refine && ff_ok && g->lstar_valid) ? 2 : 1) : 0;
         TRY(residual(kind, &res));
         // gain < 0: unknown (first round, or a residual relative to J = 0)
         est = (kind != 0 && gain >= 0.0) ? gain * res : -1.0;
         int ri = record(kind, res, est);
+        if (kind == 2) {
+            const bool stalled = res_ff_prev > 0.0 && res > 0.1 * res_ff_prev;
+            res_ff_prev = res;
+            if (stalled && !(est >= 0.0 && est <= tol)) {
+                ff_ok = false;  // this and later rounds: FP64 residuals
+                kind = 1;
+                TRY(residual(1, &res));
+                est = gain >= 0.0 ? gain * res : -1.0;
+                ri = record(1, res, est);
+            }
+        }
         if (kind == 2 && est >= 0.0 && est <= tol) {
             // float-float estimate met: the FP64 formal solution decides
             kind = 1;
@@ -1221,8 +1344,8 @@ rt3d_status line_iteration(rt3d_grid *g, const FsParams &fp, const std::vector<d
     }
     if (build)
         CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lbar, g->eps, g->a, g->a64, g->inv_diag,
-                           g->stream, g->per));
-    TRY(os_solve_dev(g, g->jbar_fs, g->J, nullptr, 50, 1e-3));
+                           g->stream, g->per, g->os_kind == kOsGaussSeidel, g->diag));
+    TRY(os_solve_dev(g, g->jbar_fs, g->J, nullptr, os_cap(g, 50), 1e-3));
     TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));
     CKL(launch_ali_update(n, g->J, g->dJ_dev, g->st, nullptr, g->stream));
     TRY(read_scalar_d(g, offsetof(OsState, rel), rel));
@@ -1272,6 +1395,30 @@ rt3d_status rt3d_grid_get_info(const rt3d_grid *g, rt3d_grid_info *info) {
     info->fs_shape.widen = g->fs_shape.widen;
     info->fs_shape.branchless = g->fs_shape.branchless;
     for (int i = 0; i < RT3D_FS_TUNE_SHAPES; ++i) info->fs_tune_ms[i] = g->fs_tune_ms[i];
+    info->sm_count = device_sm_count();
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_grid_set_os_solver(rt3d_grid *g, int solver) {
+    if (!g) return fail(RT3D_EINVAL, "NULL grid");
+    if (solver != RT3D_OS_JACOBI && solver != RT3D_OS_GAUSS_SEIDEL && solver != RT3D_OS_BICGSTAB)
+        return fail(RT3D_EINVAL, "OS solver %d not available", solver);
+    const int old = g->os_kind;
+    g->os_kind = solver == RT3D_OS_GAUSS_SEIDEL ? kOsGaussSeidel
+                 : solver == RT3D_OS_BICGSTAB   ? kOsBicgstab
+                                                : kOsJacobi;
+    // a band in use keeps working: its coefficients in the new solver's layout
+    if (g->lstar_valid && (old == kOsGaussSeidel) != (g->os_kind == kOsGaussSeidel)) {
+        CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag,
+                           g->stream, g->per, g->os_kind == kOsGaussSeidel, g->diag));
+        CK(cudaStreamSynchronize(g->stream));
+    }
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_grid_invalidate_lstar(rt3d_grid *g) {
+    if (!g) return fail(RT3D_EINVAL, "NULL grid");
+    g->lstar_valid = false;
     return RT3D_OK;
 }
 
@@ -1402,7 +1549,8 @@ rt3d_status rt3d_os_solve(rt3d_grid *g, const double *lstar, const double *eps, 
     CK(cudaMemcpyAsync(g->eps, eps, N * sizeof(double), cudaMemcpyDefault, g->stream));
     CK(cudaMemcpyAsync(g->tmp, r, N * sizeof(double), cudaMemcpyDefault, g->stream));
     g->lstar_valid = false;  // the grid's Lambda* now holds the caller's band
-    CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag, g->stream, g->per));
+    CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lstar, g->eps, g->a, g->a64, g->inv_diag, g->stream,
+                        g->per, g->os_kind == kOsGaussSeidel, g->diag));
     TRY(os_solve_dev(g, nullptr, nullptr, g->tmp, max_sweeps, tol));
     CKL(launch_copy_buf((int)N, g->dJ_dev, g->st, g->delta, g->stream));
     TRY(deliver(g, dJ_out, g->delta, N));
@@ -1439,7 +1587,8 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     const size_t N = (size_t)g->N;
     const int n = (int)N;
     rt3d_solve_stats s{};
-    g->fs_ms[0] = g->fs_ms[1] = g->fs_ms[2] = 0.0;
+    g->fs_ms[0] = g->fs_ms[1] = g->fs_ms[2] = g->fs_ms[3] = 0.0;
+    g->fs_lstar32 = 0;
     g->launches = 0;
     TRY(reset_scalar(g, offsetof(OsState, sweeps_total), sizeof(unsigned long long)));
     TRY(load_problem(g, chi, eps, B));
@@ -1457,7 +1606,9 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
         TRY(deliver(g, J_inout, g->J, N));
         CK(cudaStreamSynchronize(g->stream));
         TRY(collect_events(g));
-        s.fs32_ms = g->fs_ms[0];
+        s.fs32_ms = g->fs_ms[0] + g->fs_ms[3];
+        s.fs32_lstar_ms = g->fs_ms[3];
+        s.fs_lstar = g->fs_lstar32;
         s.fs64_ms = g->fs_ms[1];
         s.fsff_ms = g->fs_ms[2];
         {
@@ -1526,7 +1677,7 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
             if (!(res == res)) return fail(RT3D_ENUMERIC, "NaN in the FP64 residual");
             if (conv) break;  // that was the certification of the corrected J
             // delta_0 = M^-1 r64, then ALI on delta with the homogeneous FS
-            TRY(os_solve_dev(g, nullptr, nullptr, g->r64, max_sweeps, sweep_tol));
+            TRY(os_solve_dev(g, nullptr, nullptr, g->r64, os_cap(g, max_sweeps), sweep_tol));
             CKL(launch_copy_buf(n, g->dJ_dev, g->st, g->delta, g->stream));
             double drel = 1.0, dacc = 1.0;
             Progress dprog;
@@ -1539,7 +1690,7 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
                 else ++s.fs_fp64;
                 ++it;
                 // r = Lambda_hom((1-eps) delta) + r64 - delta
-                TRY(os_solve_dev(g, g->Jfs, g->delta, g->r64, max_sweeps, sweep_tol));
+                TRY(os_solve_dev(g, g->Jfs, g->delta, g->r64, os_cap(g, max_sweeps), sweep_tol));
                 TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));
                 CKL(launch_ali_update(n, g->delta, g->dJ_dev, g->st, nullptr, g->stream));
                 TRY(read_scalar_d(g, offsetof(OsState, rel), &drel));
@@ -1572,7 +1723,9 @@ rt3d_status rt3d_solve(rt3d_grid *g, const double *chi, const double *eps, const
     TRY(deliver(g, J_inout, g->J, N));
     CK(cudaStreamSynchronize(g->stream));
     TRY(collect_events(g));
-    s.fs32_ms = g->fs_ms[0];
+    s.fs32_ms = g->fs_ms[0] + g->fs_ms[3];
+    s.fs32_lstar_ms = g->fs_ms[3];
+    s.fs_lstar = g->fs_lstar32;
     s.fs64_ms = g->fs_ms[1];
     s.fsff_ms = g->fs_ms[2];
     {
@@ -1598,7 +1751,7 @@ rt3d_status rt3d_line_solve(rt3d_grid *g, int nl, const double *chi, const doubl
     if (g->sph) return fail(RT3D_EINVAL, "line transfer needs the Cartesian grid");
     if (nl < 1 || nl > 65536) return fail(RT3D_EINVAL, "nlambda %d", nl);
     if (!(tol > 0.0) || max_iter < 1) return fail(RT3D_EINVAL, "bad tol or max_iter");
-    if (is_device_ptr(scale) || is_device_ptr(wphi))
+    if (ptr_kind(scale) != 0 || ptr_kind(wphi) != 0)
         return fail(RT3D_EINVAL, "scale and wphi must be host arrays");
     std::vector<double> sc(nl), negw(nl);
     double wsum = 0.0;
@@ -1615,7 +1768,8 @@ rt3d_status rt3d_line_solve(rt3d_grid *g, int nl, const double *chi, const doubl
     const size_t N = (size_t)g->N;
     rt3d_line_stats s{};
     s.est_error = -1.0;
-    g->fs_ms[0] = g->fs_ms[1] = g->fs_ms[2] = 0.0;
+    g->fs_ms[0] = g->fs_ms[1] = g->fs_ms[2] = g->fs_ms[3] = 0.0;
+    g->fs_lstar32 = 0;
     g->launches = 0;
     TRY(reset_scalar(g, offsetof(OsState, sweeps_total), sizeof(unsigned long long)));
     TRY(line_setup(g, negw));
@@ -1674,7 +1828,8 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     const size_t N = (size_t)g->N, nf = (size_t)g->nx * g->ny, L = (size_t)nl;
     rt3d_batch_stats bs{};
     bs.nlambda = nl;
-    g->fs_ms[0] = g->fs_ms[1] = g->fs_ms[2] = 0.0;
+    g->fs_ms[0] = g->fs_ms[1] = g->fs_ms[2] = g->fs_ms[3] = 0.0;
+    g->fs_lstar32 = 0;
     g->launches = 0;
     TRY(batch_setup(g, nl));
     cudaStream_t s = g->stream;
@@ -1882,7 +2037,7 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     bs.converged = nconv;
     bs.max_est_error = max_est;
     bs.max_residual64 = max_res;
-    bs.fs32_ms = g->fs_ms[0] + bs.batch_ms;
+    bs.fs32_ms = g->fs_ms[0] + g->fs_ms[3] + bs.batch_ms;
     bs.fs64_ms = g->fs_ms[1];
     bs.fsff_ms = g->fs_ms[2];
     bs.launches = g->launches;

@@ -287,7 +287,7 @@ void launch_b_fs_t(const BatchFsParams &p, dim3 grid, int block, int conv, cudaS
 cudaError_t launch_b_source(const BatchFsParams &p, int nl, const double *J, const double *eps,
                             const double *B, cudaStream_t s) {
     const long long n = (long long)p.nx * p.ny * p.nz;
-    b_source<<<dim3(grid_x(n, 256, 152 * 2), nl), 256, 0, s>>>(p.nx, p.ny, p.nz, J, eps, B, p.chiS,
+    b_source<<<dim3(grid_x(n, 256, 2 * device_sm_count()), nl), 256, 0, s>>>(p.nx, p.ny, p.nz, J, eps, B, p.chiS,
                                                               p.bs);
     return cudaGetLastError();
 }
@@ -314,7 +314,7 @@ cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, double *J, co
                                    int max_iter, bool parabolic, const FsShape &shape,
                                    cudaStream_t s) {
     const long long n = (long long)p.nx * p.ny * p.nz;
-    const int gx = grid_x(n, 256, 152 * 2);
+    const int gx = grid_x(n, 256, 2 * device_sm_count());
     b_source<<<dim3(gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, J, eps, B, p.chiS, p.bs);
     const cudaError_t fe = launch_b_fs(p, nl, shape, parabolic, s);
     if (fe != cudaSuccess) return fe;

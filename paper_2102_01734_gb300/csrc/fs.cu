@@ -862,7 +862,8 @@ cudaError_t launch_fs64_fast(const FsParams &p, bool parabolic, cudaStream_t s) 
 cudaError_t launch_fold(int nx, int ny, int nz, double *Jrep, double *J, cudaStream_t s) {
     const long long n = (long long)nx * ny * nz;
     long long b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    const long long cap = 16LL * device_sm_count();
+    if (b > cap) b = cap;
     fold_kernel<<<(int)b, 256, 0, s>>>(nx, ny, nz, Jrep, J);
     return cudaGetLastError();
 }

@@ -198,7 +198,8 @@ __global__ void recff_kernel(long long total, const double2 *rec64, float4 *out)
 
 int blocks_cap(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
-    if (b > 152 * 16) b = 152 * 16;
+    const long long cap = 16LL * device_sm_count();
+    if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
 }
 

@@ -65,24 +65,24 @@ int blocks_for(int n, int threads, int cap) {
 
 cudaError_t launch_multi_dot(int n, const double *const *V, int k, const double *w, double *out,
                              cudaStream_t s) {
-    dim3 grid(blocks_for(n, 256, 152 * 2), k);
+    dim3 grid(blocks_for(n, 256, 2 * device_sm_count()), k);
     multi_dot_kernel<<<grid, 256, 0, s>>>(n, V, w, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_multi_axpy(int n, double *w, const double *const *V, const double *coef, int k,
                               cudaStream_t s) {
-    multi_axpy_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(n, w, V, coef, k);
+    multi_axpy_kernel<<<blocks_for(n, 256, 8 * device_sm_count()), 256, 0, s>>>(n, w, V, coef, k);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scale_copy(int n, const double *src, double alpha, double *dst, cudaStream_t s) {
-    scale_copy_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(n, src, alpha, dst);
+    scale_copy_kernel<<<blocks_for(n, 256, 8 * device_sm_count()), 256, 0, s>>>(n, src, alpha, dst);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sub(int n, const double *a, const double *b, double *out, cudaStream_t s) {
-    sub_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(n, a, b, out);
+    sub_kernel<<<blocks_for(n, 256, 8 * device_sm_count()), 256, 0, s>>>(n, a, b, out);
     return cudaGetLastError();
 }
 

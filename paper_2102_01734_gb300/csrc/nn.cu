@@ -370,7 +370,8 @@ __global__ void adam_kernel(float *w, const float *gw, float *m, float *v, int n
 
 int gsz(long long n) {
     long long b = (n + 255) / 256;
-    return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+    const long long cap = 16LL * device_sm_count();
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
 }  // namespace

@@ -162,13 +162,16 @@ rt3d_status na_fail(rt3d_status s, const char *fmt, ...) {
     return s;
 }
 
-bool na_is_device(const void *p) {
+// Whether p is memory the kernels can use on device dev: device memory of
+// dev itself, or managed memory. Device memory of another device is
+// rejected (without peer access a kernel on dev cannot read it).
+bool na_is_device(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
 }
 
 }  // namespace
@@ -186,12 +189,21 @@ extern "C" rt3d_status rt3d_os_solve_noalloc(int nx, int ny, int nz, const doubl
                        (int)RT3D_NOALLOC_MAX_VOXELS);
     if (max_sweeps < 1 || max_sweeps > kMaxSweeps)
         return na_fail(RT3D_EINVAL, "max_sweeps %d outside 1..%d", max_sweeps, kMaxSweeps);
-    if (!na_is_device(lstar) || !na_is_device(eps) || !na_is_device(r) || !na_is_device(dJ_out))
-        return na_fail(RT3D_EINVAL, "all arrays must be device memory");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(RT3D_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return na_fail(RT3D_EINVAL, "device %d out of range", dev);
+    if (!na_is_device(lstar, dev) || !na_is_device(eps, dev) || !na_is_device(r, dev) ||
+        !na_is_device(dJ_out, dev))
+        return na_fail(RT3D_EINVAL, "all arrays must be device memory of the current device %d",
+                       dev);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return na_fail(RT3D_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+    if (cap != cudaStreamCaptureStatusNone)
+        return na_fail(RT3D_EINVAL, "the stream is being captured: this call synchronises its "
+                                    "stream and cannot be captured");
     double *buf = nullptr;
     NoallocState *st = nullptr;
     {
@@ -210,7 +222,6 @@ extern "C" rt3d_status rt3d_os_solve_noalloc(int nx, int ny, int nz, const doubl
         buf = g_buf_addr[dev];
         st = g_state_addr[dev];
     }
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int n = (int)N;
     int blocks = (n + 255) / 256;
     if (blocks < 2) blocks = 2;  // >= 257 threads reset the maxima

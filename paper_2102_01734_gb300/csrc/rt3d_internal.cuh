@@ -178,6 +178,26 @@ __host__ __device__ inline long long os_coef_index(int plane, long long v) {
 }
 __host__ __device__ inline long long os_coef_count(long long N) { return ((N + 31) >> 5) * 26 * 32; }
 
+// Colour layout of the same coefficients for the eight-colour Gauss-Seidel
+// sweep: colour c = (x&1) + 2(y&1) + 4(z&1); the voxels of a colour form a
+// half-resolution sub-grid (x-major, index k); each colour holds blocks of 32
+// consecutive k with their 26 planes contiguous, so the launch of one colour
+// reads its coefficients as the Jacobi sweep reads its own.
+struct ColourGeo {
+    int nxc[8], nyc[8];
+    long long cnt[8];  // voxels of colour c
+    long long blk[8];  // first 32-voxel block of colour c
+};
+__host__ __device__ inline long long os_colour_index(int plane, long long blk0, long long k) {
+    return ((blk0 + (k >> 5)) * 26 + plane) * 32 + (k & 31);
+}
+ColourGeo colour_geo(int nx, int ny, int nz);
+// coefficients to allocate for either layout
+__host__ __device__ inline long long os_coef_alloc(long long N) { return os_coef_count(N) + 8 * 26 * 32; }
+
+// OS solver of a grid (rt3d_grid_set_os_solver)
+enum OsKind { kOsJacobi = 0, kOsGaussSeidel = 1, kOsBicgstab = 2 };
+
 #ifdef __CUDACC__
 // Coordinate of the neighbour at offset -1 / +1 along an axis of n cells:
 // wrapped on a periodic axis, else clamped to the cell itself (its
@@ -217,9 +237,38 @@ __device__ __forceinline__ A os_stencil(const A *__restrict__ a, const T *__rest
     return acc;
 }
 #endif
+// folded coefficients a (os_coef_index layout, or the colour layout when
+// colour is set), 1/diag and, when diag is given, diag itself
 cudaError_t launch_os_prep(int nx, int ny, int nz, const double *lstar, const double *eps,
                            void *a, bool a64, double *inv_diag, cudaStream_t s,
-                           Periodic per = {true, true, false});
+                           Periodic per = {true, true, false}, bool colour = false,
+                           double *diag = nullptr);
+// One sweep of the eight-colour Gauss-Seidel iteration (colour layout of a):
+// for colour 0 .. 7, every voxel of the colour from the neighbours' values
+// of this sweep (earlier colours, in dst) or of the last (src); the stop test
+// of sweep m - 1 first (as launch_os_sweep).
+cudaError_t launch_gs_sweep(int nx, int ny, int nz, const ColourGeo &cg, const void *a, bool a64,
+                            const double *inv_diag, const double *r, const double *src,
+                            double *dst, int m, double tol, OsState *st, cudaStream_t s,
+                            Periodic per);
+// BiCGStab on [1 - Lambda*(1 - eps)] x = r from x = 0 (van der Vorst):
+// device scalars and the kernels of one iteration.
+struct BicgState {
+    double rho, alpha, omega;  // of the last iteration
+    double rho1, rhv, tt, ts, rr;  // dot products (accumulated by the kernels)
+    double rr0;
+};
+struct BicgVecs {
+    double *x, *res, *rh, *p, *vv, *sv, *t;
+};
+cudaError_t launch_bicg_init(int n, const double *r, const BicgVecs &v, BicgState *bs,
+                             cudaStream_t s);
+cudaError_t launch_bicg_iteration(int nx, int ny, int nz, const void *a, bool a64,
+                                  const double *diag, const BicgVecs &v, BicgState *bs,
+                                  cudaStream_t s, Periodic per);
+// dst = src; st: count = k, done, sweeps_total += k
+cudaError_t launch_os_set_result(int n, const double *src, double *dst, int k, OsState *st,
+                                 cudaStream_t s);
 cudaError_t launch_os_init(int n, const double *Jfs, const double *J, const double *rhs_extra,
                            const double *inv_diag, double *r, double *dJ0, float *dJ0_32,
                            OsState *st, cudaStream_t s);
@@ -340,6 +389,10 @@ cudaError_t launch_sph_fs_fast(const SphFsParams &p, const float4 *rec, const in
 // per-segment records (replicated index bits, J weight, l/2, l/2)
 cudaError_t launch_sph_rec(long long nseg, const int *crep, const double *len64, const double *cw64,
                            float4 *rec, cudaStream_t s);
+
+// Streaming multiprocessors of the current device (queried once per device
+// with cudaDeviceGetAttribute), for launches capped at a multiple of them.
+int device_sm_count();
 
 // Sets the message returned by rt3d_last_error() on this thread.
 void set_last_error(const char *msg);

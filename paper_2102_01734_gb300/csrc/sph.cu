@@ -705,7 +705,8 @@ __global__ void sph_rec_kernel(long long nseg, const int *crep, const double *le
 cudaError_t launch_sph_rec(long long nseg, const int *crep, const double *len64, const double *cw64,
                            float4 *rec, cudaStream_t s) {
     long long b = (nseg + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    const long long cap = 16LL * device_sm_count();
+    if (b > cap) b = cap;
     sph_rec_kernel<<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(nseg, crep, len64, cw64, rec);
     return cudaGetLastError();
 }

@@ -34,6 +34,7 @@ SPHERICAL = 1
 LINEAR, PARABOLIC = 0, 1
 FP64, FP32_FS_FP64_ALI, FP32_FS_FF_REFINE = 0, 1, 2
 ACCEL_NONE, ACCEL_KRYLOV = 0, 1
+OS_JACOBI, OS_GAUSS_SEIDEL, OS_BICGSTAB = 0, 1, 2
 
 _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 
@@ -56,7 +57,8 @@ class SolveStats(ctypes.Structure):
                 ("residual64", _c_double), ("est_error", _c_double), ("seconds", _c_double),
                 ("fs32_ms", _c_double), ("fs64_ms", _c_double), ("launches", ctypes.c_longlong),
                 ("fs_ff", _c_int), ("fsff_ms", _c_double), ("rounds", _c_int), ("round_fp64", _c_int * 16), ("round_fs", _c_int * 16),
-                ("round_res", _c_double * 16), ("round_est", _c_double * 16)]
+                ("round_res", _c_double * 16), ("round_est", _c_double * 16),
+                ("fs_lstar", _c_int), ("fs32_lstar_ms", _c_double)]
 
     def as_dict(self):
         out = {k: getattr(self, k) for k, _ in self._fields_}
@@ -107,7 +109,7 @@ class BatchStats(ctypes.Structure):
 class GridInfo(ctypes.Structure):
     _fields_ = [("nangles", _c_int), ("kmax", _c_int), ("segments", ctypes.c_longlong),
                 ("device_bytes", ctypes.c_longlong), ("fs_shape", FsShape),
-                ("fs_tune_ms", ctypes.c_float * FS_TUNE_SHAPES)]
+                ("fs_tune_ms", ctypes.c_float * FS_TUNE_SHAPES), ("sm_count", _c_int)]
 
 
 class RT3DError(RuntimeError):
@@ -132,6 +134,8 @@ def load(path: str | None = None):
     lib.rt3d_grid_create.argtypes = [P(GridDesc), P(_vp)]
     lib.rt3d_grid_destroy.argtypes = [_vp]
     lib.rt3d_grid_destroy.restype = None
+    lib.rt3d_grid_invalidate_lstar.argtypes = [_vp]
+    lib.rt3d_grid_set_os_solver.argtypes = [_vp, _c_int]
     lib.rt3d_grid_get_info.argtypes = [_vp, P(GridInfo)]
     lib.rt3d_grid_set_fs_shape.argtypes = [_vp, ctypes.POINTER(FsShape)]
     lib.rt3d_fs_tune_shape.argtypes = [_c_int, ctypes.POINTER(FsShape)]
@@ -262,6 +266,16 @@ def grid_get_info(h) -> dict:
     out["fs_tune_ms"] = list(info.fs_tune_ms)
     out["fs_shape"] = info.fs_shape.as_tuple()
     return out
+
+
+def grid_set_os_solver(h, solver: int) -> None:
+    """OS solver of the grid: OS_JACOBI, OS_GAUSS_SEIDEL or OS_BICGSTAB."""
+    _check(load().rt3d_grid_set_os_solver(h, int(solver)))
+
+
+def grid_invalidate_lstar(h) -> None:
+    """Drops the grid's Lambda* band: the next solve or ALI step builds it."""
+    _check(load().rt3d_grid_invalidate_lstar(h))
 
 
 def fs_tune_shape(i: int) -> tuple:
@@ -440,6 +454,12 @@ class Grid:
 
     def info(self):
         return grid_get_info(self.handle)
+
+    def invalidate_lstar(self):
+        grid_invalidate_lstar(self.handle)
+
+    def set_os_solver(self, solver):
+        grid_set_os_solver(self.handle, solver)
 
     def set_fs_shape(self, shape):
         grid_set_fs_shape(self.handle, shape)

@@ -122,6 +122,9 @@ class UNet:
         return dX
 
     def _wgrad(self, X, dY, name, S, shape):
+        # the layer's input activation and output gradient of the last
+        # backward pass, kept (as references) for inspection
+        self.wgrad_inputs[name] = (X, dY, shape)
         lib = _lib()
         ci, co = self.W32[name].shape[1], self.W32[name].shape[2]
         nz, ny, nx = shape
@@ -214,6 +217,7 @@ class UNet:
         S = dY.shape[0]
         s1s, s2s, s3s = shape, half(shape), half(half(shape))
         self.gW = {n: torch.zeros_like(w) for n, w in self.W32.items()}
+        self.wgrad_inputs = {}
         self.gb = {n: torch.zeros_like(b) for n, b in self.b32.items()}
         self._wgrad(c["u1"], dY, "out", S, s1s)
         d = self._conv_T(dY, "out", S, s1s)

@@ -48,11 +48,14 @@ def test_null_arguments_are_einval(lib):
     assert lib.rt3d_solve(None, None, None, None, None, None, 1e-8, 10, None) == rt3d.EINVAL
     st = rt3d.SolveStats()
     # 4 ints, 6 doubles, 1 long long, fs_ff (+4 padding), fsff_ms, rounds,
-    # 2 x 16 ints (+4 padding), 2 x 16 doubles
-    assert ctypes.sizeof(st) == 4 * 4 + 6 * 8 + 8 + 8 + 8 + 4 + 2 * 16 * 4 + 4 + 2 * 16 * 8
+    # 2 x 16 ints (+4 padding), 2 x 16 doubles, fs_lstar (+4 padding), fs32_lstar_ms
+    assert ctypes.sizeof(st) == (4 * 4 + 6 * 8 + 8 + 8 + 8 + 4 + 2 * 16 * 4 + 4 + 2 * 16 * 8
+                                 + 4 + 4 + 8)
     assert lib.rt3d_formal_solution_ff(None, None, None, None, None) == rt3d.EINVAL
-    assert ctypes.sizeof(rt3d.GridInfo) == 2 * 4 + 2 * 8 + 4 * 4 + 8 * 4
+    assert ctypes.sizeof(rt3d.GridInfo) == 2 * 4 + 2 * 8 + 4 * 4 + 8 * 4 + 4 + 4  # + sm_count, padding
     assert lib.rt3d_grid_set_fs_shape(None, None) == rt3d.EINVAL
+    assert lib.rt3d_grid_invalidate_lstar(None) == rt3d.EINVAL
+    assert lib.rt3d_grid_set_os_solver(None, rt3d.OS_JACOBI) == rt3d.EINVAL
     assert lib.rt3d_line_solve(None, 1, None, None, None, None, None, None, None, 1e-8, 10,
                                None) == rt3d.EINVAL
     # 3 ints (+4 padding), 4 doubles, 1 long long

@@ -21,10 +21,14 @@ def rt3d():
 
 
 def _batch(n, nl, seed):
+    """nl wavelengths drawn as the batched workload draws them (eps log-uniform
+    in [1e-8, 1e-1], opacity scale 10^U(-3, 3)), the last two replaced by the
+    corners of that range: eps = 1e-8 with scales 1e-3 and 1e3."""
     chi, _, B, bc = inputs.cartesian_config(n, 1e-2, seed=seed)
     eps_l, scale_l = inputs.batched_wavelengths(nl, seed=3)
-    eps_l = np.clip(eps_l, 1e-4, None)  # keep the oracle's ALI reference short
-    scale_l = np.clip(scale_l, 1e-2, 1e1)
+    eps_l, scale_l = np.array(eps_l, dtype=float), np.array(scale_l, dtype=float)
+    eps_l[-2:] = 1e-8
+    scale_l[-2:] = (1e-3, 1e3)
     chis = np.stack([s * chi for s in scale_l])
     epss = np.stack([np.full(chi.shape, e) for e in eps_l])
     Bs = np.stack([B] * nl)

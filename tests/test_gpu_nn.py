@@ -117,29 +117,34 @@ def test_pool_upsample_against_oracle(ws):
 
 def _oracle_unet(net, X, shape, target_corr):
     """FP64 forward/backward of the same U-Net with the oracle's layers (BF16
-    weights); returns (y, {name: dW})."""
+    weights), rounding to BF16 wherever the GPU path stores a tensor in BF16
+    (every activation after bias and ReLU, pooled values, the loss gradient,
+    every data gradient after a transposed convolution, the small-grid part
+    of a concatenation's gradient and the skip sums), so that the remaining
+    difference is the compounding of single rounding flips; returns
+    (y, {name: dW})."""
     W = {n: w_oracle(net.Wt[n].float().cpu().numpy().astype(np.float64)) for n in net.Wt}
     b = {n: net.b32[n].cpu().numpy().astype(np.float64) for n in net.b32}
     relu = lambda t: np.maximum(t, 0.0)
     s1, s2 = shape, tuple((n + 1) // 2 for n in shape)
-    a1 = relu(oc.conv3d(X, W["e1a"], b["e1a"]))
-    s1v = relu(oc.conv3d(a1, W["e1b"], b["e1b"]))
-    p1 = oc.pool(s1v)
-    a2 = relu(oc.conv3d(p1, W["e2a"], b["e2a"]))
-    s2v = relu(oc.conv3d(a2, W["e2b"], b["e2b"]))
-    p2 = oc.pool(s2v)
-    a3 = relu(oc.conv3d(p2, W["b_a"], b["b_a"]))
-    bb = relu(oc.conv3d(a3, W["b_b"], b["b_b"]))
+    a1 = bf(relu(oc.conv3d(X, W["e1a"], b["e1a"])))
+    s1v = bf(relu(oc.conv3d(a1, W["e1b"], b["e1b"])))
+    p1 = bf(oc.pool(s1v))
+    a2 = bf(relu(oc.conv3d(p1, W["e2a"], b["e2a"])))
+    s2v = bf(relu(oc.conv3d(a2, W["e2b"], b["e2b"])))
+    p2 = bf(oc.pool(s2v))
+    a3 = bf(relu(oc.conv3d(p2, W["b_a"], b["b_a"])))
+    bb = bf(relu(oc.conv3d(a3, W["b_b"], b["b_b"])))
     c2 = np.concatenate([oc.upsample(bb, s2), s2v])
-    a4 = relu(oc.conv3d(c2, W["d2a"], b["d2a"]))
-    u2 = relu(oc.conv3d(a4, W["d2b"], b["d2b"]))
+    a4 = bf(relu(oc.conv3d(c2, W["d2a"], b["d2a"])))
+    u2 = bf(relu(oc.conv3d(a4, W["d2b"], b["d2b"])))
     c1 = np.concatenate([oc.upsample(u2, s1), s1v])
-    a5 = relu(oc.conv3d(c1, W["d1a"], b["d1a"]))
-    u1 = relu(oc.conv3d(a5, W["d1b"], b["d1b"]))
+    a5 = bf(relu(oc.conv3d(c1, W["d1a"], b["d1a"])))
+    u1 = bf(relu(oc.conv3d(a5, W["d1b"], b["d1b"])))
     y = oc.conv3d(u1, W["out"], b["out"])
     rows = int(np.prod(shape))
     g = np.zeros_like(y)
-    g[0] = 2.0 * (y[0] - target_corr) / rows
+    g[0] = bf(2.0 * (y[0] - target_corr) / rows)
     gW = {}
 
     def back(name, Xin, Yout, dY, use_relu=True):
@@ -147,29 +152,46 @@ def _oracle_unet(net, X, shape, target_corr):
             dY = dY * (Yout > 0)
         dXn, dWn, _ = oc.conv3d_backward(Xin, W[name], dY)
         gW[name] = dWn
-        return dXn
+        return bf(dXn)
 
     d = back("out", u1, y, g, False)
     d = back("d1b", a5, u1, d)
     d = back("d1a", c1, a5, d)
-    d_u2 = oc.upsample_backward(d[:32], s2)
+    d_u2 = bf(oc.upsample_backward(d[:32], s2))
     d_s1 = d[32:]
     d = back("d2b", a4, u2, d_u2)
     d = back("d2a", c2, a4, d)
-    d_b = oc.upsample_backward(d[:64], tuple((n + 1) // 2 for n in s2))
+    d_b = bf(oc.upsample_backward(d[:64], tuple((n + 1) // 2 for n in s2)))
     d_s2 = d[64:]
     d = back("b_b", a3, bb, d_b)
     d = back("b_a", p2, a3, d)
-    d_s2 = d_s2 + oc.pool_backward(d, s2)
+    d_s2 = bf(d_s2 + oc.pool_backward(d, s2))
     d = back("e2b", a2, s2v, d_s2)
     d = back("e2a", p1, a2, d)
-    d_s1 = d_s1 + oc.pool_backward(d, s1)
+    d_s1 = bf(d_s1 + oc.pool_backward(d, s1))
     d = back("e1b", a1, s1v, d_s1)
     back("e1a", X, a1, d)
     return y, gW
 
 
-def test_network_gradients_against_oracle(ws):
+# Where the network's layers meet. The GPU path stores activations and data
+# gradients in BF16 between layers, so through the whole network its values
+# drift from any FP64 composition by BF16 rounding (8-bit mantissa) that
+# compounds from layer to layer: an element-wise comparison of the whole
+# network is bounded by that budget only. Each layer is therefore checked
+# element-wise on the tensors the GPU actually passed it: its forward output
+# within one BF16 unit of the oracle layer on the GPU's input (plus the FP32
+# accumulation's share; 1e-5 for the FP32 output layer), and its weight
+# gradient within 1e-5 of the oracle's on the GPU's input and output gradient
+# (FP32 sums of exact BF16 products). The whole network's gradients are
+# compared with the FP64 oracle composition by direction and size, which a
+# missing or transposed path fails.
+FORWARD_PAIRS = [("e1a", "X", "a1"), ("e1b", "a1", "s1"), ("e2a", "p1", "a2"), ("e2b", "a2", "s2"),
+                 ("b_a", "p2", "a3"), ("b_b", "a3", "b"), ("d2a", "c2", "a4"), ("d2b", "a4", "u2"),
+                 ("d1a", "c1", "a5"), ("d1b", "a5", "u1"), ("out", "u1", "y")]
+
+
+def test_network_layers_and_gradients_against_oracle(ws):
     net = ws.UNet(seed=3)
     shape = (6, 8, 10)
     rng = np.random.default_rng(7)
@@ -178,57 +200,80 @@ def test_network_gradients_against_oracle(ws):
     corr = rng.standard_normal(shape) * 0.3
     Xd = to_dev_bf16(cl(X))[None]
     Yf = net.forward(Xd, shape)
+    c, _ = net.cache
     J0 = torch.ones((1,) + shape, dtype=torch.float64, device="cuda")
     target = torch.from_numpy(np.exp(corr)[None]).to("cuda")
     sse, dY = net.loss_grad(Yf, target, J0)
     gW, gb = net.backward(dY)
+    to64 = lambda t: t[0].float().cpu().numpy().astype(np.float64)
+    for name, src, dst in FORWARD_PAIRS:
+        W = w_oracle(net.Wt[name].float().cpu().numpy().astype(np.float64))
+        b = net.b32[name].cpu().numpy().astype(np.float64)
+        sh = net.wgrad_inputs[name][2]
+        xin = cf(to64(c[src]), sh)
+        ref = oc.conv3d(xin, W, b)
+        got = cf(to64(c[dst]), sh)
+        if name == "out":
+            assert relmax(got, ref) < 1e-5, name
+        else:
+            # one BF16 unit (2^-7 of the value at the bottom of its binade),
+            # plus the FP32 accumulation's error, at most a few 1e-7 of the
+            # sum of the absolute products (which also bounds a value that
+            # the two sums put on different sides of the ReLU's zero)
+            absum = oc.conv3d(np.abs(xin), np.abs(W), np.abs(b))
+            ref = np.maximum(ref, 0.0)
+            assert np.all(np.abs(got - ref) <= 2.0 ** -7 * np.abs(ref) + 1e-5 * absum), name
+        Xl, dYl, _ = net.wgrad_inputs[name]
+        _, dWo, _ = oc.conv3d_backward(cf(to64(Xl), sh), W, cf(to64(dYl), sh))
+        g = w_oracle(gW[name].cpu().numpy().astype(np.float64))
+        assert relmax(g, dWo) < 1e-5, (name, relmax(g, dWo))
+    # the whole network against the FP64 composition: direction and size
     y_o, gW_o = _oracle_unet(net, X, shape, corr)
     assert relmax(cf(Yf[0].cpu().numpy(), shape)[0], y_o[0]) < 3e-2
-    for name in ("out", "d1b", "d2a", "b_b", "e2a", "e1a"):
+    for name, *_ in ws.LAYERS:
         g = w_oracle(gW[name].cpu().numpy().astype(np.float64)).reshape(-1)
         ref = gW_o[name].reshape(-1)
-        # BF16 activations and gradients (8-bit mantissa) pass through about 20
-        # rounded layers; weight gradients are sums with cancellation, so the
-        # check is on direction and size rather than elementwise: a missing or
-        # transposed path gives a wrong direction
         cos = float(g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref)))
         ratio = float(np.linalg.norm(g) / np.linalg.norm(ref))
         assert cos > 0.98 and abs(ratio - 1.0) < 0.15, (name, cos, ratio)
 
 
 def test_training_reduces_the_starting_error(ws):
-    """Train on a few solved 16^3 boxes, then on a held-out box the network's
-    prediction is closer to the converged J than J = B is, and the certified
-    solve from it needs fewer formal solutions."""
+    """Train on solved 16^3 boxes; on three held-out boxes the network's
+    prediction is closer to the converged J than J = B is, and the plain ALI
+    (Eq. alo) started from it reaches the same certified J in at least 5 %
+    fewer iterations in total."""
     from paper_2102_01734_gb300 import inputs, rt3d
     n, nth, nph = 16, 4, 8
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
     data = []
     g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI)
-    for seed in range(100, 106):
+    for seed in range(100, 113):
         chi, eps, B, bc = inputs.cartesian_config(n, 1e-4, seed=seed)
         J = d(B).clone()
         g.solve(d(chi), d(eps), d(B), {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}, J,
                 tol=1e-9, max_iter=3000)
         data.append((d(chi)[None], d(eps)[None], d(B)[None], J[None].clone(), bc))
+    train, held = data[:10], data[10:]
     net = ws.UNet(seed=0)
-    shape = (n, n, n)
-    for step in range(300):
-        chi, eps, B, J, _ = data[step % (len(data) - 1)]
-        X = net.features(chi, eps, B, B)
-        Yf = net.forward(X, shape)
-        sse, dY = net.loss_grad(Yf, J, B)
-        net.backward(dY)
-        net.adam(lr=2e-3)
-    chi, eps, B, J, bc = data[-1]
-    pred = net.predict(chi, eps, B, B)
-    err_net = float(torch.max(torch.abs(torch.log(pred / J))))
-    err_b = float(torch.max(torch.abs(torch.log(B / J))))
-    assert err_net < 0.5 * err_b, (err_net, err_b)
-    bcd = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}
-    J1 = B[0].clone()
-    st_b = g.solve(chi[0], eps[0], B[0], bcd, J1, tol=1e-9, max_iter=3000)
-    J2 = pred[0].clone()
-    st_n = g.solve(chi[0], eps[0], B[0], bcd, J2, tol=1e-9, max_iter=3000)
-    assert torch.max(torch.abs(J2 / J1 - 1)) < 1e-8
-    assert st_n["fs_fp32"] <= st_b["fs_fp32"]
+    ws.train(net, train, 500, lr=2e-3, lr_final=2e-4)
+    # the plain ALI reduces the error by a fixed factor per iteration, so a
+    # start closer to the solution needs fewer iterations
+    ga = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI, accel=rt3d.ACCEL_NONE)
+    it_b = it_n = 0
+    for chi, eps, B, J, bc in held:
+        pred = net.predict(chi, eps, B, B)
+        err_net = float(torch.max(torch.abs(torch.log(pred / J))))
+        err_b = float(torch.max(torch.abs(torch.log(B / J))))
+        assert err_net < 0.5 * err_b, (err_net, err_b)
+        bcd = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}
+        J1 = B[0].clone()
+        st_b = ga.solve(chi[0], eps[0], B[0], bcd, J1, tol=1e-9, max_iter=20000)
+        J2 = pred[0].clone()
+        st_n = ga.solve(chi[0], eps[0], B[0], bcd, J2, tol=1e-9, max_iter=20000)
+        assert torch.max(torch.abs(J2 / J1 - 1)) < 1e-8
+        it_b += st_b["iterations"]
+        it_n += st_n["iterations"]
+        print("warm start: ALI iterations from J = B", st_b["iterations"], "from the network",
+              st_n["iterations"], "start error", err_b, err_net)
+    assert it_n <= 0.95 * it_b, (it_n, it_b)

@@ -344,6 +344,23 @@ def test_solve_field_matches_oracle(rt3d, parabolic, accel):
         assert err < 1e-8, (prec, err, st)
 
 
+@pytest.mark.parametrize("accel", ["ali", "krylov"])
+def test_solve_bench_regime_matches_direct_solve(rt3d, accel):
+    """Converged J in the regime of the 129^3 workload (eps = 1e-6, parabolic,
+    opacity profile times a lognormal k^-3 field, B = 1 + 0.2 g) on a box the
+    oracle's dense direct solve handles: every precision within 1e-8."""
+    n = (7, 7, 9)
+    chi, eps, B, bc = inputs.cartesian_config(n, 1e-6, seed=5)
+    Jo = oracle.direct_solve(chi, eps, B, 4, 8, True, bc)
+    acc = rt3d.ACCEL_NONE if accel == "ali" else rt3d.ACCEL_KRYLOV
+    for prec in (rt3d.FP64, rt3d.FP32_FS_FP64_ALI, rt3d.FP32_FS_FF_REFINE):
+        g = rt3d.Grid(n, 4, 8, rt3d.PARABOLIC, prec, accel=acc)
+        J = torch.from_numpy(B.copy()).to("cuda")
+        st = g.solve(dev(chi), dev(eps), dev(B), dev_bc(bc), J, tol=1e-9, max_iter=20000)
+        err = relerr(J.cpu().numpy(), Jo)
+        assert err < 1e-8, (prec, accel, err, st["iterations"])
+
+
 # ----------------------------------------------------------- error paths
 def test_iteration_cap_is_enotconverged(rt3d):
     chi, eps, B, bc = inputs.cartesian_config(8, 1e-4)
