@@ -48,14 +48,15 @@ def _load():
         lib.orc_parab_weight.restype = c_double
         lib.orc_ray_fs.argtypes = [c_int, _dp, _dp, c_double, c_int, _dp, _dp, _dp, _dp, _dp]
         lib.orc_fs_cart.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp,
-                                    c_double, _dp, c_double, _dp, _dp, _dp, c_int]
+                                    c_double, _dp, c_double, _dp, _dp, _dp, _dp, c_int]
         lib.orc_fs_cart.restype = c_int
         lib.orc_fs_cart_angles.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp,
-                                           c_double, _dp, c_double, _dp, _dp, c_int, _ip, c_int]
+                                           c_double, _dp, c_double, _dp, _dp, _dp, c_int, _ip,
+                                           c_int]
         lib.orc_fs_cart_angles.restype = c_int
         lib.orc_fs_cart_voxel.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp,
-                                          c_double, _dp, c_double, _dp, c_long, c_int, c_int,
-                                          _dp, _dp]
+                                          c_double, _dp, c_double, _dp, _dp, c_long, c_int,
+                                          c_int, _dp, _dp]
         lib.orc_fs_cart_voxel.restype = c_int
         lib.orc_os_jacobi.argtypes = [c_int, c_int, c_int, _dp, _dp, _dp, _dp, c_int, c_double]
         lib.orc_os_jacobi.restype = c_int
@@ -65,8 +66,9 @@ def _load():
         lib.orc_os_bicgstab.argtypes = [c_int, c_int, c_int, _dp, _dp, _dp, _dp, c_int, c_double]
         lib.orc_os_bicgstab.restype = c_int
         lib.orc_ali_solve.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, _dp, _dp, _dp,
-                                      c_double, _dp, c_double, _dp, _dp, c_double, c_int, c_int,
-                                      c_double, c_int, _dp, _dp]
+                                      c_double, _dp, c_double, _dp, _dp, _dp, c_double, c_int,
+                                      c_int, c_double, c_int, _dp, _dp]
+        lib.orc_diffusion_bc.argtypes = [c_int, c_int, c_int, _dp, _dp, _dp, _dp]
         lib.orc_ali_solve.restype = c_int
         lib.orc_sph_trace_voxel.argtypes = [c_int, c_int, c_int, c_double, c_double, _dp, c_int,
                                             c_int, _ip, _dp, _ip, _dp]
@@ -154,14 +156,31 @@ def ray_fs(chil, S, I0: float, parabolic: bool):
 
 
 def _bc_args(shape, bc):
+    """(I_top, top face, I_bottom, bottom face, bottom gradient face): the
+    optional "I_bottom_grad" (ny, nx) gives upward characteristics
+    I = I_bottom + mu I_bottom_grad (the diffusion inner boundary)."""
     nz, ny, nx = shape
     bc = bc or {}
     top = bc.get("I_top", 0.0)
     bot = bc.get("I_bottom", 0.0)
+    grad = bc.get("I_bottom_grad")
     top_face = None if np.isscalar(top) else _f64(np.broadcast_to(top, (ny, nx)))
     bot_face = None if np.isscalar(bot) else _f64(np.broadcast_to(bot, (ny, nx)))
+    grad_face = None if grad is None else _f64(np.broadcast_to(grad, (ny, nx)))
     return (float(top) if top_face is None else 0.0, top_face,
-            float(bot) if bot_face is None else 0.0, bot_face)
+            float(bot) if bot_face is None else 0.0, bot_face, grad_face)
+
+
+def diffusion_bc(chi, B):
+    """Bottom-face (I_bottom, I_bottom_grad) of the LTE diffusion inner
+    boundary: dB/dtau between the two innermost layers and B carried linearly
+    to the bottom face, each (ny, nx)."""
+    lib = _load()
+    chi, B = _f64(chi), _f64(B)
+    nz, ny, nx = chi.shape
+    I_face, grad = np.zeros((ny, nx)), np.zeros((ny, nx))
+    lib.orc_diffusion_bc(nx, ny, nz, _ptr(chi), _ptr(B), _ptr(I_face), _ptr(grad))
+    return I_face, grad
 
 
 def fs_cart(chi, S, ntheta: int, nphi: int, parabolic: bool = False, bc=None,
@@ -172,9 +191,9 @@ def fs_cart(chi, S, ntheta: int, nphi: int, parabolic: bool = False, bc=None,
     nz, ny, nx = chi.shape
     J = np.zeros(chi.shape)
     L = np.zeros((chi.size, 27)) if lstar else None
-    t, tf, b, bf = _bc_args(chi.shape, bc)
+    t, tf, b, bf, bg = _bc_args(chi.shape, bc)
     err = lib.orc_fs_cart(nx, ny, nz, ntheta, nphi, int(parabolic), _ptr(chi), _ptr(S),
-                          t, _ptr(tf), b, _ptr(bf), _ptr(J), _ptr(L),
+                          t, _ptr(tf), b, _ptr(bf), _ptr(bg), _ptr(J), _ptr(L),
                           nthreads or default_threads())
     if err:
         raise RuntimeError(f"oracle formal solution failed ({err})")
@@ -189,9 +208,9 @@ def fs_cart_angles(chi, S, ntheta: int, nphi: int, angles, parabolic: bool = Fal
     nz, ny, nx = chi.shape
     J = np.zeros(chi.shape)
     ang = np.ascontiguousarray(angles, dtype=np.int32)
-    t, tf, b, bf = _bc_args(chi.shape, bc)
+    t, tf, b, bf, bg = _bc_args(chi.shape, bc)
     err = lib.orc_fs_cart_angles(nx, ny, nz, ntheta, nphi, int(parabolic), _ptr(chi), _ptr(S),
-                                 t, _ptr(tf), b, _ptr(bf), _ptr(J),
+                                 t, _ptr(tf), b, _ptr(bf), _ptr(bg), _ptr(J),
                                  nthreads or default_threads(), ang.ctypes.data_as(_ip),
                                  int(ang.size))
     if err:
@@ -208,9 +227,9 @@ def fs_cart_voxel(chi, S, ntheta: int, nphi: int, v: int, parabolic: bool = Fals
     Jv = ctypes.c_double()
     row = np.zeros(27) if lstar else None
     lo, hi = angles if angles is not None else (0, ntheta * nphi)
-    t, tf, b, bf = _bc_args(chi.shape, bc)
+    t, tf, b, bf, bg = _bc_args(chi.shape, bc)
     err = lib.orc_fs_cart_voxel(nx, ny, nz, ntheta, nphi, int(parabolic), _ptr(chi), _ptr(S),
-                                t, _ptr(tf), b, _ptr(bf), int(v), int(lo), int(hi),
+                                t, _ptr(tf), b, _ptr(bf), _ptr(bg), int(v), int(lo), int(hi),
                                 ctypes.byref(Jv), _ptr(row))
     if err:
         raise RuntimeError(f"oracle voxel formal solution failed ({err})")
@@ -264,9 +283,9 @@ def ali_solve(chi, eps, B, ntheta: int, nphi: int, parabolic: bool = False, bc=N
     J = _f64(np.zeros(chi.shape) if J0 is None else J0).copy()
     L = np.zeros((chi.size, 27))
     hist = np.zeros(max_iter)
-    t, tf, b, bf = _bc_args(chi.shape, bc)
+    t, tf, b, bf, bg = _bc_args(chi.shape, bc)
     it = lib.orc_ali_solve(nx, ny, nz, ntheta, nphi, int(parabolic), _ptr(chi), _ptr(eps),
-                           _ptr(B), t, _ptr(tf), b, _ptr(bf), _ptr(J), tol, max_iter,
+                           _ptr(B), t, _ptr(tf), b, _ptr(bf), _ptr(bg), _ptr(J), tol, max_iter,
                            max_sweeps, sweep_tol, nthreads or default_threads(), _ptr(L),
                            _ptr(hist))
     if it <= -1000000:

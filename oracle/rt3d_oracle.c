@@ -287,13 +287,48 @@ static int orc_nb_code(int nx, int ny, int a, int b)
     return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
 }
 
-/* Boundary intensity of ray (x0,y0): top face for mu < 0, bottom face for
- * mu > 0; a face array (indexed x + nx y) overrides the scalar. */
+/* Boundary intensity of ray (x0,y0) with direction cosine mu: top face for
+ * mu < 0, bottom face for mu > 0; a face array (indexed x + nx y) overrides
+ * the scalar. A bottom gradient array (nullable) gives the inner boundary the
+ * LTE diffusion form of the test cases (Sec. 3.1, 3.2): I = I_bot + mu dB/dtau,
+ * the first-order diffusion-limit intensity, with tau the vertical optical
+ * depth increasing inward. */
 static double orc_bc(int nx, double mu, int x0, int y0, double I_top, const double *I_top_face,
-                     double I_bot, const double *I_bot_face)
+                     double I_bot, const double *I_bot_face, const double *I_bot_grad)
 {
-    if (mu < 0.0) return I_top_face ? I_top_face[x0 + nx * y0] : I_top;
-    return I_bot_face ? I_bot_face[x0 + nx * y0] : I_bot;
+    const int f = x0 + nx * y0;
+    if (mu < 0.0) return I_top_face ? I_top_face[f] : I_top;
+    double I = I_bot_face ? I_bot_face[f] : I_bot;
+    if (I_bot_grad) I += mu * I_bot_grad[f];
+    return I;
+}
+
+/* ---------------------------------------------------------------------------
+ * Face arrays of the LTE diffusion inner boundary (Sec. 3.1, 3.2 test cases)
+ * for the bottom face z = 0, per column (x, y):
+ *   grad   = dB/dtau = (B(x,y,0) - B(x,y,1)) / dtau,
+ *   dtau   = 1/2 (chi(x,y,0) + chi(x,y,1)),
+ * the one-sided difference over the innermost centre spacing (unit length,
+ * trapezoidal optical depth; tau increases inward), and
+ *   I_face = B(x,y,0) + 1/2 chi(x,y,0) grad,
+ * B carried linearly from the innermost centre to the face half a voxel
+ * below it, where the characteristics enter. A single layer (nz = 1) has no
+ * gradient: grad = 0, I_face = B(x,y,0). Faces are indexed x + nx y.
+ * ------------------------------------------------------------------------- */
+void orc_diffusion_bc(int nx, int ny, int nz, const double *chi, const double *B,
+                      double *I_face, double *grad)
+{
+    const long nf = (long)nx * ny;
+    for (long f = 0; f < nf; f++) {
+        if (nz < 2) {
+            grad[f] = 0.0;
+            I_face[f] = B[f];
+            continue;
+        }
+        double dtau = 0.5 * (chi[f] + chi[nf + f]);
+        grad[f] = (B[f] - B[nf + f]) / dtau;
+        I_face[f] = B[f] + (0.5 * chi[f]) * grad[f];
+    }
 }
 
 /* ---------------------------------------------------------------------------
@@ -310,7 +345,8 @@ static double orc_bc(int nx, double mu, int x0, int y0, double I_top, const doub
 static int orc_fs_cart_core(int nx, int ny, int nz, int nth, int nph, int parabolic,
                             const double *chi, const double *S,
                             double I_top, const double *I_top_face, double I_bot,
-                            const double *I_bot_face, double *J, double *lstar, int nthreads,
+                            const double *I_bot_face, const double *I_bot_grad, double *J,
+                            double *lstar, int nthreads,
                             const int *angles, int nang)
 {
     const long N = (long)nx * ny * nz;
@@ -366,7 +402,8 @@ static int orc_fs_cart_core(int nx, int ny, int nz, int nth, int nph, int parabo
                         chil[k] = chi[vox[k]] * len[k];
                         Sp[k] = S[vox[k]];
                     }
-                    double I0 = orc_bc(nx, d[2], x0, y0, I_top, I_top_face, I_bot, I_bot_face);
+                    double I0 = orc_bc(nx, d[2], x0, y0, I_top, I_top_face, I_bot, I_bot_face,
+                                       I_bot_grad);
                     orc_ray_fs(K, chil, Sp, I0, parabolic, I, E, al, be, ga);
                     for (int k = 0; k < K; k++) {
                         num[vox[k]] += len[k] * I[k];
@@ -420,10 +457,11 @@ static int orc_fs_cart_core(int nx, int ny, int nz, int nth, int nph, int parabo
 int orc_fs_cart(int nx, int ny, int nz, int nth, int nph, int parabolic,
                 const double *chi, const double *S,
                 double I_top, const double *I_top_face, double I_bot, const double *I_bot_face,
+                const double *I_bot_grad,
                 double *J, double *lstar, int nthreads)
 {
     return orc_fs_cart_core(nx, ny, nz, nth, nph, parabolic, chi, S, I_top, I_top_face, I_bot,
-                            I_bot_face, J, lstar, nthreads, NULL, 0);
+                            I_bot_face, I_bot_grad, J, lstar, nthreads, NULL, 0);
 }
 
 /* The same sums restricted to the listed solid angles (a bounded sample of a
@@ -431,11 +469,11 @@ int orc_fs_cart(int nx, int ny, int nz, int nth, int nph, int parabolic,
 int orc_fs_cart_angles(int nx, int ny, int nz, int nth, int nph, int parabolic,
                        const double *chi, const double *S,
                        double I_top, const double *I_top_face, double I_bot,
-                       const double *I_bot_face, double *J, int nthreads,
+                       const double *I_bot_face, const double *I_bot_grad, double *J, int nthreads,
                        const int *angles, int nang)
 {
     return orc_fs_cart_core(nx, ny, nz, nth, nph, parabolic, chi, S, I_top, I_top_face, I_bot,
-                            I_bot_face, J, NULL, nthreads, angles, nang);
+                            I_bot_face, I_bot_grad, J, NULL, nthreads, angles, nang);
 }
 
 /* ---------------------------------------------------------------------------
@@ -450,6 +488,7 @@ int orc_fs_cart_angles(int nx, int ny, int nz, int nth, int nph, int parabolic,
 int orc_fs_cart_voxel(int nx, int ny, int nz, int nth, int nph, int parabolic,
                       const double *chi, const double *S,
                       double I_top, const double *I_top_face, double I_bot, const double *I_bot_face,
+                      const double *I_bot_grad,
                       long v, int o_lo, int o_hi, double *J_v, double *lstar_row)
 {
     const int nO = nth * nph;
@@ -489,7 +528,7 @@ int orc_fs_cart_voxel(int nx, int ny, int nz, int nth, int nph, int parabolic,
                 chil[k] = chi[vox[k]] * len[k];
                 Sp[k] = S[vox[k]];
             }
-            double I0 = orc_bc(nx, d[2], x0, y0, I_top, I_top_face, I_bot, I_bot_face);
+            double I0 = orc_bc(nx, d[2], x0, y0, I_top, I_top_face, I_bot, I_bot_face, I_bot_grad);
             orc_ray_fs(K, chil, Sp, I0, parabolic, I, E, al, be, ga);
             for (int k = 0; k < K; k++) {
                 if (vox[k] != v) continue;
@@ -719,6 +758,7 @@ done:
 int orc_ali_solve(int nx, int ny, int nz, int nth, int nph, int parabolic,
                   const double *chi, const double *eps, const double *B,
                   double I_top, const double *I_top_face, double I_bot, const double *I_bot_face,
+                  const double *I_bot_grad,
                   double *J, double tol, int max_iter, int max_sweeps, double sweep_tol,
                   int nthreads, double *lstar_out, double *history)
 {
@@ -730,7 +770,7 @@ int orc_ali_solve(int nx, int ny, int nz, int nth, int nph, int parabolic,
     for (it = 0; it < max_iter; it++) {
         for (long v = 0; v < N; v++) S[v] = (1.0 - eps[v]) * J[v] + eps[v] * B[v];
         err = orc_fs_cart(nx, ny, nz, nth, nph, parabolic, chi, S, I_top, I_top_face, I_bot,
-                          I_bot_face, Jfs, it == 0 ? L : NULL, nthreads);
+                          I_bot_face, I_bot_grad, Jfs, it == 0 ? L : NULL, nthreads);
         if (err) break;
         for (long v = 0; v < N; v++) r[v] = Jfs[v] - J[v];
         orc_os_jacobi(nx, ny, nz, L, eps, r, dJ, max_sweeps, sweep_tol);

@@ -18,6 +18,16 @@ dataset is involved):
   B = 1 + 0.2 g, uniform eps; boundary: no incoming intensity at the top,
   I = B of the entered bottom voxel at the bottom.
 
+* ``grey_config(...)``: the paper's PBC test atmosphere with its grey
+  temperature structure (Sec. 3.1, items 3 and 4): chi as in
+  ``cartesian_config``, the vertical optical depth of each column at the
+  voxel centres tau(nz-1) = chi(nz-1)/2, tau(z) = tau(z+1) + (chi(z) +
+  chi(z+1))/2 (unit spacing, tau growing inward), and B = 3/4 (tau + 2/3),
+  the grey (Eddington) structure T^4 = 3/4 Teff^4 (tau + 2/3) in units of
+  sigma Teff^4 / pi; boundary: no incoming intensity at the top, and the
+  LTE diffusion condition at the bottom (its face arrays are derived from
+  chi and B by the library, not here).
+
 * ``spherical_config(...)``: the paper's second test geometry (a spherical
   shell, Sec. 3.2) on a (r, theta, phi) grid with log-spaced radial edges from
   r_in to r_out: chi = C r^-12 at the cell's geometric-mean radius with C set
@@ -79,6 +89,30 @@ def cartesian_config(n, eps: float, seed: int | None = None, sigma_ln: float = 0
     epsa = np.full(shape, float(eps))
     bc = {"I_top": 0.0, "I_bottom": B[0].copy()}
     return chi, epsa, B, bc
+
+
+def grey_tau(chi: np.ndarray) -> np.ndarray:
+    """Vertical optical depth at the voxel centres of each column of chi
+    (nz, ny, nx): half a voxel below the top face, then trapezoidal steps."""
+    tau = np.empty_like(chi)
+    tau[-1] = 0.5 * chi[-1]
+    for z in range(chi.shape[0] - 2, -1, -1):
+        tau[z] = tau[z + 1] + 0.5 * (chi[z] + chi[z + 1])
+    return tau
+
+
+def grey_config(n, eps: float, seed: int | None = None, sigma_ln: float = 0.5):
+    """(chi, eps, B, bc) of the grey atmosphere: B = 3/4 (tau + 2/3); bc holds
+    only I_top = 0 (the diffusion faces come from the library)."""
+    if np.isscalar(n):
+        n = (int(n),) * 3
+    nx, ny, nz = n
+    shape = (nz, ny, nx)
+    chi = np.broadcast_to(vertical_chi(nz)[:, None, None], shape).copy()
+    if seed is not None:
+        chi = chi * np.exp(sigma_ln * powerlaw_field(shape, seed))
+    B = 0.75 * (grey_tau(chi) + 2.0 / 3.0)
+    return chi, np.full(shape, float(eps)), B, {"I_top": 0.0}
 
 
 # Named workloads (sizes of the benchmark configurations).

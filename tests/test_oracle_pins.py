@@ -550,3 +550,81 @@ def test_P7_sqrt_eps_surface_law():
     assert errs[(1e-2, 33)] < 0.05 and errs[(1e-2, 65)] < 0.02
     assert errs[(1e-4, 65)] < errs[(1e-4, 33)]
     assert errs[(1e-4, 65)] < 0.2
+
+
+# ------------------------------------------- LTE diffusion inner boundary
+def test_diffusion_entry_in_vacuum_closed_form():
+    """chi = 0: every point keeps its characteristic's entry intensity. With
+    I_top = 0 and uniform faces I_bottom = a, gradient g, the upward half of
+    the midpoint directions (weight 1/2, sum of w mu = 1/4 exactly) gives
+    J = a/2 + g/4 everywhere."""
+    shape = (3, 5, 4)
+    S = np.random.default_rng(2).uniform(0.5, 2.0, shape)
+    a, g = 1.7, 0.9
+    for parabolic in (False, True):
+        J = oracle.fs_cart(np.zeros(shape), S, 8, 6, parabolic,
+                           bc={"I_top": 0.0, "I_bottom": a, "I_bottom_grad": np.full((5, 4), g)})
+        assert np.max(np.abs(J - (a / 2 + g / 4))) <= 1e-14
+
+
+def test_diffusion_entry_per_column_by_brute_force():
+    """chi = 0 with face arrays that differ per column: J_v is the chord
+    weighted average over the characteristics crossing v of their entry
+    values I_bottom(x0, y0) + mu g(x0, y0), rebuilt here from the traced
+    characteristics (catches a transposed face index or a wrong mu)."""
+    nz, ny, nx = 2, 3, 4
+    rng = np.random.default_rng(5)
+    face, grad = rng.uniform(0.5, 1.5, (ny, nx)), rng.uniform(-1.0, 1.0, (ny, nx))
+    top = rng.uniform(0.0, 0.3, (ny, nx))
+    nth, nph = 4, 4
+    mu, phi, d, w = oracle.directions(nth, nph)
+    Jref = np.zeros(nz * ny * nx)
+    for o in range(nth * nph):
+        num, den = np.zeros_like(Jref), np.zeros_like(Jref)
+        for y0 in range(ny):
+            for x0 in range(nx):
+                vox, ln = oracle.trace_cart((nz, ny, nx), d[o], x0, y0)
+                I0 = face[y0, x0] + mu[o] * grad[y0, x0] if mu[o] > 0 else top[y0, x0]
+                np.add.at(num, vox, ln * I0)
+                np.add.at(den, vox, ln)
+        Jref += w[o] * num / den
+    J = oracle.fs_cart(np.zeros((nz, ny, nx)), np.ones((nz, ny, nx)), nth, nph, False,
+                       bc={"I_top": top, "I_bottom": face, "I_bottom_grad": grad})
+    assert np.max(np.abs(J.reshape(-1) - Jref)) <= 1e-14
+
+
+def test_diffusion_faces_of_a_linear_source():
+    """B = a + b tau per column with tau the trapezoidal vertical optical depth
+    of a random chi: the gradient is b, and the face value is B at the bottom
+    face, whose optical depth from the top is the column's total sum of chi
+    (unit voxels); nz = 1 gives no gradient."""
+    rng = np.random.default_rng(8)
+    chi = 10 ** rng.uniform(-1, 1, (6, 3, 5))
+    a, b = rng.uniform(0.5, 2, (3, 5)), rng.uniform(0.1, 3, (3, 5))
+    B = a + b * inputs.grey_tau(chi)
+    I_face, grad = oracle.diffusion_bc(chi, B)
+    assert np.max(np.abs(grad - b) / b) < 1e-12
+    Bface = a + b * chi.sum(axis=0)
+    assert np.max(np.abs(I_face - Bface) / Bface) < 1e-13
+    I1, g1 = oracle.diffusion_bc(chi[:1], B[:1])
+    assert np.all(g1 == 0.0) and np.array_equal(I1, B[0])
+
+
+def test_diffusion_boundary_gives_j_equal_b_in_a_grey_lte_slab():
+    """Grey LTE slab (S = B = 3/4 (tau + 2/3), 0.2 optical depth per voxel,
+    bottom tau about 5): the diffusion intensity B + mu dB/dtau is the exact
+    solution for a source linear in tau, so J = B near the inner boundary up
+    to the discretisation, while the plain rule I = B leaves J short by about
+    g/4 (the upward half carries no mu g)."""
+    nz, ny, nx = 24, 4, 4
+    chi = np.full((nz, ny, nx), 0.2)
+    B = 0.75 * (inputs.grey_tau(chi) + 2.0 / 3.0)
+    I_face, g = oracle.diffusion_bc(chi, B)
+    assert np.allclose(g, 0.75, rtol=1e-13)
+    for parabolic in (False, True):
+        J_diff = oracle.fs_cart(chi, B, 8, 8, parabolic,
+                                bc={"I_top": 0.0, "I_bottom": I_face, "I_bottom_grad": g})
+        J_plain = oracle.fs_cart(chi, B, 8, 8, parabolic, bc={"I_top": 0.0, "I_bottom": B[0]})
+        d_diff, d_plain = (J_diff[0] - B[0]).mean(), (J_plain[0] - B[0]).mean()
+        assert abs(d_diff) < 0.01, d_diff
+        assert abs(d_plain + 0.75 / 4) < 0.01, d_plain
