@@ -93,7 +93,8 @@ typedef struct {
 } rt3d_grid_desc;
 
 /* Boundary intensities (Sec. 3.1: I = 0 incoming at the outer boundary; the
- * inner boundary is given by the caller, e.g. I = B of the entered voxel).
+ * inner boundary is given by the caller, e.g. I = B of the entered voxel, or
+ * the LTE diffusion condition of the paper's test cases, Sec. 3.1 and 3.2).
  * A characteristic with mu < 0 enters through the top face, one with mu > 0
  * through the bottom face, at the centre of face cell (x0, y0). A non-NULL
  * face array (double[ny][nx], host or device) overrides the scalar. */
@@ -104,6 +105,12 @@ typedef struct {
     const double *I_bottom_face;
     double I_irr;     /* RT3D_SPHERICAL: irradiation entering the outer sphere at
                          points with x > 0 along directions with d_x < 0 */
+    const double *I_bottom_grad; /* nullable double[ny][nx] (Cartesian grids; RT3D_EINVAL
+                         on a spherical one): the diffusion inner boundary, where a
+                         characteristic with direction cosine mu > 0 enters with
+                         I = I_bottom (or its face value) + mu I_bottom_grad, the
+                         gradient being dB/dtau at the boundary with tau the vertical
+                         optical depth growing inward (rt3d_diffusion_bc) */
 } rt3d_bc;
 /* On a spherical grid I_top (or I_top_face, unused) is the intensity entering
  * the outer sphere outside the irradiated part, I_bottom / I_bottom_face
@@ -267,6 +274,24 @@ rt3d_status rt3d_grid_sph_ray(const rt3d_grid *grid, int angle, int index, int *
 rt3d_status rt3d_formal_solution(rt3d_grid *grid, const double *chi, const double *S,
                                  const rt3d_bc *bc, double *J_out, double *lstar_out);
 
+/* Bottom-face arrays of the LTE diffusion inner boundary (Sec. 3.1, 3.2
+ * test cases) for nlambda stacked grids of the Cartesian grid's shape: per
+ * column f = x + nx y and grid l,
+ *   grad[l][f]   = (B[l][0][f] - B[l][1][f]) / (1/2 (chi[l][0][f] + chi[l][1][f])),
+ *   I_face[l][f] = B[l][0][f] + 1/2 chi[l][0][f] grad[l][f],
+ * the one-sided dB/dtau over the unit spacing of the two innermost layer
+ * centres (trapezoidal optical depth) and B carried linearly to the bottom
+ * face, half a voxel below the innermost centre, where the characteristics
+ * enter; nz = 1 gives grad = 0 and I_face = B[l][0][f]. Pass them as
+ * rt3d_bc's I_bottom_face and I_bottom_grad. chi, B: double[nlambda][N];
+ * I_face, grad: double[nlambda][ny][nx], written. All four must be memory of
+ * the grid's device (or managed memory); the kernel runs on the grid's
+ * stream, which the call does not synchronise. RT3D_EINVAL for a NULL
+ * argument, nlambda < 1, a spherical grid or a pointer that is not device
+ * memory. */
+rt3d_status rt3d_diffusion_bc(rt3d_grid *grid, int nlambda, const double *chi, const double *B,
+                              double *I_face, double *grad);
+
 /* The formal solution without Lambda* in float-float arithmetic (not in the
  * paper: FP64-class accuracy, about 1e-13 relative, on the FP32 pipe; GB300's
  * FP64 rate is about 1/64 of its FP32 rate). Same arguments, layouts and
@@ -339,6 +364,8 @@ typedef struct {
                                characteristic per thread) */
     float fs_tune_ms[RT3D_FS_TUNE_SHAPES]; /* its candidates' times (0: not
                                timed: two characteristics per thread) */
+    int recaptures;         /* re-captures of the iteration graph with fewer
+                               wavelengths (retired ones leave the launches) */
 } rt3d_batch_stats;
 
 /* Batched wavelengths (Sec. 4.1: the geometry is the same for all wavelength

@@ -89,6 +89,32 @@ __global__ void source_kernel(int nx, int ny, int nz, const double *J, const dou
     }
 }
 
+// Bottom-face arrays of the LTE diffusion inner boundary (the test cases of
+// Sec. 3.1): per column f and wavelength, dB/dtau = (B(z=0) - B(z=1)) /
+// (1/2 (chi(z=0) + chi(z=1))), the one-sided difference over the unit centre
+// spacing with the trapezoidal optical depth (tau grows inward), and the face
+// intensity B(z=0) + 1/2 chi(z=0) dB/dtau, B carried linearly to the face half
+// a voxel below the innermost centre; a single layer has gradient 0 and face
+// value B(z=0).
+__global__ void diffusion_bc_kernel(long long nf, int nz, int nl, const double *chi,
+                                    const double *B, double *I_face, double *grad) {
+    const long long n = nf * nl, N = nf * nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long l = i / nf, f = i - l * nf;
+        const double *c = chi + l * N, *b = B + l * N;
+        if (nz < 2) {
+            grad[i] = 0.0;
+            I_face[i] = b[f];
+            continue;
+        }
+        const double dtau = __dmul_rn(0.5, __dadd_rn(c[f], c[nf + f]));
+        const double gr = __ddiv_rn(__dsub_rn(b[f], b[nf + f]), dtau);
+        grad[i] = gr;
+        I_face[i] = __dadd_rn(b[f], __dmul_rn(__dmul_rn(0.5, c[f]), gr));
+    }
+}
+
 // neighbour index of (x, y, z) + (dx, dy, dz) with the periodic axes wrapped;
 // -1 outside a non-periodic axis
 __device__ __forceinline__ long long nb_index(int x, int y, int z, int dx, int dy, int dz, int nx,
@@ -494,6 +520,13 @@ cudaError_t launch_source(int nx, int ny, int nz, const double *J, const double 
                           cudaStream_t s) {
     const long long n = (long long)nx * ny * nz;
     source_kernel<<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, J, eps, B, chiS, fp64, homogeneous);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diffusion_bc(int nx, int ny, int nz, int nl, const double *chi,
+                                const double *B, double *I_face, double *grad, cudaStream_t s) {
+    const long long nf = (long long)nx * ny;
+    diffusion_bc_kernel<<<grid_for(nf * nl, 256), 256, 0, s>>>(nf, nz, nl, chi, B, I_face, grad);
     return cudaGetLastError();
 }
 

@@ -115,6 +115,7 @@ struct rt3d_grid {
     double *Jfs = nullptr, *r = nullptr, *dJ[2] = {nullptr, nullptr}, *inv_diag = nullptr;
     double *lstar = nullptr;  // [27][N] FP64 accumulation
     double *top = nullptr, *bot = nullptr, *tmp = nullptr, *delta = nullptr, *r64 = nullptr;
+    double *bgrad_face = nullptr;  // staged diffusion gradient face (Cartesian, [ny*nx])
     double *chi_ref = nullptr, *eps_ref = nullptr;
     double **dJ_dev = nullptr;  // device copy of {dJ[0], dJ[1]}
     float *dJ32[2] = {nullptr, nullptr};  // FP32 copies for the mixed-mode stencil
@@ -173,7 +174,7 @@ struct rt3d_grid {
     double *bchi = nullptr, *beps = nullptr, *bB = nullptr, *bJ = nullptr, *br = nullptr;
     double *bbuf0 = nullptr, *bbuf1 = nullptr, *binv = nullptr, *bJrep = nullptr;
     float *bb32_0 = nullptr, *bb32_1 = nullptr;
-    double *btop = nullptr, *bbot = nullptr;
+    double *btop = nullptr, *bbot = nullptr, *bgrad = nullptr;
     float2 *bchiS = nullptr;
     float *ba = nullptr;
     BatchState bsh{};             // host copy of the device pointers
@@ -253,6 +254,7 @@ rt3d_status fs_params(rt3d_grid *g, const rt3d_bc *bc, bool fp64, bool homogeneo
     q.toff = g->tpl.toff;
     q.tlen = g->tpl.tlen;
     q.up = g->tpl.up;
+    q.mu = g->tpl.mu;
     q.code = g->tpl.code;
     q.len = fp64 ? (const void *)g->tpl.len64 : (const void *)g->tpl.len32;
     q.cw = fp64 ? (const void *)g->tpl.cw64 : (const void *)g->tpl.cw32;
@@ -271,10 +273,15 @@ rt3d_status fs_params(rt3d_grid *g, const rt3d_bc *bc, bool fp64, bool homogeneo
         const double *tf = nullptr, *bf = nullptr;
         const size_t nf = (size_t)g->nx * g->ny;
         const size_t nfb = g->sph ? (size_t)g->ny * g->nz : nf;  // spherical core face
+        if (g->sph && bc->I_bottom_grad)
+            return fail(RT3D_EINVAL, "I_bottom_grad needs a Cartesian grid");
         if (!g->sph) TRY(stage_in(g, bc->I_top_face, nf, g->top, &tf));
         TRY(stage_in(g, bc->I_bottom_face, nfb, g->bot, &bf));
+        const double *gf = nullptr;
+        if (!g->sph) TRY(stage_in(g, bc->I_bottom_grad, nf, g->bgrad_face, &gf));
         q.top_face = tf;
         q.bot_face = bf;
+        q.bot_grad = gf;
     }
     *p = q;
     return RT3D_OK;
@@ -545,6 +552,7 @@ rt3d_status alloc_work(rt3d_grid *g) {
     TRY(g->alloc(&g->lstar, 27 * N));
     TRY(g->alloc(&g->top, nf));
     TRY(g->alloc(&g->bot, nf));
+    if (!g->sph) TRY(g->alloc(&g->bgrad_face, nf));
     TRY(g->alloc(&g->dJ_dev, 2));
     TRY(g->alloc(reinterpret_cast<double2 **>(&g->chiS64), 4 * N));
     TRY(g->alloc(reinterpret_cast<float2 **>(&g->chiS32), 4 * N));
@@ -830,6 +838,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     TRY(g->alloc(&t.toff, nO));
     TRY(g->alloc(&t.order, nO));
     TRY(g->alloc(&t.up, nO));
+    TRY(g->alloc(&t.mu, nO));
     TRY(g->alloc(&t.code, total));
     TRY(g->alloc(&t.len64, total));
     TRY(g->alloc(&t.len32, total));
@@ -855,6 +864,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     CK(cudaMemcpyAsync(d_cap, cap.data(), sizeof(int) * nO, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(t.toff, off.data(), sizeof(long long) * nO, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(t.up, up.data(), nO, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(t.mu, g->mu.data(), sizeof(double) * nO, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
     TraceParams tp{};
     tp.nx = g->nx;
@@ -1268,8 +1278,10 @@ rt3d_status batch_setup(rt3d_grid *g, int nl) {
     TRY(g->alloc(&g->ba, L * os_coef_count((long long)N)));
     TRY(g->alloc(&g->btop, L * nf));
     TRY(g->alloc(&g->bbot, L * nf));
+    TRY(g->alloc(&g->bgrad, L * nf));
     BatchState &b = g->bsh;
     TRY(g->alloc(&b.active, L));
+    TRY(g->alloc(&b.alist, L));
     TRY(g->alloc(&b.state, L));
     TRY(g->alloc(&b.done, L));
     TRY(g->alloc(&b.count, L));
@@ -1537,6 +1549,17 @@ rt3d_status rt3d_formal_solution_ff(rt3d_grid *g, const double *chi, const doubl
     TRY(run_fs_ff(g, fp, dchi, dS, nullptr, nullptr));
     TRY(deliver(g, J_out, g->Jfs, N));
     CK(cudaStreamSynchronize(g->stream));
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_diffusion_bc(rt3d_grid *g, int nl, const double *chi, const double *B,
+                              double *I_face, double *grad) {
+    if (!g || !chi || !B || !I_face || !grad) return fail(RT3D_EINVAL, "NULL argument");
+    if (nl < 1) return fail(RT3D_EINVAL, "nlambda %d < 1", nl);
+    if (g->sph) return fail(RT3D_EINVAL, "the diffusion boundary arrays need a Cartesian grid");
+    if (!is_device_ptr(chi) || !is_device_ptr(B) || !is_device_ptr(I_face) || !is_device_ptr(grad))
+        return fail(RT3D_EINVAL, "chi, B, I_face and grad must be memory of the grid's device");
+    CKL(launch_diffusion_bc(g->nx, g->ny, g->nz, nl, chi, B, I_face, grad, g->stream));
     return RT3D_OK;
 }
 
@@ -1838,8 +1861,10 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     CK(cudaMemcpyAsync(g->bB, B, L * N * sizeof(double), cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(g->bJ, J_inout, L * N * sizeof(double), cudaMemcpyDefault, s));
     const bool tf = bc && bc->I_top_face, bf = bc && bc->I_bottom_face;
+    const bool gf = bc && bc->I_bottom_grad;
     if (tf) CK(cudaMemcpyAsync(g->btop, bc->I_top_face, L * nf * sizeof(double), cudaMemcpyDefault, s));
     if (bf) CK(cudaMemcpyAsync(g->bbot, bc->I_bottom_face, L * nf * sizeof(double), cudaMemcpyDefault, s));
+    if (gf) CK(cudaMemcpyAsync(g->bgrad, bc->I_bottom_grad, L * nf * sizeof(double), cudaMemcpyDefault, s));
 
     // Lambda* of every wavelength (FP32 formal solution with Lambda*, once),
     // folded into its OS coefficients.
@@ -1855,6 +1880,7 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
         p.toff = g->tpl.toff;
         p.tlen = g->tpl.tlen;
         p.up = g->tpl.up;
+        p.mu = g->tpl.mu;
         p.code = g->tpl.code;
         p.len = g->tpl.len32;
         p.cw = g->tpl.cw32;
@@ -1877,6 +1903,9 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     std::vector<int> ones(L, 1);
     BatchState &h = g->bsh;
     CK(cudaMemcpyAsync(h.active, ones.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
+    std::vector<int> iota(L);
+    for (size_t l = 0; l < L; ++l) iota[l] = (int)l;
+    CK(cudaMemcpyAsync(h.alist, iota.data(), L * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(h.state, 0, L * sizeof(int), s));
     CK(cudaMemsetAsync(h.iters, 0, L * sizeof(int), s));
     CK(cudaMemsetAsync(g->bJrep, 0, 4 * L * N * sizeof(double), s));
@@ -1893,11 +1922,13 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     bp.toff = g->tpl.toff;
     bp.tlen = g->tpl.tlen;
     bp.up = g->tpl.up;
+    bp.mu = g->tpl.mu;
     bp.rec32 = g->tpl.rec32;
     bp.chiS = g->bchiS;
     bp.Jrep = g->bJrep;
     bp.top_face = tf ? g->btop : nullptr;
     bp.bot_face = bf ? g->bbot : nullptr;
+    bp.bot_grad = gf ? g->bgrad : nullptr;
     bp.I_top = bc ? bc->I_top : 0.0;
     bp.I_bot = bc ? bc->I_bottom : 0.0;
     bp.bs = g->bsd;
@@ -1943,18 +1974,29 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     const double switch_tol = g->fs64 ? tol : std::max(tol, 1e-6);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    CK(cudaStreamBeginCapture(g->bstream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = launch_batch_iteration(bp, nl, g->bJ, g->beps, g->bB, g->ba, g->binv, g->br,
-                                            g->bbuf0, g->bbuf1, g->bb32_0, g->bb32_1, kBatchSweeps,
-                                            1e-3, switch_tol, iter_cap, g->parab, g->bfs_shape,
-                                            g->bstream);
-    cudaError_t ce = cudaStreamEndCapture(g->bstream, &graph);
-    if (le != cudaSuccess || ce != cudaSuccess) {
+    // one iteration over a wavelength extent of nlaunch (>= the active count)
+    auto capture = [&](int nlaunch) -> rt3d_status {
+        if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
-        return fail(RT3D_ECUDA, "batch graph capture failed: %s",
-                    cudaGetErrorString(le != cudaSuccess ? le : ce));
-    }
-    CK(cudaGraphInstantiate(&exec, graph, 0));
+        exec = nullptr;
+        graph = nullptr;
+        CK(cudaStreamBeginCapture(g->bstream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = launch_batch_iteration(bp, nl, nlaunch, g->bJ, g->beps, g->bB, g->ba,
+                                                g->binv, g->br, g->bbuf0, g->bbuf1, g->bb32_0,
+                                                g->bb32_1, kBatchSweeps, 1e-3, switch_tol,
+                                                iter_cap, g->parab, g->bfs_shape, g->bstream);
+        cudaError_t ce = cudaStreamEndCapture(g->bstream, &graph);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            graph = nullptr;
+            return fail(RT3D_ECUDA, "batch graph capture failed: %s",
+                        cudaGetErrorString(le != cudaSuccess ? le : ce));
+        }
+        CK(cudaGraphInstantiate(&exec, graph, 0));
+        return RT3D_OK;
+    };
+    int nlaunch = nl;
+    TRY(capture(nlaunch));
     const long long per_iter = 7 + kBatchSweeps;
     CK(cudaEventRecord(g->bev0, s));
     CK(cudaStreamWaitEvent(g->bstream, g->bev0, 0));
@@ -1971,6 +2013,13 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
         CK(cudaMemcpyAsync(&nactive, &g->bsd->nactive, sizeof(int), cudaMemcpyDeviceToHost,
                            g->bstream));
         CK(cudaStreamSynchronize(g->bstream));
+        // retired wavelengths leave the launches: a smaller extent once a
+        // quarter of the launched ones has retired
+        if (nactive > 0 && 4 * nactive <= 3 * nlaunch) {
+            nlaunch = nactive;
+            TRY(capture(nlaunch));
+            ++bs.recaptures;
+        }
     }
     CK(cudaEventRecord(t1, g->bstream));
     CK(cudaEventSynchronize(t1));
@@ -2014,6 +2063,7 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
         bl.I_bottom = bc ? bc->I_bottom : 0.0;
         bl.I_top_face = tf ? g->btop + l * nf : nullptr;
         bl.I_bottom_face = bf ? g->bbot + l * nf : nullptr;
+        bl.I_bottom_grad = gf ? g->bgrad + l * nf : nullptr;
         FsParams fp, fp64k, fphomk;
         TRY(fs_params(g, &bl, g->fs64, false, &fp));
         TRY(fs_params(g, &bl, true, false, &fp64k));

@@ -1,9 +1,11 @@
 // Batched wavelengths: n_lambda independent ALI solves (Eq. alo) that share
-// the geometry cache (Sec. 4.1: "the geometry and thus, the set of tracks ...
-// remain the same for all wavelength points"). Every kernel takes the
-// wavelength from blockIdx.y (or .z) and returns at once for a retired one,
-// so one captured sequence of launches (a CUDA graph) serves every
-// iteration whatever the number of wavelengths still active. A wavelength
+// the geometry cache (Sec. 4.1: the tracks are the same for every wavelength).
+// Every kernel takes its wavelength from the compacted list of active ones,
+// alist[blockIdx.y] (or .z), and a block past the active count returns at
+// once, so one captured sequence of launches (a CUDA graph) serves every
+// iteration whatever the number of wavelengths still active; the host
+// re-captures it with a smaller wavelength extent as wavelengths retire, so
+// retired wavelengths cost no blocks at all. A wavelength
 // retires on the device when the estimated error of its J (last change
 // times rho/(1-rho), rho from the last kHist changes) is below tol, or when
 // its changes stagnate (the FP32 floor), which hands it to the FP64
@@ -50,8 +52,8 @@ __device__ __forceinline__ void bmax_atomic(double x, unsigned long long *dst) {
 // every active wavelength (blockIdx.y).
 __global__ void b_source(int nx, int ny, int nz, const double *J, const double *eps,
                          const double *B, float2 *chiS, const BatchState *bs) {
-    const int l = blockIdx.y;
-    if (!bs->active[l]) return;
+    if ((int)blockIdx.y >= bs->nactive) return;
+    const int l = bs->alist[blockIdx.y];
     const long long n = (long long)nx * ny * nz;
     const double *Jl = J + l * n, *el = eps + l * n, *Bl = B + l * n;
     float2 *cl = chiS + 4 * l * n;
@@ -73,8 +75,8 @@ __global__ void b_source(int nx, int ny, int nz, const double *J, const double *
 template <bool PARAB, int CONV, bool BL>
 __global__ void __launch_bounds__(256) b_fs(BatchFsParams p) {
     constexpr bool W0 = CONV == 1, W1 = CONV >= 1;
-    const int l = blockIdx.z;
-    if (!p.bs->active[l]) return;
+    if ((int)blockIdx.z >= p.bs->nactive) return;
+    const int l = p.bs->alist[blockIdx.z];
     const int nray = p.nx * p.ny;
     const int ray = blockIdx.x * blockDim.x + threadIdx.x;
     if (ray >= nray) return;
@@ -84,9 +86,10 @@ __global__ void __launch_bounds__(256) b_fs(BatchFsParams p) {
     const float4 *__restrict__ rec = p.rec32 + p.toff[o];
     const float2 *__restrict__ chiS = p.chiS + l * n4;
     double *__restrict__ J = p.Jrep + l * n4;
-    double I0;
-    if (p.up[o]) I0 = p.bot_face ? p.bot_face[(long long)l * nray + ray] : p.I_bot;
-    else I0 = p.top_face ? p.top_face[(long long)l * nray + ray] : p.I_top;
+    const long long lf = (long long)l * nray;
+    const double I0 = entry_intensity(p.up[o], p.mu, o, ray, p.top_face ? p.top_face + lf : nullptr,
+                                      p.bot_face ? p.bot_face + lf : nullptr,
+                                      p.bot_grad ? p.bot_grad + lf : nullptr, p.I_top, p.I_bot);
     RayF s;
     s.live = true;
     s.base = ray % p.nx + 2 * p.nx * (ray / p.nx);
@@ -125,8 +128,8 @@ __global__ void __launch_bounds__(256) b_fs(BatchFsParams p) {
 __global__ void b_fold_init(int nx, int ny, int nz, double *Jrep, const double *J,
                             const double *inv_diag, double *r, double *dJ0, float *dJ0_32,
                             BatchState *bs) {
-    const int l = blockIdx.y;
-    if (!bs->active[l]) return;
+    if ((int)blockIdx.y >= bs->nactive) return;
+    const int l = bs->alist[blockIdx.y];
     const long long n = (long long)nx * ny * nz;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     if (tid == 0) {
@@ -163,8 +166,9 @@ __global__ void __launch_bounds__(256) b_sweep(int nx, int ny, int nz, const flo
                                                const double *__restrict__ r, double *buf0,
                                                double *buf1, float *b32_0, float *b32_1, int m,
                                                double tol, BatchState *bs) {
-    const int l = blockIdx.y;
-    if (!bs->active[l] || bs->done[l]) return;
+    if ((int)blockIdx.y >= bs->nactive) return;
+    const int l = bs->alist[blockIdx.y];
+    if (bs->done[l]) return;
     unsigned long long *dmx = bs->dmax + l * (kBatchSweeps + 1);
     unsigned long long *jmx = bs->jmax + l * (kBatchSweeps + 1);
     if (m >= 2) {
@@ -199,8 +203,8 @@ __global__ void __launch_bounds__(256) b_sweep(int nx, int ny, int nz, const flo
 // J += dJ (final sweep buffer); rel = max |dJ| / |J| per wavelength.
 __global__ void b_update(int n, double *J, const double *buf0, const double *buf1,
                          int max_sweeps, BatchState *bs) {
-    const int l = blockIdx.y;
-    if (!bs->active[l]) return;
+    if ((int)blockIdx.y >= bs->nactive) return;
+    const int l = bs->alist[blockIdx.y];
     const int cnt = bs->done[l] ? bs->count[l] : max_sweeps;
     const double *dJ = (cnt & 1 ? buf1 : buf0) + (long long)l * n;
     double *Jl = J + (long long)l * n;
@@ -263,11 +267,42 @@ __global__ void b_retire(int nl, double tol, int max_iter, BatchState *bs) {
     }
 }
 
-__global__ void b_count_active(int nl, BatchState *bs) {
-    int c = 0;
-    for (int l = threadIdx.x; l < nl; l += 32) c += bs->active[l];
-    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-    if (threadIdx.x == 0) bs->nactive = c;
+// The active count and the compacted list of active wavelengths (one block
+// of 1024 threads: an exclusive scan of the active flags per chunk of 1024).
+__global__ void __launch_bounds__(1024) b_count_active(int nl, BatchState *bs) {
+    __shared__ int wsum[32];
+    __shared__ int total;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) total = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nl; c0 += 1024) {
+        const int l = c0 + threadIdx.x;
+        const int f = l < nl ? bs->active[l] : 0;
+        int incl = f;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int w = wsum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += y;
+            }
+            wsum[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        const int pos = total + (wid ? wsum[wid - 1] : 0) + incl - f;
+        if (f) bs->alist[pos] = l;
+        __syncthreads();
+        if (threadIdx.x == 0) total += wsum[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bs->nactive = total;
 }
 
 int grid_x(long long n, int threads, int cap) {
@@ -307,25 +342,27 @@ cudaError_t launch_b_fs(const BatchFsParams &p, int nl, const FsShape &sh, bool 
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, double *J, const double *eps,
-                                   const double *B, const float *a, const double *inv_diag,
+cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, int nlaunch, double *J,
+                                   const double *eps, const double *B, const float *a,
+                                   const double *inv_diag,
                                    double *r, double *buf0, double *buf1, float *b32_0,
                                    float *b32_1, int max_sweeps, double sweep_tol, double tol,
                                    int max_iter, bool parabolic, const FsShape &shape,
                                    cudaStream_t s) {
     const long long n = (long long)p.nx * p.ny * p.nz;
     const int gx = grid_x(n, 256, 2 * device_sm_count());
-    b_source<<<dim3(gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, J, eps, B, p.chiS, p.bs);
-    const cudaError_t fe = launch_b_fs(p, nl, shape, parabolic, s);
+    const int nw = nlaunch;
+    b_source<<<dim3(gx, nw), 256, 0, s>>>(p.nx, p.ny, p.nz, J, eps, B, p.chiS, p.bs);
+    const cudaError_t fe = launch_b_fs(p, nw, shape, parabolic, s);
     if (fe != cudaSuccess) return fe;
-    b_fold_init<<<dim3(gx < 2 ? 2 : gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, p.Jrep, J, inv_diag,
+    b_fold_init<<<dim3(gx < 2 ? 2 : gx, nw), 256, 0, s>>>(p.nx, p.ny, p.nz, p.Jrep, J, inv_diag,
                                                           r, buf0, b32_0, p.bs);
     for (int m = 1; m <= max_sweeps; ++m)
-        b_sweep<<<dim3(gx, nl), 256, 0, s>>>(p.nx, p.ny, p.nz, a, inv_diag, r, buf0, buf1, b32_0,
+        b_sweep<<<dim3(gx, nw), 256, 0, s>>>(p.nx, p.ny, p.nz, a, inv_diag, r, buf0, buf1, b32_0,
                                             b32_1, m, sweep_tol, p.bs);
-    b_update<<<dim3(gx, nl), 256, 0, s>>>((int)n, J, buf0, buf1, max_sweeps, p.bs);
+    b_update<<<dim3(gx, nw), 256, 0, s>>>((int)n, J, buf0, buf1, max_sweeps, p.bs);
     b_retire<<<(nl + 127) / 128, 128, 0, s>>>(nl, tol, max_iter, p.bs);
-    b_count_active<<<1, 32, 0, s>>>(nl, p.bs);
+    b_count_active<<<1, 1024, 0, s>>>(nl, p.bs);
     return cudaGetLastError();
 }
 

@@ -44,6 +44,11 @@ template <typename R> struct V2;
 template <> struct V2<float> { using T = float2; };
 template <> struct V2<double> { using T = double2; };
 
+// A contribution as the FP64 value its reduction adds: FP32 values widened by
+// integer moves (widen_f32), keeping the FP64 pipe free.
+__device__ __forceinline__ double red_value(float x) { return widen_f32(x); }
+__device__ __forceinline__ double red_value(double x) { return x; }
+
 // Taylor coefficients of p(u) = e2/u^3 = 2 sum_m (-1)^m u^m / (m+3)!.
 constexpr double fact(int n) { return n <= 1 ? 1.0 : n * fact(n - 1); }
 constexpr double pc(int m) { return (m % 2 ? -2.0 : 2.0) / fact(m + 3); }
@@ -168,10 +173,9 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
     const long long N = (long long)nray * p.nz;
 
     double I0 = 0.0;
-    if (!p.homogeneous) {
-        if (p.up[o]) I0 = p.bot_face ? p.bot_face[ray] : p.I_bot;
-        else I0 = p.top_face ? p.top_face[ray] : p.I_top;
-    }
+    if (!p.homogeneous)
+        I0 = entry_intensity(p.up[o], p.mu, o, ray, p.top_face, p.bot_face, p.bot_grad, p.I_top,
+                             p.I_bot);
     R I = (R)I0;
 
     int v = voxel_of(__ldg(code), x0, y0, p.nx, p.ny);
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
         }
         I = f.E * I + al * S_p + bg * S_c + ga * (S_n - S_c);
         const R c = __ldg(cw + k);
-        atomicAdd(p.J + v, (double)(c * I));
+        atomicAdd(p.J + v, red_value(c * I));
         if (LSTAR) {
             // ring[i] = dI_k / dS_{k-7+i}
 #pragma unroll
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
 #pragma unroll
             for (int i = 0; i < kWin; ++i) {
                 const unsigned dc = (unsigned)(wc >> (5 * i)) & 31u;
-                if (dc != kWinNone) atomicAdd(p.lstar + (long long)dc * N + v, (double)(c * ring[i]));
+                if (dc != kWinNone) atomicAdd(p.lstar + (long long)dc * N + v, red_value(c * ring[i]));
             }
         }
         chil_p = chil_c;
@@ -235,6 +239,10 @@ __global__ void __launch_bounds__(128) fs_kernel(FsParams p) {
         S_c = S_n;
         v = vn;
     }
+    // the widening does not carry a non-finite value: a non-finite intensity
+    // (it persists along the recurrence) makes J of the last point NaN
+    if (!(fabs((double)I) <= 1.79769313486231570e308))
+        atomicAdd(p.J + v, __longlong_as_double(0x7ff8000000000000LL));
 }
 
 // FP32 formal solution without Lambda* (every iteration after the first),
@@ -271,10 +279,9 @@ __global__ void __launch_bounds__(256) fs_fast_kernel(FsParams p) {
     const int x0 = ray % p.nx, y0 = ray / p.nx;
     s.base = x0 + 2 * p.nx * y0;
     double I0 = 0.0;
-    if (!p.homogeneous) {
-        if (p.up[o]) I0 = p.bot_face ? p.bot_face[ray] : p.I_bot;
-        else I0 = p.top_face ? p.top_face[ray] : p.I_top;
-    }
+    if (!p.homogeneous)
+        I0 = entry_intensity(p.up[o], p.mu, o, ray, p.top_face, p.bot_face, p.bot_grad, p.I_top,
+                             p.I_bot);
     s.I = (float)I0;
     s.vc = s.base + __float_as_int(r.x);
     const float2 cs = chiS[s.vc];
@@ -306,7 +313,7 @@ __global__ void __launch_bounds__(256) fs_fast_kernel(FsParams p) {
 }
 
 // FP32 formal solution without Lambda*, two characteristics per thread in
-// packed FP32x2 arithmetic (pair_advance): face cells (x0, y0) and
+// packed FP32x2 arithmetic (pair_advance_c): face cells (x0, y0) and
 // (x0, y0 + 1) with y0 even. Both sit at the same offset of the cached
 // characteristic, so one 16-byte load of the pair-packed (chi, S) (p.pairs)
 // serves both, and the step record (one 16-byte broadcast load per point) is
@@ -316,6 +323,8 @@ __global__ void __launch_bounds__(256) fs_fast_kernel(FsParams p) {
 // fs_fast_kernel (CONV: 0 both contributions widened by the conversion
 // instruction, 1 both by integer moves, 2 the first by conversion and the
 // second by integer moves).
+// The next point's step record and pair-packed (chi, S) are loaded one point
+// ahead, so the gather's L2 latency overlaps the arithmetic of a point.
 template <bool PARAB, int CONV>
 __global__ void __launch_bounds__(256) fs_pair_kernel(FsParams p) {
     const int nyh = (p.ny + 1) >> 1;
@@ -334,25 +343,30 @@ __global__ void __launch_bounds__(256) fs_pair_kernel(FsParams p) {
 
     float Ia = 0.0f, Ib = 0.0f;
     if (!p.homogeneous) {
-        const double *face = p.up[o] ? p.bot_face : p.top_face;
-        const double I1 = p.up[o] ? p.I_bot : p.I_top;
+        const bool up = p.up[o];
         const int fa = y0 * p.nx + x0;
-        Ia = (float)(face ? face[fa] : I1);
-        if (lb) Ib = (float)(face ? face[fa + p.nx] : I1);
+        Ia = (float)entry_intensity(up, p.mu, o, fa, p.top_face, p.bot_face, p.bot_grad, p.I_top,
+                                    p.I_bot);
+        if (lb)
+            Ib = (float)entry_intensity(up, p.mu, o, fa + p.nx, p.top_face, p.bot_face, p.bot_grad,
+                                        p.I_top, p.I_bot);
     }
     RayP s;
     const float4 r0 = __ldg(rec);
     int vc = __float_as_int(r0.x);
     pair_init(s, __ldg(P + vc), pk(r0.z, r0.w), Ia, Ib);
     float cwc = r0.y;
+    float4 rq = __ldg(rec + (K > 1 ? 1 : 0));
+    float4 cq = __ldg(P + __float_as_int(rq.x));
 #pragma unroll 2
     for (int k = 1; k < K; ++k) {
-        const float4 rn = __ldg(rec + k);
-        const int vn = __float_as_int(rn.x);
-        const float2 cI = mul2(pair_advance<PARAB>(s, P, vn, pk(rn.z, rn.w)), pk1(cwc));
+        const float4 rn = rq, cn = cq;
+        rq = __ldg(rec + (k + 1 < K ? k + 1 : k));
+        cq = __ldg(P + __float_as_int(rq.x));
+        const float2 cI = mul2(pair_advance_c<PARAB>(s, cn, pk(rn.z, rn.w)), pk1(cwc));
         atomicAdd(Ja + vc, pair_widen<CA>(cI.x));
         if (lb) atomicAdd(Jb + vc, pair_widen<CB>(cI.y));
-        vc = vn;
+        vc = __float_as_int(rn.x);
         cwc = rn.y;
     }
     // the last point: linear form
@@ -462,11 +476,12 @@ __global__ void __launch_bounds__(256, 3) fs_quad_kernel(FsParams p) {
 
     float Iv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (!p.homogeneous) {
-        const double *face = p.up[o] ? p.bot_face : p.top_face;
-        const double I1 = p.up[o] ? p.I_bot : p.I_top;
+        const bool up = p.up[o];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-            if (y0 + r < p.ny) Iv[r] = (float)(face ? face[(y0 + r) * p.nx + x0] : I1);
+            if (y0 + r < p.ny)
+                Iv[r] = (float)entry_intensity(up, p.mu, o, (y0 + r) * p.nx + x0, p.top_face,
+                                               p.bot_face, p.bot_grad, p.I_top, p.I_bot);
     }
     RayP a, b;
     const float4 r0 = __ldg(rec);
@@ -705,10 +720,9 @@ __global__ void __launch_bounds__(128) fs64_fast_kernel(FsParams p) {
     const int base = x0 + 2 * p.nx * y0;
 
     double I = 0.0;
-    if (!p.homogeneous) {
-        if (p.up[o]) I = p.bot_face ? p.bot_face[ray] : p.I_bot;
-        else I = p.top_face ? p.top_face[ray] : p.I_top;
-    }
+    if (!p.homogeneous)
+        I = entry_intensity(p.up[o], p.mu, o, ray, p.top_face, p.bot_face, p.bot_grad, p.I_top,
+                            p.I_bot);
     int vc = base + __float_as_int(__ldg(&rec[0].x));
     double2 r = __ldg(rd);
     const double2 cs = chiS[vc];

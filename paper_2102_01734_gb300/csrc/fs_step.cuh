@@ -242,13 +242,6 @@ __device__ __forceinline__ float2 pair_advance_c(RayP &s, const float4 &c, float
     return In;
 }
 
-// The same with the gather from P at offset vn.
-template <bool PARAB>
-__device__ __forceinline__ float2 pair_advance(RayP &s, const float4 *__restrict__ P, int vn,
-                                               float2 hl) {
-    return pair_advance_c<PARAB>(s, __ldg(P + vn), hl);
-}
-
 // The last point of a pair (linear form): its intensities.
 __device__ __forceinline__ float2 pair_last(const RayP &s) {
     const IntervalE2 f = interval2(s.u, s.nru);

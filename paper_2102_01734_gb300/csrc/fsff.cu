@@ -113,10 +113,9 @@ __global__ void __launch_bounds__(128) fsff_kernel(FsParams p, const float4 *__r
     const int base = ray % p.nx + 2 * p.nx * (ray / p.nx);
 
     double I0 = 0.0;
-    if (!p.homogeneous) {
-        if (p.up[o]) I0 = p.bot_face ? p.bot_face[ray] : p.I_bot;
-        else I0 = p.top_face ? p.top_face[ray] : p.I_top;
-    }
+    if (!p.homogeneous)
+        I0 = entry_intensity(p.up[o], p.mu, o, ray, p.top_face, p.bot_face, p.bot_grad, p.I_top,
+                             p.I_bot);
     ff I = ff_split(I0);
     int vc = base + __float_as_int(__ldg(&rec[0].x));
     float4 r = __ldg(rf);

@@ -33,6 +33,7 @@ struct Template {
     long long *toff = nullptr;  // [nangles] offset of its first point
     int *order = nullptr;       // [nangles] angles by decreasing length
     signed char *up = nullptr;  // [nangles] 1 if mu > 0 (enters at the bottom)
+    double *mu = nullptr;       // [nangles] direction cosine to the z axis
     uint32_t *code = nullptr;   // [total] step codes
     double *len64 = nullptr;    // [total] chords
     float *len32 = nullptr;
@@ -61,6 +62,22 @@ __host__ __device__ inline long long rep_index(int x, int y, int z, int nx, int 
     return (long long)x + 2LL * nx * ((long long)y + 2LL * ny * z);
 }
 
+// Intensity entering a characteristic through face cell f (Sec. 3.1): the
+// top face's for mu < 0, the bottom face's for mu > 0, a face array
+// overriding its scalar. A bottom gradient array gives the inner boundary the
+// LTE diffusion form of the paper's test cases, I = I_bot + mu dB/dtau (tau
+// the vertical optical depth, increasing inward), rounded as a product and a
+// sum.
+// mu (the direction cosines by angle) is read only with a gradient array.
+__device__ __forceinline__ double entry_intensity(bool up, const double *mu, int o, long long f,
+                                                  const double *top_face, const double *bot_face,
+                                                  const double *bot_grad, double I_top,
+                                                  double I_bot) {
+    if (!up) return top_face ? top_face[f] : I_top;
+    const double I = bot_face ? bot_face[f] : I_bot;
+    return bot_grad ? __dadd_rn(I, __dmul_rn(mu[o], bot_grad[f])) : I;
+}
+
 struct FsParams {
     int nx, ny, nz;
     int nangles;
@@ -85,6 +102,10 @@ struct FsParams {
     double *lstar;     // nullable [27][N], accumulated into
     const double *top_face;  // nullable [ny*nx]
     const double *bot_face;  // nullable [ny*nx]
+    // nullable [ny*nx]: dB/dtau of the diffusion inner boundary, the upward
+    // entry intensity being I_bot (face) + mu dB/dtau; mu = the template's
+    const double *bot_grad;
+    const double *mu;  // [nangles] direction cosines (read with bot_grad)
     double I_top, I_bot;
     double I_irr;      // spherical grid: irradiation
     int homogeneous;   // 1: zero boundary intensity, whatever the faces say
@@ -165,6 +186,10 @@ cudaError_t launch_pack(int nx, int ny, int nz, const double *chi, double chi_sc
 cudaError_t launch_source(int nx, int ny, int nz, const double *J, const double *eps,
                           const double *B, void *chiS, bool fp64, bool homogeneous,
                           cudaStream_t s);
+// bottom-face (B, dB/dtau) of the diffusion inner boundary for nl stacked
+// (chi, B) grids, outputs [nl][ny*nx]
+cudaError_t launch_diffusion_bc(int nx, int ny, int nz, int nl, const double *chi,
+                                const double *B, double *I_face, double *grad, cudaStream_t s);
 // periodic axes of the 27-point OS stencil: Cartesian box x and y, spherical
 // grid phi (the third index)
 struct Periodic {
@@ -296,6 +321,8 @@ constexpr int kHist = 11;         // changes kept per wavelength for the error e
 // n_lambda x (kBatchSweeps + 1), change history of n_lambda x kHist).
 struct BatchState {
     int *active;   // 1 while iterating
+    int *alist;    // [nactive] the active wavelengths in increasing order: the
+                   // batched kernels take wavelength alist[blockIdx.y] (.z)
     int *state;    // 0 running, 1 converged, 2 stagnated, 3 NaN, 4 iteration cap
     int *done;     // Jacobi stop test met
     int *count;    // Jacobi sweeps done
@@ -315,6 +342,8 @@ struct BatchFsParams {
     float2 *chiS;          // [n_lambda][4N]
     double *Jrep;          // [n_lambda][4N]
     const double *top_face, *bot_face;  // nullable [n_lambda][ny*nx]
+    const double *bot_grad;             // nullable [n_lambda][ny*nx]: diffusion dB/dtau
+    const double *mu;                   // [nangles] direction cosines
     double I_top, I_bot;
     BatchState *bs;        // device copy
 };
@@ -329,7 +358,11 @@ cudaError_t launch_b_source(const BatchFsParams &p, int nl, const double *J, con
 // characteristic per thread; rays_per_thread is not used)
 cudaError_t launch_b_fs(const BatchFsParams &p, int nl, const FsShape &sh, bool parabolic,
                         cudaStream_t s);
-cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, double *J, const double *eps,
+// nl: all wavelengths (retirement, compaction); nlaunch >= the active count:
+// the wavelength extent of the other launches (blocks past the active count
+// return at once)
+cudaError_t launch_batch_iteration(const BatchFsParams &p, int nl, int nlaunch, double *J,
+                                   const double *eps,
                                    const double *B, const float *a, const double *inv_diag,
                                    double *r, double *buf0, double *buf1, float *b32_0,
                                    float *b32_1, int max_sweeps, double sweep_tol, double tol,

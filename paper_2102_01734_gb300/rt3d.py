@@ -48,7 +48,7 @@ class GridDesc(ctypes.Structure):
 
 class BC(ctypes.Structure):
     _fields_ = [("I_top", _c_double), ("I_bottom", _c_double), ("I_top_face", _vp),
-                ("I_bottom_face", _vp), ("I_irr", _c_double)]
+                ("I_bottom_face", _vp), ("I_irr", _c_double), ("I_bottom_grad", _vp)]
 
 
 class SolveStats(ctypes.Structure):
@@ -95,7 +95,8 @@ class BatchStats(ctypes.Structure):
                 ("max_residual64", _c_double), ("batch_ms", _c_double), ("fs32_ms", _c_double),
                 ("fs64_ms", _c_double), ("seconds", _c_double), ("launches", ctypes.c_longlong),
                 ("fs_lambda_ff", ctypes.c_longlong), ("fsff_ms", _c_double),
-                ("fs_shape", FsShape), ("fs_tune_ms", ctypes.c_float * FS_TUNE_SHAPES)]
+                ("fs_shape", FsShape), ("fs_tune_ms", ctypes.c_float * FS_TUNE_SHAPES),
+                ("recaptures", _c_int)]
 
     def as_dict(self):
         out = {k: getattr(self, k) for k, _ in self._fields_}
@@ -143,6 +144,7 @@ def load(path: str | None = None):
     lib.rt3d_formal_solution.argtypes = [_vp, _vp, _vp, P(BC), _vp, _vp]
     lib.rt3d_os_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, _c_int, _c_double, P(_c_int)]
     lib.rt3d_formal_solution_ff.argtypes = [_vp, _vp, _vp, P(BC), _vp]
+    lib.rt3d_diffusion_bc.argtypes = [_vp, _c_int, _vp, _vp, _vp, _vp]
     lib.rt3d_ali_step.argtypes = [_vp, _vp, _vp, _vp, P(BC), _vp, P(_c_double)]
     lib.rt3d_solve.argtypes = [_vp, _vp, _vp, _vp, P(BC), _vp, _c_double, _c_int, P(SolveStats)]
     lib.rt3d_os_solve_noalloc.argtypes = [_c_int, _c_int, _c_int, _vp, _vp, _vp, _vp, _c_int,
@@ -205,7 +207,8 @@ def _empty_like(x, shape):
 
 
 def _bc(bc, keep):
-    """rt3d_bc from a dict {I_top: float|array, I_bottom: float|array}."""
+    """rt3d_bc from a dict {I_top: float|array, I_bottom: float|array,
+    I_bottom_grad: array (optional), I_irr: float (optional)}."""
     if bc is None:
         return None
     s = BC()
@@ -224,6 +227,14 @@ def _bc(bc, keep):
             setattr(s, fval, 0.0)
             setattr(s, fptr, _ptr(val))
     s.I_irr = float(bc.get("I_irr", 0.0))
+    grad = bc.get("I_bottom_grad")
+    if grad is not None:
+        if isinstance(grad, np.ndarray):
+            grad = np.ascontiguousarray(grad, dtype=np.float64)
+        elif _is_torch(grad):
+            grad = grad.to(torch.float64).contiguous()
+        keep.append(grad)
+        s.I_bottom_grad = _ptr(grad)
     return s
 
 
@@ -337,6 +348,18 @@ def formal_solution_ff(h, chi, S, bc=None, J_out=None):
     _check(load().rt3d_formal_solution_ff(h, _ptr(chi), _ptr(S), ctypes.byref(b) if b else None,
                                           _ptr(J_out)))
     return J_out
+
+
+def diffusion_bc(h, chi, B):
+    """Bottom-face (I_bottom, I_bottom_grad) of the diffusion inner boundary
+    from device tensors chi, B of shape (nz, ny, nx) or (n_lambda, nz, ny, nx);
+    returns two device tensors of shape (ny, nx) or (n_lambda, ny, nx)."""
+    nl = 1 if chi.dim() == 3 else int(chi.shape[0])
+    face_shape = tuple(chi.shape[:-3]) + tuple(chi.shape[-2:])
+    I_face = torch.empty(face_shape, dtype=torch.float64, device=chi.device)
+    grad = torch.empty_like(I_face)
+    _check(load().rt3d_diffusion_bc(h, nl, _ptr(chi), _ptr(B), _ptr(I_face), _ptr(grad)))
+    return I_face, grad
 
 
 def os_solve(h, lstar, eps, r, dJ_out, max_sweeps: int = 50, tol: float = 1e-3) -> int:
@@ -479,6 +502,9 @@ class Grid:
         J = J_out if J_out is not None else _empty_like(chi, self.shape)
         formal_solution_ff(self.handle, chi, S, bc, J)
         return J
+
+    def diffusion_bc(self, chi, B):
+        return diffusion_bc(self.handle, chi, B)
 
     def os_solve(self, lstar, eps, r, max_sweeps=50, tol=1e-3):
         dJ = _empty_like(r, r.shape)

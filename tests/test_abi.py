@@ -56,6 +56,7 @@ def test_null_arguments_are_einval(lib):
     assert lib.rt3d_grid_set_fs_shape(None, None) == rt3d.EINVAL
     assert lib.rt3d_grid_invalidate_lstar(None) == rt3d.EINVAL
     assert lib.rt3d_grid_set_os_solver(None, rt3d.OS_JACOBI) == rt3d.EINVAL
+    assert lib.rt3d_diffusion_bc(None, 1, None, None, None, None) == rt3d.EINVAL
     assert lib.rt3d_line_solve(None, 1, None, None, None, None, None, None, None, 1e-8, 10,
                                None) == rt3d.EINVAL
     # 3 ints (+4 padding), 4 doubles, 1 long long

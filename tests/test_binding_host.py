@@ -40,11 +40,17 @@ def test_bc_struct_from_scalars_and_faces():
     # a non-contiguous or integer face array is converted, and kept alive
     s = rt3d._bc({"I_bottom": np.arange(12).reshape(4, 3).T}, keep)
     assert keep[-1].dtype == np.float64 and keep[-1].flags.c_contiguous
+    assert not s.I_bottom_grad
+    # the diffusion gradient face is marshalled as its own pointer
+    grad = np.arange(12, dtype=np.float64).reshape(3, 4)
+    s = rt3d._bc({"I_bottom": face, "I_bottom_grad": grad}, keep)
+    assert s.I_bottom_grad == keep[-1].ctypes.data and s.I_bottom_face == keep[-2].ctypes.data
 
 
 def test_struct_layouts_match_the_header():
-    # rt3d_bc: 2 doubles, 2 pointers, 1 double
-    assert ctypes.sizeof(rt3d.BC) == 5 * 8
+    # rt3d_bc: 2 doubles, 2 pointers, 1 double, 1 pointer
+    assert ctypes.sizeof(rt3d.BC) == 6 * 8
+    assert rt3d.BC.I_bottom_grad.offset == 5 * 8
     # rt3d_grid_desc: geometry, n[3], ntheta, nphi, interp, precision,
     # nlambda (9 ints, +4 padding), stream pointer, accel (+4), r_in, r_out
     assert ctypes.sizeof(rt3d.GridDesc) == 9 * 4 + 4 + 8 + 4 + 4 + 2 * 8
