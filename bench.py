@@ -3,7 +3,8 @@
 A step is one converged solve (all steps of the path: tracer cache reused,
 FP32 formal solutions with the Lambda* band built in the first iteration (the
 band is dropped before every step, so each step builds it),
-FP64 Jacobi OS solves inside FGMRES, refinement residuals from float-float
+FP64 OS solves (eight-colour Gauss-Seidel by default) inside FGMRES,
+refinement residuals from float-float
 formal solutions (or FP64 with --precision mixed) and an FP64 formal solution
 certifying the result) of the box129_field workload: 129^3 periodic box,
 32 x 64 solid angles, parabolic interpolation, eps = 1e-6, chi = vertical
@@ -37,9 +38,16 @@ UNIT = "ray-segment updates/s"
 WORKLOAD = "box129_field"
 DESCR = ("129^3 periodic box, 32x64 angles, parabolic, eps=1e-6, chi=10^(-4+6(nz-1-z)/(nz-1))"
          " x exp(0.5 g), g ~ k^-3 Gaussian field (seed 1), B=1+0.2g; FP32 formal solution,"
-         " FP64 Jacobi/vector algebra, {refine} refinement residuals, FP64 formal solution"
+         " FP64 OS solves (preconditioner of FGMRES) and vector algebra, {refine} refinement"
+         " residuals, FP64 formal solution"
          " certifying the residual; converged to est. rel error 1e-8 from J=B")
 REFINE = {"ff": "float-float", "mixed": "FP64"}
+
+
+def os_solver_of(name):
+    from paper_2102_01734_gb300 import rt3d
+    return {"jacobi": rt3d.OS_JACOBI, "gs": rt3d.OS_GAUSS_SEIDEL,
+            "bicgstab": rt3d.OS_BICGSTAB}[name]
 
 
 def precision_of(name):
@@ -261,6 +269,7 @@ def run_ours(args):
     # weak scaling: every rank solves its own atmosphere (independent problems)
     chi, eps, B, bc = inputs.cartesian_config(n, cfg["eps"], seed=cfg["seed"] + rank)
     g = rt3d.Grid(n, cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, precision_of(args.precision))
+    g.set_os_solver(os_solver_of(args.os_solver))
     info = g.info()
     seg_per_fs = info["segments"]
     tchi, teps, tB = (torch.from_numpy(a).to(dev) for a in (chi, eps, B))
@@ -356,7 +365,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "description": DESCR.format(refine=REFINE[args.precision]),
-                   "precision": args.precision, "grid": [n, n, n],
+                   "precision": args.precision, "os_solver": args.os_solver,
+                   "grid": [n, n, n],
                    "angles": [cfg["ntheta"], cfg["nphi"]], "segments_per_fs": seg_per_fs,
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -455,6 +465,112 @@ def run_kernels(args):
                           "note": "includes the fold and staging on the current stream"}))
     torch.cuda.synchronize()
     print("kernels done")
+    return 0
+
+
+def run_os_solvers(args):
+    """The converged solve of the workload with each OS solver as the Krylov
+    preconditioner (Jacobi, eight-colour Gauss-Seidel, BiCGStab): seconds,
+    formal solutions and OS sweeps per solve (CUDA events around the solve,
+    Lambda* built in each), and each solver's sweep alone on the workload's
+    band."""
+    import torch
+
+    from paper_2102_01734_gb300 import build, inputs, rt3d
+
+    build.build()
+    cfg = inputs.CONFIGS[WORKLOAD]
+    chi, eps, B, bc = inputs.cartesian_config(cfg["n"], cfg["eps"], seed=cfg["seed"])
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    tchi, teps, tB = d(chi), d(eps), d(B)
+    tbc = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}
+    g = rt3d.Grid(cfg["n"], cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, precision_of(args.precision))
+    names = {rt3d.OS_JACOBI: "jacobi", rt3d.OS_GAUSS_SEIDEL: "gauss_seidel",
+             rt3d.OS_BICGSTAB: "bicgstab"}
+    J = tB.clone()
+    g.solve(tchi, teps, tB, tbc, J, tol=args.tol, max_iter=args.max_iter)  # tune, warm up
+    ref = J.clone()
+    # one OS solve on the workload's band: its own cost per sweep
+    Jfs, L = g.formal_solution(tchi, tB, tbc, lstar=True)
+    r = Jfs - tB
+    for kind in (rt3d.OS_JACOBI, rt3d.OS_GAUSS_SEIDEL, rt3d.OS_BICGSTAB):
+        g.set_os_solver(kind)
+        g.os_solve(L, teps, r, max_sweeps=4, tol=0.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        _, m = g.os_solve(L, teps, r, max_sweeps=20, tol=0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"os_solver": names[kind], "sweeps": m,
+                          "ms_per_sweep": e0.elapsed_time(e1) / m,
+                          "note": "20 sweeps (BiCGStab: iterations, two matrix products each) on "
+                                  "the workload's band, tol 0; includes the OS right-hand side"}))
+    for kind in (rt3d.OS_JACOBI, rt3d.OS_GAUSS_SEIDEL, rt3d.OS_BICGSTAB):
+        g.set_os_solver(kind)
+        J = tB.clone()
+        g.invalidate_lstar()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = g.solve(tchi, teps, tB, tbc, J, tol=args.tol, max_iter=args.max_iter)
+        e1.record()
+        torch.cuda.synchronize()
+        dj = float(torch.max(torch.abs(J / ref - 1)))
+        print(json.dumps({"os_solver": names[kind], "solve_s": e0.elapsed_time(e1) / 1e3,
+                          "fs_fp32": st["fs_fp32"], "fs_ff": st["fs_ff"], "fs_fp64": st["fs_fp64"],
+                          "os_sweeps": st["jacobi_sweeps"], "residual64": st["residual64"],
+                          "est_error": st["est_error"], "max_rel_diff_vs_jacobi_solve": dj}))
+    return 0
+
+
+def run_diffusion(args):
+    """The grey atmosphere of the paper's test cases (B = 3/4 (tau + 2/3)) on the
+    workload's 129^3 box and angles with the LTE diffusion inner boundary
+    (face arrays from rt3d_diffusion_bc): converged solve (CUDA events, Lambda*
+    built in it) against the same solve with the plain I = B bottom rule, and
+    J/B - 1 averaged over the innermost layer for both."""
+    import torch
+
+    from paper_2102_01734_gb300 import build, inputs, rt3d
+
+    build.build()
+    cfg = inputs.CONFIGS[WORKLOAD]
+    chi, eps, B, _ = inputs.grey_config(cfg["n"], args.diff_eps, seed=cfg["seed"])
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    tchi, teps, tB = d(chi), d(eps), d(B)
+    g = rt3d.Grid(cfg["n"], cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, precision_of(args.precision))
+    g.set_os_solver(os_solver_of(args.os_solver))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    I_face, grad = g.diffusion_bc(tchi, tB)
+    e1.record()
+    torch.cuda.synchronize()
+    bc_ms = e0.elapsed_time(e1)
+    rules = {"diffusion": {"I_top": 0.0, "I_bottom": I_face, "I_bottom_grad": grad},
+             "plain_I_eq_B": {"I_top": 0.0, "I_bottom": tB[0].contiguous()}}
+    J = tB.clone()
+    g.solve(tchi, teps, tB, rules["diffusion"], J, tol=args.tol, max_iter=args.max_iter)  # warm-up
+    seg = g.info()["segments"]
+    for name, bc in rules.items():
+        J = tB.clone()
+        g.invalidate_lstar()
+        torch.cuda.synchronize()
+        e0.record()
+        st = g.solve(tchi, teps, tB, bc, J, tol=args.tol, max_iter=args.max_iter)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        nfs = st["fs_fp32"] + st["fs_fp64"] + st["fs_ff"]
+        inner = float(torch.mean(J[0] / tB[0] - 1.0))
+        print(json.dumps({"workload": "box129_grey", "inner_bc": name, "eps": args.diff_eps,
+                          "solve_s": sec, "solves_per_s": 1.0 / sec,
+                          "segments_per_s": seg * nfs / sec, "fs_fp32": st["fs_fp32"],
+                          "fs_ff": st["fs_ff"], "fs_fp64": st["fs_fp64"],
+                          "residual64": st["residual64"], "est_error": st["est_error"],
+                          "mean_J_over_B_minus_1_inner_layer": inner,
+                          "diffusion_bc_ms": bc_ms}))
     return 0
 
 
@@ -738,6 +854,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-angles", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--os-solver", default="gs", choices=["jacobi", "gs", "bicgstab"],
+                    help="OS solver of the Krylov preconditioner (eight-colour Gauss-Seidel: "
+                         "fewest formal solutions on this workload)")
+    ap.add_argument("--os-solvers", action="store_true",
+                    help="converged solve with each OS solver as the preconditioner")
     ap.add_argument("--kernels", action="store_true",
                     help="run the profiling workload (for ncu) instead of the benchmark")
     ap.add_argument("--fp64-fs", action="store_true", help="with --kernels: add an FP64 FS")
@@ -750,6 +871,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="with --precisions: skip the FP64 path")
     ap.add_argument("--precision", default="ff", choices=["ff", "mixed"],
                     help="refinement residuals: float-float (ff) or FP64 (mixed)")
+    ap.add_argument("--diffusion", action="store_true",
+                    help="grey atmosphere with the diffusion inner boundary vs I = B")
+    ap.add_argument("--diff-eps", type=float, default=1e-2)
     ap.add_argument("--spherical", action="store_true",
                     help="spherical shell at a reduced size (ray-set build, FS, solve)")
     ap.add_argument("--sph-n", type=int, nargs=3, default=[65, 33, 65])
@@ -774,6 +898,10 @@ def main():
         return run_warmstart(args)
     if args.precisions:
         return run_precisions(args)
+    if args.os_solvers:
+        return run_os_solvers(args)
+    if args.diffusion:
+        return run_diffusion(args)
     if args.spherical:
         return run_spherical(args)
     if args.line:
