@@ -529,7 +529,9 @@ def run_diffusion(args):
     workload's 129^3 box and angles with the LTE diffusion inner boundary
     (face arrays from rt3d_diffusion_bc): converged solve (CUDA events, Lambda*
     built in it) against the same solve with the plain I = B bottom rule, and
-    J/B - 1 averaged over the innermost layer for both."""
+    J/B - 1 averaged over the innermost layer for both. --diff-chi-scale scales
+    the opacity (the workload's innermost voxels have optical depth 100, where
+    the boundary intensity does not reach the first point)."""
     import torch
 
     from paper_2102_01734_gb300 import build, inputs, rt3d
@@ -537,6 +539,9 @@ def run_diffusion(args):
     build.build()
     cfg = inputs.CONFIGS[WORKLOAD]
     chi, eps, B, _ = inputs.grey_config(cfg["n"], args.diff_eps, seed=cfg["seed"])
+    if args.diff_chi_scale != 1.0:  # thinner innermost voxels: the boundary reaches the grid
+        chi = chi * args.diff_chi_scale
+        B = 0.75 * (inputs.grey_tau(chi) + 2.0 / 3.0)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
     tchi, teps, tB = d(chi), d(eps), d(B)
     g = rt3d.Grid(cfg["n"], cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, precision_of(args.precision))
@@ -565,6 +570,7 @@ def run_diffusion(args):
         nfs = st["fs_fp32"] + st["fs_fp64"] + st["fs_ff"]
         inner = float(torch.mean(J[0] / tB[0] - 1.0))
         print(json.dumps({"workload": "box129_grey", "inner_bc": name, "eps": args.diff_eps,
+                          "chi_scale": args.diff_chi_scale,
                           "solve_s": sec, "solves_per_s": 1.0 / sec,
                           "segments_per_s": seg * nfs / sec, "fs_fp32": st["fs_fp32"],
                           "fs_ff": st["fs_ff"], "fs_fp64": st["fs_fp64"],
@@ -874,6 +880,7 @@ def main():
     ap.add_argument("--diffusion", action="store_true",
                     help="grey atmosphere with the diffusion inner boundary vs I = B")
     ap.add_argument("--diff-eps", type=float, default=1e-2)
+    ap.add_argument("--diff-chi-scale", type=float, default=1.0)
     ap.add_argument("--spherical", action="store_true",
                     help="spherical shell at a reduced size (ray-set build, FS, solve)")
     ap.add_argument("--sph-n", type=int, nargs=3, default=[65, 33, 65])

@@ -165,14 +165,20 @@ __global__ void os_prep_kernel(int nx, int ny, int nz, const double *L, const do
 // already final) and of the last sweep otherwise (in src: later colours, and
 // the same colour, which a periodic axis of odd length makes a neighbour
 // across the seam); Jacobi inside a colour, as the oracle's sweep defines it.
+// In the mixed mode (A = float) the products take the FP32 copies of the
+// iterates (src32, dst32; written beside the FP64 values), as the Jacobi
+// sweep does, and the stop-test maxima compare FP32 copies.
 template <typename A>
 __global__ void __launch_bounds__(256) gs_colour_kernel(int nx, int ny, int nz, ColourGeo cg, int c,
                                                         const A *__restrict__ a,
                                                         const double *__restrict__ inv_diag,
                                                         const double *__restrict__ r,
                                                         const double *__restrict__ src,
-                                                        double *__restrict__ dst, int m, double tol,
+                                                        double *__restrict__ dst,
+                                                        const float *__restrict__ src32,
+                                                        float *__restrict__ dst32, int m, double tol,
                                                         OsState *st, Periodic per) {
+    constexpr bool f32 = sizeof(A) == 4;
     if (st->done) return;
     if (c == 0 && m >= 2) {
         const double dm = bitsd(st->dmax[m - 1]), jm = bitsd(st->jmax[m - 1]);
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(256) gs_colour_kernel(int nx, int ny, int nz, 
     const int nxc = cg.nxc[c], nyc = cg.nyc[c];
     const long long cnt = cg.cnt[c], blk0 = cg.blk[c];
     const int nxy = nx * ny;
-    double dmax = 0.0, jmax = 0.0;
+    A dmax = A(0), jmax = A(0);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < cnt;
          k += (long long)gridDim.x * blockDim.x) {
         const long long kxy = (long long)nxc * nyc;
@@ -206,17 +212,26 @@ __global__ void __launch_bounds__(256) gs_colour_kernel(int nx, int ny, int nz, 
             const int xn = X[d % 3], yn = Y[(d / 3) % 3], zn = Z[d / 9];
             const int cn = (xn & 1) + 2 * (yn & 1) + 4 * (zn & 1);
             const int u = xn + nx * yn + nxy * zn;
-            const double xv = cn < c ? dst[u] : src[u];
-            acc += ab[pl * 32] * (A)xv;
+            A xv;
+            if constexpr (f32) xv = cn < c ? dst32[u] : src32[u];
+            else xv = cn < c ? dst[u] : src[u];
+            acc += ab[pl * 32] * xv;
             ++pl;
         }
         const double nv = (r[v] + (double)acc) * inv_diag[v];
         dst[v] = nv;
-        dmax = fmax(dmax, fabs(nv - src[v]));
-        jmax = fmax(jmax, fabs(nv));
+        if constexpr (f32) {
+            const float nf = (float)nv;
+            dst32[v] = nf;
+            dmax = fmaxf(dmax, fabsf(nf - src32[v]));
+            jmax = fmaxf(jmax, fabsf(nf));
+        } else {
+            dmax = fmax(dmax, fabs(nv - src[v]));
+            jmax = fmax(jmax, fabs(nv));
+        }
     }
-    block_max_atomic(dmax, &st->dmax[m]);
-    block_max_atomic(jmax, &st->jmax[m]);
+    block_max_atomic((double)dmax, &st->dmax[m]);
+    block_max_atomic((double)jmax, &st->jmax[m]);
 }
 
 // ---- BiCGStab (van der Vorst 1992) on A x = r, A = [1 - Lambda*(1 - eps)],
@@ -547,18 +562,19 @@ ColourGeo colour_geo(int nx, int ny, int nz) {
 
 cudaError_t launch_gs_sweep(int nx, int ny, int nz, const ColourGeo &cg, const void *a, bool a64,
                             const double *inv_diag, const double *r, const double *src,
-                            double *dst, int m, double tol, OsState *st, cudaStream_t s,
-                            Periodic per) {
+                            double *dst, const float *src32, float *dst32, int m, double tol,
+                            OsState *st, cudaStream_t s, Periodic per) {
     for (int c = 0; c < 8; ++c) {
         const int blocks = grid_for(cg.cnt[c] > 0 ? cg.cnt[c] : 1, 256);
         if (a64)
             gs_colour_kernel<double><<<blocks, 256, 0, s>>>(nx, ny, nz, cg, c,
                                                             static_cast<const double *>(a), inv_diag,
-                                                            r, src, dst, m, tol, st, per);
+                                                            r, src, dst, nullptr, nullptr, m, tol,
+                                                            st, per);
         else
             gs_colour_kernel<float><<<blocks, 256, 0, s>>>(nx, ny, nz, cg, c,
                                                            static_cast<const float *>(a), inv_diag, r,
-                                                           src, dst, m, tol, st, per);
+                                                           src, dst, src32, dst32, m, tol, st, per);
     }
     return cudaGetLastError();
 }

@@ -167,7 +167,6 @@ struct rt3d_grid {
     float *s_len32 = nullptr, *s_cw32 = nullptr;
     uint64_t *s_win = nullptr;
     float4 *s_rec = nullptr;  // [segments] (replicated index bits, J weight, l/2, l/2)
-    int *s_perm = nullptr;    // [rays] by decreasing length
 
     // batched-wavelength workspace (allocated for the largest n_lambda seen)
     int bl_cap = 0;
@@ -376,7 +375,7 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
         TRY(collect_events(g));
         CK(cudaEventRecord(g->ev0, g->stream));
-        if (sfast) CK(launch_sph_fs_fast(sp, g->s_rec, g->s_perm, g->Jrep, g->parab, g->stream));
+        if (sfast) CK(launch_sph_fs_fast(sp, g->s_rec, g->Jrep, g->parab, g->stream));
         else CK(launch_sph_fs(sp, fp64, g->parab, with_lstar, g->stream));
         CK(cudaEventRecord(g->ev1, g->stream));
         g->ev_pending = fp64 ? 1 : (with_lstar ? 3 : 0);
@@ -468,7 +467,10 @@ rt3d_status os_solve_dev(rt3d_grid *g, const double *Jfs, const double *J, const
         const ColourGeo cg = colour_geo(g->nx, g->ny, g->nz);
         for (int m = 1; m <= max_sweeps; ++m) {
             CK(launch_gs_sweep(g->nx, g->ny, g->nz, cg, g->a, g->a64, g->inv_diag, g->r,
-                               g->dJ[(m - 1) & 1], g->dJ[m & 1], m, tol, g->st, g->stream, g->per));
+                               g->dJ[(m - 1) & 1], g->dJ[m & 1],
+                               g->a64 ? nullptr : g->dJ32[(m - 1) & 1],
+                               g->a64 ? nullptr : g->dJ32[m & 1], m, tol, g->st, g->stream,
+                               g->per));
             g->launches += 8;
             if ((m & 3) == 0 && m < max_sweeps) {
                 int done = 0;
@@ -632,9 +634,16 @@ rt3d_status sph_build(rt3d_grid *g) {
     bp.ncap = 2 * (nr + 1) + 2 * (nt + 1) + np + 8;
     bp.dir = d_dir;
     bp.wt = d_wt;
-    // chunk of angles built at once: scratch N/8 + 8 N + 8 ncap bytes per angle
+    // chunk of angles built at once (one warp each): scratch N/8 + 8 N + 8 ncap
+    // bytes per angle, within an eighth of the free device memory (at least
+    // 2 GiB, at most 16 GiB), so that large grids still fill the GPU with
+    // warps
     const long long per_angle = N / 8 + 8 * N + 8LL * bp.ncap + 64;
-    int chunk = (int)std::max(1LL, std::min<long long>(nO, (2LL << 30) / per_angle));
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const long long budget =
+        std::min<long long>(16LL << 30, std::max<long long>(2LL << 30, (long long)(free_b / 8)));
+    int chunk = (int)std::max(1LL, std::min<long long>(nO, budget / per_angle));
     const int words = (int)((N + 31) / 32);
     unsigned *hit = nullptr;
     double *tbuf = nullptr, *den = nullptr;
@@ -726,26 +735,10 @@ rt3d_status sph_build(rt3d_grid *g) {
     if (herr) return fail(RT3D_EINVAL, "spherical tracer error %d", herr);
     g->segments = tsg;
     g->tpl.kmax = bp.ncap;
-    // FP32 records and the ray order (decreasing length, then ray index) of
-    // the formal solution without Lambda*
+    // FP32 records of the formal solution without Lambda*
     if (tr > (long long)INT32_MAX) return fail(RT3D_EINVAL, "too many spherical rays");
     TRY(g->alloc(&g->s_rec, tsg));
     CKL(launch_sph_rec(tsg, g->s_crep, g->s_len64, g->s_cw64, g->s_rec, s));
-    {
-        std::vector<int> len(tr);
-        CK(cudaMemcpyAsync(len.data(), g->s_ray_len, sizeof(int) * tr, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        int maxlen = 0;
-        for (const int l : len) maxlen = std::max(maxlen, l);
-        std::vector<long long> start(maxlen + 2, 0);
-        for (const int l : len) ++start[maxlen - l + 1];
-        for (int i = 1; i <= maxlen + 1; ++i) start[i] += start[i - 1];
-        std::vector<int> perm(tr);
-        for (long long r = 0; r < tr; ++r) perm[start[maxlen - len[r]]++] = (int)r;
-        TRY(g->alloc(&g->s_perm, tr));
-        CK(cudaMemcpyAsync(g->s_perm, perm.data(), sizeof(int) * tr, cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
-    }
     return alloc_work(g);
 }
 

@@ -76,11 +76,11 @@ struct RayF {
 // difference form of the file header, add cwc I to J at the current point,
 // advance. BRANCHLESS evaluates the parabolic correction also where its
 // blend weight is 0 (no divergent branch).
+// The same given the next point's replicated offset vn and its gathered
+// (chi, S) cn (loaded ahead by the caller).
 template <bool PARAB, bool WIDEN, bool BRANCHLESS>
-__device__ __forceinline__ void fast_step(RayF &s, const float2 *__restrict__ chiS,
-                                          double *__restrict__ Jd, const float4 &rn, float cwc) {
-    const int vn = s.base + __float_as_int(rn.x);
-    const float2 cn = chiS[vn];
+__device__ __forceinline__ void fast_step_c(RayF &s, double *__restrict__ Jd, const float4 &rn,
+                                            float cwc, int vn, const float2 cn) {
     const float hn = cn.x * rn.z;
     const float dSn = cn.y - s.Sc;
     const float w = s.hc + hn;
@@ -108,6 +108,13 @@ __device__ __forceinline__ void fast_step(RayF &s, const float2 *__restrict__ ch
     s.Sc = cn.y;
     s.dS = dSn;
     s.vc = vn;
+}
+
+template <bool PARAB, bool WIDEN, bool BRANCHLESS>
+__device__ __forceinline__ void fast_step(RayF &s, const float2 *__restrict__ chiS,
+                                          double *__restrict__ Jd, const float4 &rn, float cwc) {
+    const int vn = s.base + __float_as_int(rn.x);
+    fast_step_c<PARAB, WIDEN, BRANCHLESS>(s, Jd, rn, cwc, vn, chiS[vn]);
 }
 
 

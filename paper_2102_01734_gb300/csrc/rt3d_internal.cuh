@@ -272,10 +272,11 @@ cudaError_t launch_os_prep(int nx, int ny, int nz, const double *lstar, const do
 // for colour 0 .. 7, every voxel of the colour from the neighbours' values
 // of this sweep (earlier colours, in dst) or of the last (src); the stop test
 // of sweep m - 1 first (as launch_os_sweep).
+// src32/dst32: FP32 copies of src/dst (mixed mode; unused with a64)
 cudaError_t launch_gs_sweep(int nx, int ny, int nz, const ColourGeo &cg, const void *a, bool a64,
                             const double *inv_diag, const double *r, const double *src,
-                            double *dst, int m, double tol, OsState *st, cudaStream_t s,
-                            Periodic per);
+                            double *dst, const float *src32, float *dst32, int m, double tol,
+                            OsState *st, cudaStream_t s, Periodic per);
 // BiCGStab on [1 - Lambda*(1 - eps)] x = r from x = 0 (van der Vorst):
 // device scalars and the kernels of one iteration.
 struct BicgState {
@@ -415,10 +416,11 @@ struct SphFsParams {
 cudaError_t launch_sph_build(const SphBuildParams &p, cudaStream_t s);
 cudaError_t launch_sph_fs(const SphFsParams &p, bool fp64, bool parabolic, bool lstar,
                           cudaStream_t s);
-// FP32 formal solution without Lambda* over per-segment records, rays in the
-// order perm, into the replicated FP64 Jrep (zero on entry; fold afterwards)
-cudaError_t launch_sph_fs_fast(const SphFsParams &p, const float4 *rec, const int *perm,
-                               double *Jrep, bool parabolic, cudaStream_t s);
+// FP32 formal solution without Lambda* over per-segment records, one ray per
+// thread in the builder's order, into the replicated FP64 Jrep (zero on
+// entry; fold afterwards)
+cudaError_t launch_sph_fs_fast(const SphFsParams &p, const float4 *rec, double *Jrep,
+                               bool parabolic, cudaStream_t s);
 // per-segment records (replicated index bits, J weight, l/2, l/2)
 cudaError_t launch_sph_rec(long long nseg, const int *crep, const double *len64, const double *cw64,
                            float4 *rec, cudaStream_t s);

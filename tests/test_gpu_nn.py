@@ -240,9 +240,10 @@ def test_network_layers_and_gradients_against_oracle(ws):
 
 def test_training_reduces_the_starting_error(ws):
     """Train on solved 16^3 boxes; on three held-out boxes the network's
-    prediction is closer to the converged J than J = B is, and the plain ALI
-    (Eq. alo) started from it reaches the same certified J in at least 5 %
-    fewer iterations in total."""
+    prediction is closer to the converged J than J = B is, stays closer after
+    the same number of ALI iterations (Eq. alo), and the converged, certified
+    solve (FGMRES, the library's default iteration) started from it needs at
+    least 15 % fewer formal solutions in total, reaching the same J."""
     from paper_2102_01734_gb300 import inputs, rt3d
     n, nth, nph = 16, 4, 8
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
@@ -257,23 +258,30 @@ def test_training_reduces_the_starting_error(ws):
     train, held = data[:10], data[10:]
     net = ws.UNet(seed=0)
     ws.train(net, train, 500, lr=2e-3, lr_final=2e-4)
-    # the plain ALI reduces the error by a fixed factor per iteration, so a
-    # start closer to the solution needs fewer iterations
     ga = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI, accel=rt3d.ACCEL_NONE)
-    it_b = it_n = 0
+    gk = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, rt3d.FP32_FS_FP64_ALI, accel=rt3d.ACCEL_KRYLOV)
+    fs_b = fs_n = 0
+    lmax = lambda A, Jc: float(torch.max(torch.abs(torch.log(A / Jc))))
     for chi, eps, B, J, bc in held:
         pred = net.predict(chi, eps, B, B)
-        err_net = float(torch.max(torch.abs(torch.log(pred / J))))
-        err_b = float(torch.max(torch.abs(torch.log(B / J))))
+        err_net, err_b = lmax(pred, J), lmax(B, J)
         assert err_net < 0.5 * err_b, (err_net, err_b)
         bcd = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}
+        # equal work: five ALI iterations from each start
+        Jb, Jn = B[0].clone(), pred[0].clone()
+        for _ in range(5):
+            ga.ali_step(chi[0], eps[0], B[0], bcd, Jb)
+            ga.ali_step(chi[0], eps[0], B[0], bcd, Jn)
+        e5_b, e5_n = lmax(Jb, J[0]), lmax(Jn, J[0])
+        assert e5_n < 0.1 * e5_b, (e5_n, e5_b)
+        # the certified solve from each start
         J1 = B[0].clone()
-        st_b = ga.solve(chi[0], eps[0], B[0], bcd, J1, tol=1e-9, max_iter=20000)
+        st_b = gk.solve(chi[0], eps[0], B[0], bcd, J1, tol=1e-9, max_iter=20000)
         J2 = pred[0].clone()
-        st_n = ga.solve(chi[0], eps[0], B[0], bcd, J2, tol=1e-9, max_iter=20000)
+        st_n = gk.solve(chi[0], eps[0], B[0], bcd, J2, tol=1e-9, max_iter=20000)
         assert torch.max(torch.abs(J2 / J1 - 1)) < 1e-8
-        it_b += st_b["iterations"]
-        it_n += st_n["iterations"]
-        print("warm start: ALI iterations from J = B", st_b["iterations"], "from the network",
-              st_n["iterations"], "start error", err_b, err_net)
-    assert it_n <= 0.95 * it_b, (it_n, it_b)
+        fs_b += st_b["fs_fp32"] + st_b["fs_fp64"]
+        fs_n += st_n["fs_fp32"] + st_n["fs_fp64"]
+        print("warm start: error after 5 ALI iterations", e5_b, e5_n, "formal solutions",
+              st_b["fs_fp32"] + st_b["fs_fp64"], st_n["fs_fp32"] + st_n["fs_fp64"])
+    assert fs_n <= 0.85 * fs_b, (fs_n, fs_b)
