@@ -162,11 +162,11 @@ struct rt3d_grid {
     std::vector<int> s_nrays_angle;
     long long *s_ray_off = nullptr;
     int *s_ray_len = nullptr, *s_ray_angle = nullptr, *s_ray_launch = nullptr;
-    int *s_ray_kind = nullptr, *s_ray_face = nullptr, *s_cell = nullptr, *s_crep = nullptr;
+    int *s_ray_kind = nullptr, *s_ray_face = nullptr;
+    // per segment (32 bytes): record (replicated index bits, FP32 J weight,
+    // l/2, l/2), FP64 chord and J weight
+    float4 *s_rec = nullptr;
     double *s_len64 = nullptr, *s_cw64 = nullptr;
-    float *s_len32 = nullptr, *s_cw32 = nullptr;
-    uint64_t *s_win = nullptr;
-    float4 *s_rec = nullptr;  // [segments] (replicated index bits, J weight, l/2, l/2)
 
     // batched-wavelength workspace (allocated for the largest n_lambda seen)
     int bl_cap = 0;
@@ -357,11 +357,12 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         sp.ray_len = g->s_ray_len;
         sp.ray_kind = g->s_ray_kind;
         sp.ray_face = g->s_ray_face;
-        sp.cell = g->s_cell;
-        sp.crep = g->s_crep;
-        sp.len = fp64 ? (const void *)g->s_len64 : (const void *)g->s_len32;
-        sp.cw = fp64 ? (const void *)g->s_cw64 : (const void *)g->s_cw32;
-        sp.win = g->s_win;
+        sp.nr = g->nx;
+        sp.nt = g->ny;
+        sp.np = g->nz;
+        sp.rec = g->s_rec;
+        sp.len64 = g->s_len64;
+        sp.cw64 = g->s_cw64;
         sp.chiS = p.chiS;
         sp.J = g->Jfs;
         sp.lstar = p.lstar;
@@ -375,7 +376,7 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
         TRY(collect_events(g));
         CK(cudaEventRecord(g->ev0, g->stream));
-        if (sfast) CK(launch_sph_fs_fast(sp, g->s_rec, g->Jrep, g->parab, g->stream));
+        if (sfast) CK(launch_sph_fs_fast(sp, g->Jrep, g->parab, g->stream));
         else CK(launch_sph_fs(sp, fp64, g->parab, with_lstar, g->stream));
         CK(cudaEventRecord(g->ev1, g->stream));
         g->ev_pending = fp64 ? 1 : (with_lstar ? 3 : 0);
@@ -700,13 +701,9 @@ rt3d_status sph_build(rt3d_grid *g) {
     TRY(g->alloc(&g->s_ray_launch, tr));
     TRY(g->alloc(&g->s_ray_kind, tr));
     TRY(g->alloc(&g->s_ray_face, tr));
-    TRY(g->alloc(&g->s_cell, tsg));
-    TRY(g->alloc(&g->s_crep, tsg));
+    TRY(g->alloc(&g->s_rec, tsg));
     TRY(g->alloc(&g->s_len64, tsg));
     TRY(g->alloc(&g->s_cw64, tsg));
-    TRY(g->alloc(&g->s_len32, tsg));
-    TRY(g->alloc(&g->s_cw32, tsg));
-    TRY(g->alloc(&g->s_win, tsg));
     bp.pass = 2;
     bp.ray_base = d_rbase;
     bp.seg_base = d_sbase;
@@ -716,13 +713,9 @@ rt3d_status sph_build(rt3d_grid *g) {
     bp.ray_launch = g->s_ray_launch;
     bp.ray_kind = g->s_ray_kind;
     bp.ray_face = g->s_ray_face;
-    bp.cell = g->s_cell;
-    bp.crep = g->s_crep;
+    bp.rec = g->s_rec;
     bp.len64 = g->s_len64;
     bp.cw64 = g->s_cw64;
-    bp.len32 = g->s_len32;
-    bp.cw32 = g->s_cw32;
-    bp.win = g->s_win;
     for (int o0 = 0; o0 < nO; o0 += chunk) {
         bp.o0 = o0;
         bp.nchunk = std::min(chunk, nO - o0);
@@ -735,10 +728,7 @@ rt3d_status sph_build(rt3d_grid *g) {
     if (herr) return fail(RT3D_EINVAL, "spherical tracer error %d", herr);
     g->segments = tsg;
     g->tpl.kmax = bp.ncap;
-    // FP32 records of the formal solution without Lambda*
     if (tr > (long long)INT32_MAX) return fail(RT3D_EINVAL, "too many spherical rays");
-    TRY(g->alloc(&g->s_rec, tsg));
-    CKL(launch_sph_rec(tsg, g->s_crep, g->s_len64, g->s_cw64, g->s_rec, s));
     return alloc_work(g);
 }
 
@@ -1474,9 +1464,15 @@ rt3d_status rt3d_grid_sph_ray(const rt3d_grid *gc, int angle, int index, int *K,
         return fail(RT3D_EINVAL, "capacity below %d points", k);
     }
     *K = k;
-    if (vox) CK(cudaMemcpyAsync(vox, g->s_cell + off, sizeof(int) * k, cudaMemcpyDeviceToHost, g->stream));
+    std::vector<float4> rec(vox ? k : 0);
+    if (vox) CK(cudaMemcpyAsync(rec.data(), g->s_rec + off, sizeof(float4) * k, cudaMemcpyDeviceToHost, g->stream));
     if (len) CK(cudaMemcpyAsync(len, g->s_len64 + off, sizeof(double) * k, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
+    for (int i = 0; vox && i < k; ++i) {
+        int rep;
+        std::memcpy(&rep, &rec[i].x, sizeof rep);
+        vox[i] = sph_cell_of_rep(rep, g->nx, g->ny);
+    }
     if (launch) *launch = ln;
     if (kind) *kind = kd;
     return RT3D_OK;

@@ -391,21 +391,21 @@ struct SphBuildParams {
     const long long *ray_base, *seg_base;  // [nangles] (pass 2)
     long long *ray_off;
     int *ray_len, *ray_angle, *ray_launch, *ray_kind, *ray_face;
-    int *cell, *crep;
+    // per segment: record (replicated index of the cell as int bits, FP32 J
+    // weight, l/2, l/2), FP64 chord and J weight (32 bytes in all)
+    float4 *rec;
     double *len64, *cw64;
-    float *len32, *cw32;
-    uint64_t *win;
     int *err;
 };
 
 struct SphFsParams {
     long long nrays;
     int N;
+    int nr, nt, np;                // grid (cells decoded from the records' indices)
     const long long *ray_off;
     const int *ray_len, *ray_kind, *ray_face;
-    const int *cell, *crep;
-    const void *len, *cw;
-    const uint64_t *win;
+    const float4 *rec;             // per segment (replicated index bits, J weight, l/2, l/2)
+    const double *len64, *cw64;    // per segment FP64 chord and J weight
     const void *chiS;              // replicated packed (chi, S)
     double *J, *lstar;
     const double *core_face;       // nullable [np][nt]
@@ -416,14 +416,16 @@ struct SphFsParams {
 cudaError_t launch_sph_build(const SphBuildParams &p, cudaStream_t s);
 cudaError_t launch_sph_fs(const SphFsParams &p, bool fp64, bool parabolic, bool lstar,
                           cudaStream_t s);
-// FP32 formal solution without Lambda* over per-segment records, one ray per
-// thread in the builder's order, into the replicated FP64 Jrep (zero on
+// FP32 formal solution without Lambda* over the per-segment records, one ray
+// per thread in the builder's order, into the replicated FP64 Jrep (zero on
 // entry; fold afterwards)
-cudaError_t launch_sph_fs_fast(const SphFsParams &p, const float4 *rec, double *Jrep,
-                               bool parabolic, cudaStream_t s);
-// per-segment records (replicated index bits, J weight, l/2, l/2)
-cudaError_t launch_sph_rec(long long nseg, const int *crep, const double *len64, const double *cw64,
-                           float4 *rec, cudaStream_t s);
+cudaError_t launch_sph_fs_fast(const SphFsParams &p, double *Jrep, bool parabolic,
+                               cudaStream_t s);
+// the cell (r + nr (t + nt p)) of a replicated index r + 2 nr (t + 2 nt p)
+__host__ __device__ inline int sph_cell_of_rep(int rep, int nr, int nt) {
+    const int q = rep / (2 * nr), p = q / (2 * nt);
+    return (rep - q * 2 * nr) + nr * ((q - p * 2 * nt) + nt * p);
+}
 
 // Streaming multiprocessors of the current device (queried once per device
 // with cudaDeviceGetAttribute), for launches capped at a multiple of them.

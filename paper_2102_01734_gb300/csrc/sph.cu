@@ -46,123 +46,6 @@ __device__ int sph_cell(const SphTables &T, double p0, double p1, double p2) {
     return ir + T.nr * (it + T.nt * ip);
 }
 
-__device__ void heapsort(double *a, int n) {
-    for (int start = n / 2 - 1; start >= 0; --start) {
-        int root = start;
-        while (2 * root + 1 < n) {
-            int child = 2 * root + 1;
-            if (child + 1 < n && a[child] < a[child + 1]) ++child;
-            if (a[root] < a[child]) {
-                const double t = a[root];
-                a[root] = a[child];
-                a[child] = t;
-                root = child;
-            } else {
-                break;
-            }
-        }
-    }
-    for (int end = n - 1; end > 0; --end) {
-        const double t = a[0];
-        a[0] = a[end];
-        a[end] = t;
-        int root = 0;
-        while (2 * root + 1 < end) {
-            int child = 2 * root + 1;
-            if (child + 1 < end && a[child] < a[child + 1]) ++child;
-            if (a[root] < a[child]) {
-                const double u = a[root];
-                a[root] = a[child];
-                a[child] = u;
-                root = child;
-            } else {
-                break;
-            }
-        }
-    }
-}
-
-// Crossing parameters of the line P + t d strictly inside (t0, t1), sorted
-// and merged, with t0 and t1 at the ends; returns the number of parameters.
-// entry: 0 outer sphere, 1 core sphere.
-__device__ int sph_params(const SphTables &T, const double *P, const double *d, double *ts,
-                          int *entry, double *pin) {
-    const double b = da(da(dm(P[0], d[0]), dm(P[1], d[1])), dm(P[2], d[2]));
-    const double P2 = da(da(dm(P[0], P[0]), dm(P[1], P[1])), dm(P[2], P[2]));
-    const double disc = ds(dm(b, b), ds(P2, T.re2[T.nr]));
-    const double sq = __dsqrt_rn(disc);
-    double t0 = ds(-b, sq), t1 = da(-b, sq);
-    *entry = 0;
-    const double dc = ds(dm(b, b), ds(P2, T.re2[0]));
-    if (dc > 0.0) {
-        const double sc = __dsqrt_rn(dc);
-        const double a = ds(-b, sc), c = da(-b, sc);
-        if (c <= 0.0 && c > t0) {
-            t0 = c;
-            *entry = 1;
-        }
-        if (a >= 0.0 && a < t1) t1 = a;
-    }
-    int n = 1;  // ts[0] = t0 later
-    for (int i = 1; i < T.nr; ++i) {
-        const double di = ds(dm(b, b), ds(P2, T.re2[i]));
-        if (!(di > 0.0)) continue;
-        const double s = __dsqrt_rn(di);
-        const double r1 = ds(-b, s), r2 = da(-b, s);
-        if (r1 > t0 && r1 < t1) ts[n++] = r1;
-        if (r2 > t0 && r2 < t1) ts[n++] = r2;
-    }
-    for (int j = 1; j < T.nt; ++j) {
-        if (2 * j == T.nt) {
-            if (d[2] != 0.0) {
-                const double t = dd(-P[2], d[2]);
-                if (t > t0 && t < t1) ts[n++] = t;
-            }
-            continue;
-        }
-        const double c2 = dm(T.ct[j], T.ct[j]);
-        const double A = ds(dm(d[2], d[2]), c2);
-        const double Bh = ds(dm(P[2], d[2]), dm(c2, b));
-        const double C = ds(dm(P[2], P[2]), dm(c2, P2));
-        double roots[2];
-        int nr_ = 0;
-        if (A == 0.0) {
-            if (Bh != 0.0) roots[nr_++] = dd(-C, dm(2.0, Bh));
-        } else {
-            const double dq = ds(dm(Bh, Bh), dm(A, C));
-            if (dq > 0.0) {
-                const double s = __dsqrt_rn(dq);
-                roots[nr_++] = dd(ds(-Bh, s), A);
-                roots[nr_++] = dd(da(-Bh, s), A);
-            }
-        }
-        for (int q = 0; q < nr_; ++q) {
-            const double t = roots[q];
-            if (!(t > t0 && t < t1)) continue;
-            const double z = da(P[2], dm(t, d[2]));
-            if (dm(z, T.ct[j]) > 0.0) ts[n++] = t;
-        }
-    }
-    for (int k = 0; k < T.np; ++k) {
-        const double den = ds(dm(T.cpe[k], d[1]), dm(T.spe[k], d[0]));
-        if (den == 0.0) continue;
-        const double t = dd(ds(dm(T.spe[k], P[0]), dm(T.cpe[k], P[1])), den);
-        if (!(t > t0 && t < t1)) continue;
-        const double x = da(P[0], dm(t, d[0])), y = da(P[1], dm(t, d[1]));
-        if (da(dm(T.cpe[k], x), dm(T.spe[k], y)) > 0.0) ts[n++] = t;
-    }
-    heapsort(ts + 1, n - 1);
-    ts[0] = t0;
-    int m = 1;
-    for (int i = 1; i < n; ++i)
-        if (ts[i] != ts[m - 1]) ts[m++] = ts[i];
-    if (t1 != ts[m - 1]) ts[m++] = t1;
-    pin[0] = da(P[0], dm(t0, d[0]));
-    pin[1] = da(P[1], dm(t0, d[1]));
-    pin[2] = da(P[2], dm(t0, d[2]));
-    return m;
-}
-
 __device__ __forceinline__ int nb_code_sph(int nr, int nt, int np, int a, int b) {
     const int ra = a % nr, ta = (a / nr) % nt, pa = a / (nr * nt);
     const int rb = b % nr, tb = (b / nr) % nt, pb = b / (nr * nt);
@@ -232,7 +115,7 @@ __global__ void __launch_bounds__(32) sph_build_kernel(SphBuildParams p, int npo
         const int ir = v % T.nr, it = (v / T.nr) % T.nt, ip = v / (T.nr * T.nt);
         const double P[3] = {dm(dm(T.rc[ir], T.stc[it]), T.cpc[ip]),
                              dm(dm(T.rc[ir], T.stc[it]), T.spc[ip]), dm(T.rc[ir], T.ctc[it])};
-        // ends of the line (as in sph_params)
+        // ends of the line: entry through the outer sphere, or the core sphere
         const double b = da(da(dm(P[0], d[0]), dm(P[1], d[1])), dm(P[2], d[2]));
         const double P2 = da(da(dm(P[0], P[0]), dm(P[1], P[1])), dm(P[2], P[2]));
         const double disc = ds(dm(b, b), ds(P2, T.re2[T.nr]));
@@ -388,28 +271,25 @@ __global__ void __launch_bounds__(32) sph_build_kernel(SphBuildParams p, int npo
             for (int k = lane; k < K; k += 32) {
                 const long long sidx = seg + k;
                 const int c = cells[k];
-                p.cell[sidx] = c;
                 const int cr = c % T.nr, ct = (c / T.nr) % T.nt, cp = c / (T.nr * T.nt);
-                p.crep[sidx] = (int)rep_index(cr, ct, cp, T.nr, T.nt);
                 const double l = ds(ts[k + 1], ts[k]);
+                const float lh = (float)(0.5 * l);
+                // the J weight's slot holds the cell until the weights are known
+                p.rec[sidx] = make_float4(__int_as_float((int)rep_index(cr, ct, cp, T.nr, T.nt)),
+                                          __int_as_float(c), lh, lh);
                 p.len64[sidx] = l;
-                p.len32[sidx] = (float)l;
-                // Lambda* window of the segment
+                // the Lambda* window of the segment (the run of points ending at
+                // k + 1 in the 3^3 neighbourhood of its cell) must fit the nine
+                // slots of the kernels that build Lambda*, which find it again
+                // from the cells
                 const int jend = (k + 1 < K) ? k + 1 : k;
-                uint64_t wc = 0;
-                for (int r = 0; r < kWin; ++r) wc |= (uint64_t)kWinNone << (5 * r);
                 for (int j = jend; j >= 0; --j) {
-                    const int dcode = nb_code_sph(T.nr, T.nt, T.np, cells[j], c);
-                    if (dcode < 0) break;
-                    const int r = j - k + 7;
-                    if (r < 0) {
+                    if (nb_code_sph(T.nr, T.nt, T.np, cells[j], c) < 0) break;
+                    if (j - k + 7 < 0) {
                         atomicCAS(p.err, 0, 3);
                         break;
                     }
-                    wc &= ~((uint64_t)31 << (5 * r));
-                    wc |= (uint64_t)dcode << (5 * r);
                 }
-                p.win[sidx] = wc;
             }
             if (lane == 0) {
                 p.ray_off[ray] = seg;
@@ -446,15 +326,15 @@ __global__ void __launch_bounds__(32) sph_build_kernel(SphBuildParams p, int npo
     for (int c = lane; c < N; c += 32) den[c] = 0.0;
     __syncwarp();
     for (long long sg = seg0; sg < seg; ++sg) {
-        const int c = p.cell[sg];
+        const int c = __float_as_int(p.rec[sg].y);
         if ((c & 31) == lane) den[c] += p.len64[sg];
     }
     __syncwarp();
     const double w = p.wt[o];
     for (long long sg = seg0 + lane; sg < seg; sg += 32) {
-        const double c = w * (p.len64[sg] / den[p.cell[sg]]);
+        const double c = w * (p.len64[sg] / den[__float_as_int(p.rec[sg].y)]);
         p.cw64[sg] = c;
-        p.cw32[sg] = (float)c;
+        p.rec[sg].y = (float)c;
     }
     for (int c = lane; c < N; c += 32)
         if (!(den[c] > 0.0)) atomicCAS(p.err, 0, 5);
@@ -531,20 +411,51 @@ template <typename R> __device__ __forceinline__ R clamp01s(R x) {
 __device__ __forceinline__ float divs(float x, float y) { return __fdividef(x, y); }
 __device__ __forceinline__ double divs(double x, double y) { return x / y; }
 
-// One thread per characteristic of the cache (all angles flattened).
+// Lambda* neighbour code (dr+1) + 3 (dt+1) + 9 (dp+1) of cell a relative to
+// cell b from their (r, theta, phi) indices (periodic in phi), -1 outside the
+// 3^3 neighbourhood (as nb_code_sph).
+__device__ __forceinline__ int nb_code_rtp(int ra, int ta, int pa, int rb, int tb, int pb, int np) {
+    const int dr = ra - rb, dt = ta - tb;
+    int dp = pa - pb;
+    if (dp < 0) dp += np;
+    if (dp == np - 1) dp = -1;
+    else if (dp > 1) return -1;
+    if (dr < -1 || dr > 1 || dt < -1 || dt > 1) return -1;
+    return (dr + 1) + 3 * (dt + 1) + 9 * (dp + 1);
+}
+
+__device__ __forceinline__ double red_value_s(float x) { return widen_f32(x); }
+__device__ __forceinline__ double red_value_s(double x) { return x; }
+
+// One thread per characteristic of the cache (all angles flattened). Per
+// segment it reads the record (cell index, FP32 J weight and half chord) and,
+// in FP64, the FP64 chord and J weight. With Lambda* the cells of the points
+// k-7 .. k+1 ride along in registers and the passage window of point k (the
+// run of points ending at k+1 inside the 3^3 neighbourhood of its cell, as
+// the oracle defines it) is found from them.
 template <typename R, bool PARAB, bool LSTAR>
 __global__ void __launch_bounds__(128) sph_fs_kernel(SphFsParams p) {
     using R2 = typename V2s<R>::T;
+    constexpr bool F64 = sizeof(R) == 8;
     const long long ray = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (ray >= p.nrays) return;
     const long long s0 = p.ray_off[ray];
     const int K = p.ray_len[ray];
     const int kind = p.ray_kind[ray];
     const R2 *__restrict__ chiS = static_cast<const R2 *>(p.chiS);
-    const R *__restrict__ len = static_cast<const R *>(p.len) + s0;
-    const R *__restrict__ cw = static_cast<const R *>(p.cw) + s0;
-    const int *__restrict__ cell = p.cell + s0;
-    const int *__restrict__ crep = p.crep + s0;
+    const float4 *__restrict__ rec = p.rec + s0;
+    const double *__restrict__ l64 = p.len64 + s0;
+    const double *__restrict__ c64 = p.cw64 + s0;
+    // chord of segment k and its J weight in the kernel's precision (2 (l/2)
+    // in FP32 is the FP32 chord exactly)
+    auto seg_len = [&](int k) -> R {
+        if constexpr (F64) return l64[k];
+        else return 2.0f * __ldg(&rec[k].z);
+    };
+    auto seg_cw = [&](int k) -> R {
+        if constexpr (F64) return c64[k];
+        else return __ldg(&rec[k].y);
+    };
     double I0 = 0.0;
     if (!p.homogeneous) {
         if (kind == 2) I0 = p.core_face ? p.core_face[p.ray_face[ray]] : p.I_core;
@@ -552,24 +463,41 @@ __global__ void __launch_bounds__(128) sph_fs_kernel(SphFsParams p) {
         else I0 = p.I_out;
     }
     R I = (R)I0;
-    int v = cell[0];
-    R2 cs = chiS[crep[0]];
-    R chil_c = cs.x * len[0], chil_p = R(0);
+    const int nr2 = 2 * p.nr, nt2 = 2 * p.nt;
+    int rep = __float_as_int(__ldg(&rec[0].x));
+    int v = sph_cell_of_rep(rep, p.nr, p.nt);
+    R2 cs = chiS[rep];
+    R chil_c = cs.x * seg_len(0), chil_p = R(0);
     R S_c = cs.y, S_p = cs.y;
     R ring[kWin];
+    // (r, theta, phi) of points k-8 .. k (slot 8 = the current point) before
+    // the shift of step k; -8 marks no point
+    int wr[kWin], wt[kWin], wp[kWin];
 #pragma unroll
-    for (int i = 0; i < kWin; ++i) ring[i] = R(0);
+    for (int i = 0; i < kWin; ++i) {
+        ring[i] = R(0);
+        wr[i] = -8;
+        wt[i] = -8;
+        wp[i] = -8;
+    }
+    if (LSTAR) {
+        const int q = rep / nr2, pc = q / nt2;
+        wr[kWin - 1] = rep - q * nr2;
+        wt[kWin - 1] = q - pc * nt2;
+        wp[kWin - 1] = pc;
+    }
     for (int k = 0; k < K; ++k) {
         const R u = R(0.5) * (chil_p + chil_c);
         R E, a0, a, d;
         ifn(u, E, a0, a, d);
         const bool has_next = k + 1 < K;
-        int vn = v;
+        int vn = v, repn = rep;
         R chil_n = R(0), S_n = S_c;
         if (has_next) {
-            vn = cell[k + 1];
-            const R2 c2 = chiS[crep[k + 1]];
-            chil_n = c2.x * len[k + 1];
+            repn = __float_as_int(__ldg(&rec[k + 1].x));
+            vn = sph_cell_of_rep(repn, p.nr, p.nt);
+            const R2 c2 = chiS[repn];
+            chil_n = c2.x * seg_len(k + 1);
             S_n = c2.y;
         }
         R al = a0, bg = a, ga = R(0);
@@ -587,20 +515,41 @@ __global__ void __launch_bounds__(128) sph_fs_kernel(SphFsParams p) {
             }
         }
         I = E * I + al * S_p + bg * S_c + ga * (S_n - S_c);
-        const R c = cw[k];
-        atomicAdd(p.J + v, (double)(c * I));
+        const R c = seg_cw(k);
+        atomicAdd(p.J + v, red_value_s(c * I));
         if (LSTAR) {
+            // cells of points k-7 .. k+1 in slots 0 .. 8
+#pragma unroll
+            for (int i = 0; i < kWin - 1; ++i) {
+                wr[i] = wr[i + 1];
+                wt[i] = wt[i + 1];
+                wp[i] = wp[i + 1];
+            }
+            if (has_next) {
+                const int q = repn / nr2, pc = q / nt2;
+                wr[kWin - 1] = repn - q * nr2;
+                wt[kWin - 1] = q - pc * nt2;
+                wp[kWin - 1] = pc;
+            } else {
+                wr[kWin - 1] = -8;
+            }
+            // ring[i] = dI_k / dS_{k-7+i}
 #pragma unroll
             for (int i = 0; i < kWin - 1; ++i) ring[i] = E * ring[i + 1];
             if (k == 0) ring[7] += al;
             else ring[6] += al;
             ring[7] += bg - ga;
             ring[8] = ga;
-            const uint64_t wc = p.win[s0 + k];
+            // the window: from point k+1 (or k at the last point) backwards
+            // while the points stay in the neighbourhood of point k's cell
+            bool run = true;
 #pragma unroll
-            for (int i = 0; i < kWin; ++i) {
-                const unsigned dc = (unsigned)(wc >> (5 * i)) & 31u;
-                if (dc != kWinNone) atomicAdd(p.lstar + (long long)dc * p.N + v, (double)(c * ring[i]));
+            for (int i = kWin - 1; i >= 0; --i) {
+                if (i == kWin - 1 && !has_next) continue;  // the last point: the run ends at k
+                const int dc = run ? nb_code_rtp(wr[i], wt[i], wp[i], wr[7], wt[7], wp[7], p.np)
+                                   : -1;
+                run = dc >= 0;
+                if (run) atomicAdd(p.lstar + (long long)dc * p.N + v, red_value_s(c * ring[i]));
             }
         }
         chil_p = chil_c;
@@ -608,7 +557,12 @@ __global__ void __launch_bounds__(128) sph_fs_kernel(SphFsParams p) {
         S_p = S_c;
         S_c = S_n;
         v = vn;
+        rep = repn;
     }
+    // the widening does not carry a non-finite value: a non-finite intensity
+    // (it persists along the recurrence) makes J of the last point NaN
+    if (!F64 && !(fabs((double)I) <= 1.79769313486231570e308))
+        atomicAdd(p.J + v, __longlong_as_double(0x7ff8000000000000LL));
 }
 
 template <typename R, bool PARAB, bool LSTAR>
@@ -645,15 +599,14 @@ namespace {
 // counts but scatters a warp over the shell); contributions reduced in FP64
 // at the replicated index (folded afterwards).
 template <bool PARAB>
-__global__ void __launch_bounds__(128) sph_fs_fast_kernel(SphFsParams p, const float4 *__restrict__ rec,
-                                                          double *__restrict__ Jrep) {
+__global__ void __launch_bounds__(128) sph_fs_fast_kernel(SphFsParams p, double *__restrict__ Jrep) {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= p.nrays) return;
     const long long ray = idx;
     const long long s0 = p.ray_off[ray];
     const int K = p.ray_len[ray];
     const int kind = p.ray_kind[ray];
-    const float4 *__restrict__ rr = rec + s0;
+    const float4 *__restrict__ rr = p.rec + s0;
     const float2 *__restrict__ chiS = static_cast<const float2 *>(p.chiS);
     double I0 = 0.0;
     if (!p.homogeneous) {
@@ -675,18 +628,21 @@ __global__ void __launch_bounds__(128) sph_fs_fast_kernel(SphFsParams p, const f
     st.dS = 0.0f;
     st.ru = __fdividef(1.0f, fmaxf(st.hc, 1e-30f));
     float cwc = r0.y;
-    // the next point's record and (chi, S) are loaded one point ahead;
-    // contributions are widened by integer moves (the FP64 pipe stays free)
-    float4 rq = __ldg(rr + (K > 1 ? 1 : 0));
-    float2 cq = chiS[__float_as_int(rq.x)];
-#pragma unroll 2
-    for (int k = 1; k < K; ++k) {
-        const float4 rn = rq;
-        const float2 cn = cq;
-        rq = __ldg(rr + (k + 1 < K ? k + 1 : k));
-        cq = chiS[__float_as_int(rq.x)];
-        fast_step_c<PARAB, true, false>(st, Jrep, rn, cwc, __float_as_int(rn.x), cn);
-        cwc = rn.y;
+    // two points per trip; contributions widened by integer moves (the FP64
+    // pipe stays free). Loading a point ahead (as the Cartesian pair kernel
+    // does) was 4 % slower here: the lanes of a warp run rays of different
+    // lengths, and the extra loads cost more than the latency they hide.
+    int k = 1;
+    for (; k + 1 < K; k += 2) {
+        const float4 r1 = __ldg(rr + k), r2 = __ldg(rr + k + 1);
+        fast_step<PARAB, true, false>(st, chiS, Jrep, r1, cwc);
+        fast_step<PARAB, true, false>(st, chiS, Jrep, r2, r1.y);
+        cwc = r2.y;
+    }
+    if (k < K) {
+        const float4 r1 = __ldg(rr + k);
+        fast_step<PARAB, true, false>(st, chiS, Jrep, r1, cwc);
+        cwc = r1.y;
     }
     const IntervalE f = interval_fast(st.u, PARAB ? st.ru : __fdividef(1.0f, st.u));
     st.I = fmaf(f.a, st.dS, fmaf(f.e0, st.Sp - st.I, st.I));
@@ -695,31 +651,14 @@ __global__ void __launch_bounds__(128) sph_fs_fast_kernel(SphFsParams p, const f
         atomicAdd(Jrep + st.vc, __longlong_as_double(0x7ff8000000000000LL));
 }
 
-// per segment: (replicated index as int bits, J weight, l/2, l/2)
-__global__ void sph_rec_kernel(long long nseg, const int *crep, const double *len64,
-                               const double *cw64, float4 *rec) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nseg;
-         i += (long long)gridDim.x * blockDim.x)
-        rec[i] = make_float4(__int_as_float(crep[i]), (float)cw64[i], (float)(0.5 * len64[i]), (float)(0.5 * len64[i]));
-}
-
 }  // namespace
 
-cudaError_t launch_sph_rec(long long nseg, const int *crep, const double *len64, const double *cw64,
-                           float4 *rec, cudaStream_t s) {
-    long long b = (nseg + 255) / 256;
-    const long long cap = 16LL * device_sm_count();
-    if (b > cap) b = cap;
-    sph_rec_kernel<<<(int)(b < 1 ? 1 : b), 256, 0, s>>>(nseg, crep, len64, cw64, rec);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sph_fs_fast(const SphFsParams &p, const float4 *rec, double *Jrep,
-                               bool parabolic, cudaStream_t s) {
+cudaError_t launch_sph_fs_fast(const SphFsParams &p, double *Jrep, bool parabolic,
+                               cudaStream_t s) {
     const int threads = 128;
     const long long blocks = (p.nrays + threads - 1) / threads;
-    if (parabolic) sph_fs_fast_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(p, rec, Jrep);
-    else sph_fs_fast_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(p, rec, Jrep);
+    if (parabolic) sph_fs_fast_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(p, Jrep);
+    else sph_fs_fast_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(p, Jrep);
     return cudaGetLastError();
 }
 
