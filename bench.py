@@ -682,6 +682,10 @@ def run_spherical(args):
         g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, prec, geometry=rt3d.SPHERICAL)
         torch.cuda.synchronize()
         info = g.info()
+        free_b, _ = torch.cuda.mem_get_info()
+        print(json.dumps({"progress": f"{name} grid built", "segments": info["segments"],
+                          "device_bytes": info["device_bytes"], "free_bytes": free_b}),
+              file=sys.stderr, flush=True)
         out.setdefault("build_seconds", time.perf_counter() - t0)
         out["segments_per_fs"] = info["segments"]
         out["device_bytes"] = info["device_bytes"]

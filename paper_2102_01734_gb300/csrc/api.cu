@@ -163,10 +163,10 @@ struct rt3d_grid {
     long long *s_ray_off = nullptr;
     int *s_ray_len = nullptr, *s_ray_angle = nullptr, *s_ray_launch = nullptr;
     int *s_ray_kind = nullptr, *s_ray_face = nullptr;
-    // per segment (32 bytes): record (replicated index bits, FP32 J weight,
-    // l/2, l/2), FP64 chord and J weight
+    // per segment (24 bytes): record (replicated index bits, FP32 J weight,
+    // l/2, FP32 remainder of the FP64 J weight) and the FP64 chord
     float4 *s_rec = nullptr;
-    double *s_len64 = nullptr, *s_cw64 = nullptr;
+    double *s_len64 = nullptr;
 
     // batched-wavelength workspace (allocated for the largest n_lambda seen)
     int bl_cap = 0;
@@ -206,8 +206,12 @@ struct rt3d_grid {
         cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return fail(RT3D_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
-                        cudaGetErrorString(e));
+            size_t fr = 0, tot = 0;
+            cudaMemGetInfo(&fr, &tot);
+            cudaGetLastError();
+            return fail(RT3D_ENOMEM,
+                        "cudaMalloc of %zu bytes failed: %s (grid holds %lld bytes; %zu of %zu free)",
+                        count * sizeof(T), cudaGetErrorString(e), dev_bytes, fr, tot);
         }
         allocs.push_back(q);
         dev_bytes += (long long)(count * sizeof(T));
@@ -362,7 +366,6 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         sp.np = g->nz;
         sp.rec = g->s_rec;
         sp.len64 = g->s_len64;
-        sp.cw64 = g->s_cw64;
         sp.chiS = p.chiS;
         sp.J = g->Jfs;
         sp.lstar = p.lstar;
@@ -690,6 +693,17 @@ rt3d_status sph_build(rt3d_grid *g) {
     g->s_nseg = tsg;
     g->s_ray_base = rbase;
     g->s_nrays_angle = nrays;
+    {
+        // the cache: 28 bytes per ray, 24 per segment
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        const long long need = 28LL * tr + 24LL * tsg;
+        if ((unsigned long long)need > fr)
+            return fail(RT3D_ENOMEM,
+                        "spherical cache of %lld rays and %lld segments needs %lld bytes, %zu free "
+                        "(build scratch %lld bytes for %d angles at a time)",
+                        tr, tsg, need, fr, g->dev_bytes, chunk);
+    }
     long long *d_rbase = nullptr, *d_sbase = nullptr;
     TRY(g->alloc(&d_rbase, nO));
     TRY(g->alloc(&d_sbase, nO));
@@ -703,7 +717,6 @@ rt3d_status sph_build(rt3d_grid *g) {
     TRY(g->alloc(&g->s_ray_face, tr));
     TRY(g->alloc(&g->s_rec, tsg));
     TRY(g->alloc(&g->s_len64, tsg));
-    TRY(g->alloc(&g->s_cw64, tsg));
     bp.pass = 2;
     bp.ray_base = d_rbase;
     bp.seg_base = d_sbase;
@@ -715,7 +728,6 @@ rt3d_status sph_build(rt3d_grid *g) {
     bp.ray_face = g->s_ray_face;
     bp.rec = g->s_rec;
     bp.len64 = g->s_len64;
-    bp.cw64 = g->s_cw64;
     for (int o0 = 0; o0 < nO; o0 += chunk) {
         bp.o0 = o0;
         bp.nchunk = std::min(chunk, nO - o0);

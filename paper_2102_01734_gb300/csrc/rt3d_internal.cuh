@@ -392,9 +392,10 @@ struct SphBuildParams {
     long long *ray_off;
     int *ray_len, *ray_angle, *ray_launch, *ray_kind, *ray_face;
     // per segment: record (replicated index of the cell as int bits, FP32 J
-    // weight, l/2, l/2), FP64 chord and J weight (32 bytes in all)
+    // weight, l/2, the FP32 remainder of the FP64 J weight) and the FP64
+    // chord (24 bytes in all)
     float4 *rec;
-    double *len64, *cw64;
+    double *len64;
     int *err;
 };
 
@@ -404,8 +405,9 @@ struct SphFsParams {
     int nr, nt, np;                // grid (cells decoded from the records' indices)
     const long long *ray_off;
     const int *ray_len, *ray_kind, *ray_face;
-    const float4 *rec;             // per segment (replicated index bits, J weight, l/2, l/2)
-    const double *len64, *cw64;    // per segment FP64 chord and J weight
+    const float4 *rec;             // per segment (replicated index bits, J weight, l/2,
+                                   // remainder of the FP64 J weight)
+    const double *len64;           // per segment FP64 chord
     const void *chiS;              // replicated packed (chi, S)
     double *J, *lstar;
     const double *core_face;       // nullable [np][nt]

@@ -333,8 +333,9 @@ __global__ void __launch_bounds__(32) sph_build_kernel(SphBuildParams p, int npo
     const double w = p.wt[o];
     for (long long sg = seg0 + lane; sg < seg; sg += 32) {
         const double c = w * (p.len64[sg] / den[__float_as_int(p.rec[sg].y)]);
-        p.cw64[sg] = c;
-        p.rec[sg].y = (float)c;
+        const float hi = (float)c;
+        p.rec[sg].y = hi;                 // the FP32 kernels' weight
+        p.rec[sg].w = (float)(c - hi);   // with it, the FP64 weight to ~2^-48
     }
     for (int c = lane; c < N; c += 32)
         if (!(den[c] > 0.0)) atomicCAS(p.err, 0, 5);
@@ -428,8 +429,9 @@ __device__ __forceinline__ double red_value_s(float x) { return widen_f32(x); }
 __device__ __forceinline__ double red_value_s(double x) { return x; }
 
 // One thread per characteristic of the cache (all angles flattened). Per
-// segment it reads the record (cell index, FP32 J weight and half chord) and,
-// in FP64, the FP64 chord and J weight. With Lambda* the cells of the points
+// segment it reads the record (cell index, FP32 J weight, half chord, and
+// the weight's FP32 remainder) and, in FP64, the FP64 chord; the FP64 J
+// weight is the record's two-float sum. With Lambda* the cells of the points
 // k-7 .. k+1 ride along in registers and the passage window of point k (the
 // run of points ending at k+1 inside the 3^3 neighbourhood of its cell, as
 // the oracle defines it) is found from them.
@@ -445,7 +447,6 @@ __global__ void __launch_bounds__(128) sph_fs_kernel(SphFsParams p) {
     const R2 *__restrict__ chiS = static_cast<const R2 *>(p.chiS);
     const float4 *__restrict__ rec = p.rec + s0;
     const double *__restrict__ l64 = p.len64 + s0;
-    const double *__restrict__ c64 = p.cw64 + s0;
     // chord of segment k and its J weight in the kernel's precision (2 (l/2)
     // in FP32 is the FP32 chord exactly)
     auto seg_len = [&](int k) -> R {
@@ -453,8 +454,12 @@ __global__ void __launch_bounds__(128) sph_fs_kernel(SphFsParams p) {
         else return 2.0f * __ldg(&rec[k].z);
     };
     auto seg_cw = [&](int k) -> R {
-        if constexpr (F64) return c64[k];
-        else return __ldg(&rec[k].y);
+        if constexpr (F64) {
+            const float4 r = __ldg(&rec[k]);
+            return (double)r.y + (double)r.w;
+        } else {
+            return __ldg(&rec[k].y);
+        }
     };
     double I0 = 0.0;
     if (!p.homogeneous) {
