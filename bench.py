@@ -601,12 +601,13 @@ def run_precisions(args):
     tchi, teps, tB = d(chi), d(eps), d(B)
     tbc = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}
     n, nth, nph = cfg["n"], cfg["ntheta"], cfg["nphi"]
-    out = {"mode": "precisions", "workload": WORKLOAD, "tol": args.tol}
+    out = {"mode": "precisions", "workload": WORKLOAD, "tol": args.tol, "os_solver": args.os_solver}
     Jref = {}
     names = ["ff", "mixed"] + ([] if args.no_fp64 else ["fp64"])
     for name in names:
         prec = precision_of(name)
         g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, prec)
+        g.set_os_solver(os_solver_of(args.os_solver))  # the same OS step for every precision
         J = tB.clone()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -634,6 +635,7 @@ def run_precisions(args):
         return 0
     # plain ALI (Eq. alo iterated, no Krylov), FP64
     g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, rt3d.FP64, accel=rt3d.ACCEL_NONE)
+    g.set_os_solver(os_solver_of(args.os_solver))
     J = tB.clone()
     k = args.ali_iters
     rels = []
