@@ -270,6 +270,8 @@ def run_ours(args):
     chi, eps, B, bc = inputs.cartesian_config(n, cfg["eps"], seed=cfg["seed"] + rank)
     g = rt3d.Grid(n, cfg["ntheta"], cfg["nphi"], rt3d.PARABOLIC, precision_of(args.precision))
     g.set_os_solver(os_solver_of(args.os_solver))
+    if args.fs_shape:  # a fixed ray-bundle shape instead of the autotuner's pick
+        g.set_fs_shape(tuple(int(v) for v in args.fs_shape.split(",")))
     info = g.info()
     seg_per_fs = info["segments"]
     tchi, teps, tB = (torch.from_numpy(a).to(dev) for a in (chi, eps, B))
@@ -873,6 +875,9 @@ def main():
     ap.add_argument("--os-solver", default="gs", choices=["jacobi", "gs", "bicgstab"],
                     help="OS solver of the Krylov preconditioner (eight-colour Gauss-Seidel: "
                          "fewest formal solutions on this workload)")
+    ap.add_argument("--fs-shape", default=None,
+                    help="block,rays_per_thread,widen,branchless: fix the FP32 formal solution's "
+                         "shape (a profiler's timings would mislead the autotuner)")
     ap.add_argument("--os-solvers", action="store_true",
                     help="converged solve with each OS solver as the preconditioner")
     ap.add_argument("--kernels", action="store_true",
