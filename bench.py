@@ -854,7 +854,9 @@ def run_batched(args):
     per = st.pop("per_lambda")
     out = {"mode": "batched", "grid": [n, n, n], "angles": [16, 32], "nlambda": nl,
            "seconds": dt, "lambda_solves_per_s": int(st["converged"]) / dt,
-           "batched_phase_segments_per_s": (st["fs_lambda32"] - nl) * seg / (st["batch_ms"] / 1e3)
+           # segments of the batched iterations' formal solutions per second of the
+           # batched phase (formal solutions, sweeps, updates and retirement)
+           "batched_phase_segments_per_s": st["fs_batched"] * seg / (st["batch_ms"] / 1e3)
            if st["batch_ms"] > 0 else None,
            "stats": st, "not_converged": int(np.sum(per != 0))}
     print(json.dumps(out))

@@ -366,6 +366,9 @@ typedef struct {
                                timed: two characteristics per thread) */
     int recaptures;         /* re-captures of the iteration graph with fewer
                                wavelengths (retired ones leave the launches) */
+    long long fs_batched;   /* single-wavelength FP32 formal solutions inside the
+                               batched iterations (of fs_lambda32; batch_ms is their
+                               phase's device time) */
 } rt3d_batch_stats;
 
 /* Batched wavelengths (Sec. 4.1: the geometry is the same for all wavelength

@@ -2039,7 +2039,8 @@ rt3d_status rt3d_solve_batched(rt3d_grid *g, int nl, const double *chi, const do
     CK(cudaMemcpyAsync(iters.data(), h.iters, L * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(state.data(), h.state, L * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    for (int l = 0; l < nl; ++l) bs.fs_lambda32 += iters[l];
+    for (int l = 0; l < nl; ++l) bs.fs_batched += iters[l];
+    bs.fs_lambda32 += bs.fs_batched;
     bs.iterations = replays;
 
     // FP64 refinement and certification of every wavelength with the

@@ -96,7 +96,7 @@ class BatchStats(ctypes.Structure):
                 ("fs64_ms", _c_double), ("seconds", _c_double), ("launches", ctypes.c_longlong),
                 ("fs_lambda_ff", ctypes.c_longlong), ("fsff_ms", _c_double),
                 ("fs_shape", FsShape), ("fs_tune_ms", ctypes.c_float * FS_TUNE_SHAPES),
-                ("recaptures", _c_int)]
+                ("recaptures", _c_int), ("fs_batched", ctypes.c_longlong)]
 
     def as_dict(self):
         out = {k: getattr(self, k) for k, _ in self._fields_}
