@@ -721,8 +721,10 @@ def run_spherical(args):
 
 def run_line(args):
     """Line transfer (wavelengths of one line coupled through the
-    profile-averaged mean intensity): one converged line solve on the box
-    workload's structure at a reduced size (FP64 formal solutions)."""
+    profile-averaged mean intensity): converged line solves on the box
+    workload's structure at a reduced size, with FP64 formal solutions
+    throughout (an RT3D_FP64 grid) and in mixed precision (FP32 formal
+    solutions down to their floor, then FP64)."""
     import torch
 
     from paper_2102_01734_gb300 import build, inputs, rt3d
@@ -735,20 +737,30 @@ def run_line(args):
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
     tchi, teps, tB = d(chi), d(eps), d(B)
     tbc = {"I_top": 0.0, "I_bottom": d(bc["I_bottom"])}
-    g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, rt3d.FP64)
-    seg = g.info()["segments"]
-    J = tB.clone()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st = g.line_solve(tchi, scale, wphi, teps, tB, tbc, J, tol=args.tol, max_iter=args.max_iter)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
     out = {"mode": "line", "grid": [n] * 3, "angles": [nth, nph], "eps": args.line_eps,
-           "nlambda": args.line_lambdas, "seconds": dt, "iterations": st["iterations"],
-           "fs_lambda": st["fs_lambda"], "est_error": st["est_error"],
-           "segments_per_s": st["fs_lambda"] * seg / dt,
-           "fs_kernel_segments_per_s": st["fs_lambda"] * seg / (st["fs64_ms"] / 1e3),
-           "note": "FP64 formal solutions; the first iteration builds the averaged Lambda*"}
+           "nlambda": args.line_lambdas}
+    Js = {}
+    for name, prec in (("fp64", rt3d.FP64), ("mixed", rt3d.FP32_FS_FP64_ALI)):
+        g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, prec)
+        seg = g.info()["segments"]
+        J = tB.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.line_solve(tchi, scale, wphi, teps, tB, tbc, J, tol=args.tol,
+                          max_iter=args.max_iter)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        Js[name] = J
+        out[name] = {"seconds": dt, "iterations": st["iterations"], "fs_lambda": st["fs_lambda"],
+                     "fs_lambda32": st["fs_lambda32"], "fs64_ms": st["fs64_ms"],
+                     "fs32_ms": st["fs32_ms"], "est_error": st["est_error"],
+                     "residual64": st["residual64"],
+                     "segments_per_s": st["fs_lambda"] * seg / dt}
+        del g
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    out["max_rel_diff_mixed_vs_fp64"] = torch.max(
+        torch.abs(Js["mixed"] - Js["fp64"]) / torch.abs(Js["fp64"])).item()
+    out["note"] = "the first iteration builds the averaged Lambda*"
     print(json.dumps(out))
     return 0
 

@@ -393,15 +393,19 @@ rt3d_status rt3d_solve_batched(rt3d_grid *grid, int nlambda, const double *chi,
 
 typedef struct {
     int iterations;         /* line ALI iterations done */
-    int fs_lambda;          /* single-wavelength FP64 formal solutions done (those of
-                               the first iteration also build Lambda*) */
+    int fs_lambda;          /* single-wavelength formal solutions done, FP32 and FP64
+                               (those of the first iteration also build Lambda*) */
     int jacobi_sweeps;      /* Jacobi sweeps of all OS solves */
     double rel_change;      /* last max_v |dJbar_v| / |Jbar_v| */
     double est_error;       /* rel_change * rho / (1 - rho), rho the observed
                                contraction (-1 before the second iteration) */
     double seconds;         /* wall time of the call */
-    double fs64_ms;         /* summed device time of the formal-solution kernels */
+    double fs64_ms;         /* summed device time of the FP64 formal-solution kernels */
     long long launches;     /* kernels launched by the call */
+    int fs_lambda32;        /* of fs_lambda, those in FP32 (mixed grids) */
+    double fs32_ms;         /* summed device time of the FP32 formal-solution kernels */
+    double residual64;      /* mixed grids: max_v |Jbar_FS64(S(Jbar))_v - Jbar_v| / |Jbar_v|
+                               of the last FP64 residual (0 on an RT3D_FP64 grid) */
 } rt3d_line_stats;
 
 /* Line transfer (Sec. 2, with Eq. alisol: J weighted by the line profile
@@ -419,9 +423,18 @@ typedef struct {
  *   Jbar += dJ,
  * until the last change times rho/(1 - rho) (rho the observed contraction,
  * from the second iteration on) is below tol, or for max_iter iterations
- * (max_iter = 1: exactly one iteration, returning RT3D_ENOTCONVERGED). The
- * formal solutions run in FP64 on every grid precision (the OS coefficients
- * follow the grid's precision, which changes only the convergence rate).
+ * (max_iter = 1: exactly one iteration, returning RT3D_ENOTCONVERGED). On an
+ * RT3D_FP64 grid every formal solution is FP64. On the mixed grids the
+ * iterations use FP32 formal solutions (the first also building the band)
+ * until the estimate falls below max(tol, 1e-6) or the changes stop
+ * decreasing (the FP32 rounding floor); then, as in rt3d_solve, defect
+ * correction: an FP64 residual r = Jbar_FS64(S(Jbar)) - Jbar, a correction
+ * from the homogeneous problem (1 - Lbar(1 - eps)) delta = r by the same
+ * iteration with FP32 formal solutions (iterated to the relative accuracy that
+ * brings the estimate to tol/2, between 1e-4 and 0.1), Jbar += delta, until
+ * |delta| times its estimated relative accuracy is below tol; a last FP64
+ * residual certifies the result (residual64). The OS coefficients follow the grid's precision, which
+ * changes only the convergence rate.
  * chi, eps, B: double[N] (host or device); scale, wphi: HOST double[nlambda]
  * with scale[l] > 0 and wphi[l] >= 0, finite, sum of wphi > 0;
  * 1 <= nlambda <= 65536;

@@ -1329,18 +1329,22 @@ rt3d_status line_setup(rt3d_grid *g, const std::vector<double> &negw) {
 // FP64 formal solution added into jbar_fs with weight wphi[l] (and, when
 // build, its Lambda* band into lbar); then the OS solve with the averaged band
 // and Jbar += dJ. *rel = max |dJ| / |Jbar_new|.
-rt3d_status line_iteration(rt3d_grid *g, const FsParams &fp, const std::vector<double> &scale,
-                           bool build, double *rel, int *fs_count) {
+// Jbar_FS = sum_l wphi[l] J_FS,l of the source S = (1 - eps) x + eps B
+// (homogeneous: (1 - eps) x, with fp a homogeneous parameter set) into
+// g->jbar_fs; with build also Lbar* = sum_l wphi[l] Lambda*_l into g->lbar.
+rt3d_status line_fs(rt3d_grid *g, const FsParams &fp, bool fp64, const std::vector<double> &scale,
+                    const double *x, bool homogeneous, bool build, int *fs_count) {
     const size_t N = (size_t)g->N;
     const int n = (int)N;
+    void *chiS = fp64 ? (void *)g->chiS64 : (void *)g->chiS32;
     CK(cudaMemsetAsync(g->jbar_fs, 0, sizeof(double) * N, g->stream));
     if (build) CK(cudaMemsetAsync(g->lbar, 0, sizeof(double) * 27 * N, g->stream));
     for (int l = 0; l < (int)scale.size(); ++l) {
-        CKL(launch_pack(g->nx, g->ny, g->nz, g->chi, scale[l], g->chi /*S placeholder*/,
-                        g->chiS64, true, g->stream));
-        CKL(launch_source(g->nx, g->ny, g->nz, g->J, g->eps, g->B, g->chiS64, true, false,
-                          g->stream));
-        TRY(run_fs(g, fp, true, build));
+        CKL(launch_pack(g->nx, g->ny, g->nz, g->chi, scale[l], g->chi /*S placeholder*/, chiS,
+                        fp64, g->stream));
+        CKL(launch_source(g->nx, g->ny, g->nz, x, g->eps, homogeneous ? nullptr : g->B, chiS, fp64,
+                          homogeneous, g->stream));
+        TRY(run_fs(g, fp, fp64, build));
         ++*fs_count;
         // jbar_fs -= (-wphi[l]) Jfs
         CKL(launch_multi_axpy(n, g->jbar_fs, g->lptr, g->lcoef + l, 1, g->stream));
@@ -1349,6 +1353,14 @@ rt3d_status line_iteration(rt3d_grid *g, const FsParams &fp, const std::vector<d
                 CKL(launch_multi_axpy(n, g->lbar + (size_t)d * N, g->lptr + 1 + d, g->lcoef + l,
                                       1, g->stream));
     }
+    return RT3D_OK;
+}
+
+rt3d_status line_iteration(rt3d_grid *g, const FsParams &fp, bool fp64,
+                           const std::vector<double> &scale, bool build, double *rel,
+                           int *fs_count) {
+    const int n = (int)g->N;
+    TRY(line_fs(g, fp, fp64, scale, g->J, false, build, fs_count));
     if (build)
         CKL(launch_os_prep(g->nx, g->ny, g->nz, g->lbar, g->eps, g->a, g->a64, g->inv_diag,
                            g->stream, g->per, g->os_kind == kOsGaussSeidel, g->diag));
@@ -1800,31 +1812,95 @@ rt3d_status rt3d_line_solve(rt3d_grid *g, int nl, const double *chi, const doubl
     g->lstar_valid = false;  // the grid's Lambda* and OS coefficients become the line's
     TRY(load_problem(g, chi, eps, B));
     CK(cudaMemcpyAsync(g->J, Jbar_inout, N * sizeof(double), cudaMemcpyDefault, g->stream));
-    FsParams fp;
-    TRY(fs_params(g, bc, true, false, &fp));
+    FsParams fp64p, fp32p, fphom;
+    TRY(fs_params(g, bc, true, false, &fp64p));
+    const bool mixed = !g->fs64;
+    if (mixed) {
+        TRY(fs_params(g, bc, false, false, &fp32p));
+        TRY(fs_params(g, nullptr, false, true, &fphom));
+    }
+    // Phase 1: the line ALI, in FP32 formal solutions on the mixed grids
+    // down to their rounding floor (estimate below 1e-6, or no decrease)
     Progress prog;
     double rel = 1.0;
     bool conv = false;
     int it = 0;
+    const double switch_at = mixed ? std::max(tol, 1e-6) : tol;
     while (it < max_iter) {
-        TRY(line_iteration(g, fp, sc, it == 0, &rel, &s.fs_lambda));
+        const int before = s.fs_lambda;
+        TRY(line_iteration(g, mixed ? fp32p : fp64p, !mixed, sc, it == 0, &rel, &s.fs_lambda));
+        if (mixed) s.fs_lambda32 += s.fs_lambda - before;
         ++it;
         if (!(rel == rel)) return fail(RT3D_ENUMERIC, "NaN in the line ALI change at iteration %d", it);
         prog.add(rel);
         if (it >= 2) {
             s.est_error = prog.error_estimate();
-            if (s.est_error <= tol) {
-                conv = true;
+            if (s.est_error <= switch_at) {
+                conv = !mixed;
                 break;
             }
         }
+        if (mixed && prog.stagnated()) break;
+    }
+    s.rel_change = rel;
+    // Phase 2 (mixed grids), as the continuum solve's: defect correction with
+    // FP64 residuals r64 = Jbar_FS64(S(Jbar)) - Jbar and corrections delta
+    // from the homogeneous problem (1 - Lbar(1 - eps)) delta = r64 iterated
+    // with FP32 formal solutions; the error after Jbar += delta is about
+    // |delta| times delta's relative accuracy; a last FP64 residual
+    // certifies the returned Jbar.
+    const int n = (int)N;
+    if (mixed && it < max_iter) {
+        for (int round = 0; round < 8 && it < max_iter; ++round) {
+            TRY(line_fs(g, fp64p, true, sc, g->J, false, false, &s.fs_lambda));
+            TRY(reset_scalar(g, offsetof(OsState, res), sizeof(unsigned long long)));
+            CKL(launch_residual(n, g->jbar_fs, g->J, g->r64, g->st, g->stream));
+            double res = 0.0;
+            TRY(read_scalar_d(g, offsetof(OsState, res), &res));
+            s.residual64 = res;
+            if (!(res == res)) return fail(RT3D_ENUMERIC, "NaN in the FP64 line residual");
+            if (conv) break;  // that was the certification of the corrected Jbar
+            // delta_0 = M^-1 r64, then the ALI on delta with homogeneous FP32
+            // solutions, to the relative accuracy that brings the estimated
+            // error (about |delta| times that accuracy) to half of tol
+            TRY(os_solve_dev(g, nullptr, nullptr, g->r64, os_cap(g, 50), 1e-3));
+            CKL(launch_copy_buf(n, g->dJ_dev, g->st, g->delta, g->stream));
+            const double err_now = s.est_error > 0.0 ? s.est_error : 1.0;
+            const double target = std::min(0.1, std::max(1e-4, 0.5 * tol / err_now));
+            double drel = 1.0, dacc = 1.0;
+            Progress dprog;
+            for (int inner = 0; inner < 1000 && it < max_iter; ++inner) {
+                const int before = s.fs_lambda;
+                TRY(line_fs(g, fphom, false, sc, g->delta, true, false, &s.fs_lambda));
+                s.fs_lambda32 += s.fs_lambda - before;
+                ++it;
+                // r = Lbar_hom((1 - eps) delta) + r64 - delta
+                TRY(os_solve_dev(g, g->jbar_fs, g->delta, g->r64, os_cap(g, 50), 1e-3));
+                TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));
+                CKL(launch_ali_update(n, g->delta, g->dJ_dev, g->st, nullptr, g->stream));
+                TRY(read_scalar_d(g, offsetof(OsState, rel), &drel));
+                if (!(drel == drel)) return fail(RT3D_ENUMERIC, "NaN in the line defect correction");
+                dprog.add(drel);
+                dacc = std::max(dprog.error_estimate(), drel);
+                if (dacc <= target) break;
+                if (dprog.stagnated()) break;
+            }
+            // Jbar += delta; size of the correction relative to Jbar
+            TRY(reset_scalar(g, offsetof(OsState, rel), sizeof(unsigned long long)));
+            CKL(launch_axpy_rel(n, g->J, g->delta, g->st, g->stream));
+            double crel = 0.0;
+            TRY(read_scalar_d(g, offsetof(OsState, rel), &crel));
+            s.est_error = crel * dacc;
+            s.rel_change = crel;
+            if (s.est_error <= tol) conv = true;
+        }
     }
     s.iterations = it;
-    s.rel_change = rel;
     TRY(deliver(g, Jbar_inout, g->J, N));
     CK(cudaStreamSynchronize(g->stream));
     TRY(collect_events(g));
     s.fs64_ms = g->fs_ms[1];
+    s.fs32_ms = g->fs_ms[0] + g->fs_ms[3];
     {
         unsigned long long sw = 0;
         CK(cudaMemcpyAsync(&sw, &g->st->sweeps_total, sizeof sw, cudaMemcpyDeviceToHost, g->stream));

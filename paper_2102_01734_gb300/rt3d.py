@@ -71,7 +71,8 @@ class SolveStats(ctypes.Structure):
 class LineStats(ctypes.Structure):
     _fields_ = [("iterations", _c_int), ("fs_lambda", _c_int), ("jacobi_sweeps", _c_int),
                 ("rel_change", _c_double), ("est_error", _c_double), ("seconds", _c_double),
-                ("fs64_ms", _c_double), ("launches", ctypes.c_longlong)]
+                ("fs64_ms", _c_double), ("launches", ctypes.c_longlong),
+                ("fs_lambda32", _c_int), ("fs32_ms", _c_double), ("residual64", _c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

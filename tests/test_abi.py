@@ -59,8 +59,8 @@ def test_null_arguments_are_einval(lib):
     assert lib.rt3d_diffusion_bc(None, 1, None, None, None, None) == rt3d.EINVAL
     assert lib.rt3d_line_solve(None, 1, None, None, None, None, None, None, None, 1e-8, 10,
                                None) == rt3d.EINVAL
-    # 3 ints (+4 padding), 4 doubles, 1 long long
-    assert ctypes.sizeof(rt3d.LineStats) == 3 * 4 + 4 + 4 * 8 + 8
+    # 3 ints (+4 padding), 4 doubles, 1 long long, 1 int (+4 padding), 2 doubles
+    assert ctypes.sizeof(rt3d.LineStats) == 3 * 4 + 4 + 4 * 8 + 8 + 4 + 4 + 2 * 8
 
 
 def test_fs_tune_shapes_are_valid(lib):
