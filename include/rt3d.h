@@ -75,6 +75,32 @@ enum {
                                   FP64 residuals); Cartesian grids only */
 };
 
+/* Residency of the spherical geometry cache (Sec. 4.3: the LargeGPU mode keeps
+ * the tracking caches on the GPU; the SmallGPU mode keeps them in host memory
+ * and moves them to the GPU solid angle by solid angle). The ray tables
+ * (offset, length, kind, core face: 20 bytes per ray, plus the launch voxel and
+ * angle) stay on the device in every mode; these modes place the per-segment
+ * records (24 bytes per segment, the bulk of the cache). */
+enum {
+    RT3D_CACHE_DEVICE = 0,        /* records in device memory, one launch per
+                                     formal solution (LargeGPU) */
+    RT3D_CACHE_HOST_STREAMED = 1, /* records in pinned host memory, cut at solid
+                                     angle boundaries into chunks of at most
+                                     stream_bytes; each formal solution copies
+                                     chunk c into device buffer c % 2 on a copy
+                                     stream while the kernel integrates chunk
+                                     c - 1 (SmallGPU) */
+    RT3D_CACHE_HOST_MAPPED = 2,   /* records in pinned, mapped host memory that
+                                     the kernels read in place over the host link,
+                                     one launch per chunk */
+    RT3D_CACHE_HOST_CHORDS = 3    /* split by precision: the 16-byte records the
+                                     FP32 kernels read stay on the device, the
+                                     8-byte FP64 chords (read only by FP64 formal
+                                     solutions) live in pinned host memory and are
+                                     streamed as in RT3D_CACHE_HOST_STREAMED, in
+                                     chunks of at most stream_bytes of chords */
+};
+
 typedef struct {
     int geometry;     /* RT3D_CARTESIAN_PERIODIC_XY or RT3D_SPHERICAL */
     int n[3];         /* Cartesian: nx, ny, nz with 4 <= nx, ny <= 2047,
@@ -90,6 +116,17 @@ typedef struct {
     int accel;        /* rt3d_solve iteration: RT3D_ACCEL_NONE (plain ALI, Eq. alo
                          with Jacobi OS solves) or RT3D_ACCEL_KRYLOV */
     double r_in, r_out; /* RT3D_SPHERICAL: core and outer radius (0 < r_in < r_out) */
+    int cache;        /* RT3D_CACHE_*; anything but RT3D_CACHE_DEVICE needs
+                         RT3D_SPHERICAL (the Cartesian cache is one template
+                         per angle) */
+    long long stream_bytes; /* host modes: the largest chunk of what is streamed
+                         (24 bytes a segment; 8 in RT3D_CACHE_HOST_CHORDS), 0 for
+                         1 GiB; a solid angle is never split, so a chunk holds
+                         at least one angle. The streaming modes hold two
+                         device buffers of the largest chunk; while
+                         the grid is built, a staging buffer of up to 16 GiB (a
+                         quarter of the free memory, at least one chunk) is
+                         held as well */
 } rt3d_grid_desc;
 
 /* Boundary intensities (Sec. 3.1: I = 0 incoming at the outer boundary; the
@@ -188,6 +225,12 @@ typedef struct {
     int sm_count;             /* streaming multiprocessors of the grid's device
                                  (cudaDevAttrMultiProcessorCount), which sizes the
                                  library's capped launches */
+    int cache;                /* RT3D_CACHE_* of the grid */
+    long long host_bytes;     /* pinned host memory held by the grid (the
+                                 per-segment records, or the FP64 chords, in the
+                                 host modes) */
+    int cache_chunks;         /* host modes: chunks of solid angles a formal
+                                 solution goes through (1 on the device) */
 } rt3d_grid_info;
 
 /* Creates a grid: builds the direction set (host, FP64) and traces one
@@ -195,7 +238,13 @@ typedef struct {
  * geometry cache of Sec. 4.1). All nx*ny characteristics of an angle are
  * integer translates of that one. Returns RT3D_EINVAL for sizes outside the
  * limits above, a zero direction component along z (impossible with this
- * direction set), or a Lambda* window longer than 9 points. */
+ * direction set), or a Lambda* window longer than 9 points. A spherical grid
+ * builds its cache of long characteristics on the device (one warp per solid
+ * angle); in the host cache modes each chunk of angles is built into a device
+ * buffer and copied to pinned host memory. RT3D_ENOMEM when the device cache
+ * does not fit the free device memory, or the host records would take more
+ * than half of the host memory available to the process (MemAvailable, and
+ * the cgroup limit where one is set). */
 rt3d_status rt3d_grid_create(const rt3d_grid_desc *desc, rt3d_grid **out);
 
 /* Releases the grid and all device memory it holds. NULL is ignored. */

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "rt3d_internal.cuh"
+#include "stream.cuh"
 
 using namespace rt3d;
 
@@ -167,6 +168,25 @@ struct rt3d_grid {
     // l/2, FP32 remainder of the FP64 J weight) and the FP64 chord
     float4 *s_rec = nullptr;
     double *s_len64 = nullptr;
+    // host cache modes (RT3D_CACHE_HOST_*): the records above (only the FP64
+    // chords in the chords mode) are the device addresses of pinned, mapped
+    // host arrays; chunk c holds the angles [c_angle[c], c_angle[c+1]), their
+    // rays from c_ray[c] and segments from c_seg[c] (ray offsets relative to
+    // c_seg[c]); the streaming modes copy a chunk into slot c % 2 on cstream
+    // (c_free: the slot's last kernel is done; c_copied: the chunk is in the
+    // slot; c_fork: the formal solution began); without copies the chunks'
+    // kernels alternate between the grid's stream and cstream
+    int cache = RT3D_CACHE_DEVICE;
+    float4 *h_rec = nullptr;
+    double *h_len64 = nullptr;
+    std::vector<int> c_angle;
+    std::vector<long long> c_ray, c_seg, s_angle_chunk_seg;
+    float4 *slot_rec[2] = {nullptr, nullptr};
+    double *slot_len64[2] = {nullptr, nullptr};
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t c_fork = nullptr, c_copied[2] = {nullptr, nullptr}, c_free[2] = {nullptr, nullptr};
+    std::vector<void *> host_allocs;
+    long long host_bytes = 0;
 
     // batched-wavelength workspace (allocated for the largest n_lambda seen)
     int bl_cap = 0;
@@ -218,7 +238,49 @@ struct rt3d_grid {
         *p = static_cast<T *>(q);
         return RT3D_OK;
     }
+    // frees a device allocation of alloc() (count elements of T) before the
+    // grid is destroyed; synchronises the device (cudaFree)
+    template <typename T>
+    void release(T *&p, size_t count) {
+        if (!p) return;
+        auto it = std::find(allocs.begin(), allocs.end(), static_cast<void *>(p));
+        if (it != allocs.end()) {
+            allocs.erase(it);
+            cudaFree(p);
+            dev_bytes -= (long long)(count * sizeof(T));
+        }
+        p = nullptr;
+    }
+    // pinned, mapped host memory; *dev receives its device address
+    template <typename T>
+    rt3d_status alloc_host(T **p, T **dev, size_t count) {
+        void *q = nullptr;
+        cudaError_t e = cudaHostAlloc(&q, count * sizeof(T) + 16, cudaHostAllocMapped);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RT3D_ENOMEM, "cudaHostAlloc of %zu bytes failed: %s (grid holds %lld "
+                        "host bytes)", count * sizeof(T), cudaGetErrorString(e), host_bytes);
+        }
+        host_allocs.push_back(q);
+        host_bytes += (long long)(count * sizeof(T));
+        void *d = nullptr;
+        e = cudaHostGetDevicePointer(&d, q, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RT3D_ECUDA, "cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
+        }
+        *p = static_cast<T *>(q);
+        *dev = static_cast<T *>(d);
+        return RT3D_OK;
+    }
     ~rt3d_grid() {
+        if (cstream) cudaStreamDestroy(cstream);
+        if (c_fork) cudaEventDestroy(c_fork);
+        for (int i = 0; i < 2; ++i) {
+            if (c_copied[i]) cudaEventDestroy(c_copied[i]);
+            if (c_free[i]) cudaEventDestroy(c_free[i]);
+        }
+        for (void *p : host_allocs) cudaFreeHost(p);
         if (bstream) cudaStreamDestroy(bstream);
         if (bev0) cudaEventDestroy(bev0);
         if (bev1) cudaEventDestroy(bev1);
@@ -379,12 +441,67 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
         TRY(collect_events(g));
         CK(cudaEventRecord(g->ev0, g->stream));
-        if (sfast) CK(launch_sph_fs_fast(sp, g->Jrep, g->parab, g->stream));
-        else CK(launch_sph_fs(sp, fp64, g->parab, with_lstar, g->stream));
+        if (g->cache == RT3D_CACHE_DEVICE) {
+            if (sfast) CK(launch_sph_fs_fast(sp, g->Jrep, g->parab, g->stream));
+            else CK(launch_sph_fs(sp, fp64, g->parab, with_lstar, g->stream));
+            ++g->launches;
+        } else {
+            // host records, chunk by chunk of solid angles: the streamed mode
+            // copies chunk c into slot c % 2 on the copy stream once the
+            // kernel of chunk c - 2 has released the slot, and the kernel of
+            // chunk c waits for its copy; the mapped mode reads the chunk in
+            // place; the chords mode reads the records on the device and
+            // streams the FP64 chords, which only the FP64 kernel reads.
+            // (In the mapped and chords modes cp.len64 is never read by the
+            // FP32 kernels.)
+            const bool chords = g->cache == RT3D_CACHE_HOST_CHORDS;
+            const bool copy = g->cache == RT3D_CACHE_HOST_STREAMED || (chords && fp64);
+            // without copies the chunks' kernels alternate between the grid's
+            // stream and the second stream, so that the tail of one overlaps
+            // the next (they only add into J and Lambda*)
+            const bool alt = !copy;
+            CK(cudaEventRecord(g->c_fork, g->stream));
+            CK(cudaStreamWaitEvent(g->cstream, g->c_fork, 0));
+            const int nch = (int)g->c_angle.size() - 1;
+            for (int c = 0; c < nch; ++c) {
+                SphFsParams cp = sp;
+                const long long r0 = g->c_ray[c], s0 = g->c_seg[c], ns = g->c_seg[c + 1] - s0;
+                cp.nrays = g->c_ray[c + 1] - r0;
+                cp.ray_off = g->s_ray_off + r0;
+                cp.ray_len = g->s_ray_len + r0;
+                cp.ray_kind = g->s_ray_kind + r0;
+                cp.ray_face = g->s_ray_face + r0;
+                const int k = c & 1;
+                cp.rec = g->s_rec + s0;
+                cp.len64 = g->s_len64 + s0;
+                if (copy) {
+                    CK(cudaStreamWaitEvent(g->cstream, g->c_free[k], 0));
+                    if (!chords) {
+                        CK(cudaMemcpyAsync(g->slot_rec[k], g->h_rec + s0, sizeof(float4) * ns,
+                                           cudaMemcpyHostToDevice, g->cstream));
+                        cp.rec = g->slot_rec[k];
+                    }
+                    if (fp64)
+                        CK(cudaMemcpyAsync(g->slot_len64[k], g->h_len64 + s0, sizeof(double) * ns,
+                                           cudaMemcpyHostToDevice, g->cstream));
+                    cp.len64 = g->slot_len64[k];
+                    CK(cudaEventRecord(g->c_copied[k], g->cstream));
+                    CK(cudaStreamWaitEvent(g->stream, g->c_copied[k], 0));
+                }
+                cudaStream_t ks = alt && k ? g->cstream : g->stream;
+                if (sfast) CK(launch_sph_fs_fast(cp, g->Jrep, g->parab, ks));
+                else CK(launch_sph_fs(cp, fp64, g->parab, with_lstar, ks));
+                ++g->launches;
+                if (copy) CK(cudaEventRecord(g->c_free[k], g->stream));
+            }
+            if (alt) {  // join
+                CK(cudaEventRecord(g->c_copied[0], g->cstream));
+                CK(cudaStreamWaitEvent(g->stream, g->c_copied[0], 0));
+            }
+        }
         CK(cudaEventRecord(g->ev1, g->stream));
         g->ev_pending = fp64 ? 1 : (with_lstar ? 3 : 0);
         if (!fp64 && with_lstar) ++g->fs_lstar32;
-        ++g->launches;
         if (sfast) {
             CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
             ++g->launches;
@@ -577,9 +694,42 @@ rt3d_status alloc_work(rt3d_grid *g) {
     return RT3D_OK;
 }
 
+// Host memory this process may still take, in bytes: MemAvailable, lowered
+// to the cgroup's limit less its usage where one is set (v2, else v1); -1
+// when none of them can be read.
+long long host_memory_available() {
+    long long avail = -1;
+    if (FILE *f = std::fopen("/proc/meminfo", "r")) {
+        char line[256];
+        long long kb = 0;
+        while (std::fgets(line, sizeof line, f))
+            if (std::sscanf(line, "MemAvailable: %lld kB", &kb) == 1) avail = kb * 1024;
+        std::fclose(f);
+    }
+    auto read_ll = [](const char *path, long long *v) -> bool {
+        FILE *f = std::fopen(path, "r");
+        if (!f) return false;
+        const bool ok = std::fscanf(f, "%lld", v) == 1;  // "max" (no limit) reads as no number
+        std::fclose(f);
+        return ok;
+    };
+    long long lim = 0, used = 0;
+    if ((read_ll("/sys/fs/cgroup/memory.max", &lim) && read_ll("/sys/fs/cgroup/memory.current", &used)) ||
+        (read_ll("/sys/fs/cgroup/memory/memory.limit_in_bytes", &lim) &&
+         read_ll("/sys/fs/cgroup/memory/memory.usage_in_bytes", &used))) {
+        const long long room = std::max(0LL, lim - used);
+        if (lim < (1LL << 60)) avail = avail < 0 ? room : std::min(avail, room);
+    }
+    return avail;
+}
+
 // Spherical geometry cache: trig tables on the host (plain IEEE arithmetic
 // and libm), the ray set of every solid angle built on the device in angle
-// chunks (pass 1 counts rays and segments, pass 2 fills the tables).
+// chunks (pass 1 counts rays and segments, pass 2 fills the tables). In the
+// host cache modes pass 2 runs chunk of angles by chunk of angles (the
+// residency chunks of the formal solution) into a device buffer, with
+// segment offsets relative to the chunk, and each chunk is copied to the
+// pinned host records.
 rt3d_status sph_build(rt3d_grid *g) {
     const rt3d_grid_desc &d = g->desc;
     const int nr = g->nx, nt = g->ny, np = g->nz, nO = g->nO;
@@ -693,30 +843,113 @@ rt3d_status sph_build(rt3d_grid *g) {
     g->s_nseg = tsg;
     g->s_ray_base = rbase;
     g->s_nrays_angle = nrays;
+    // residency chunks: all angles on the device; in the host modes runs of
+    // consecutive angles whose records fit stream_bytes (at least one angle)
+    const bool host = g->cache != RT3D_CACHE_DEVICE;
+    const bool chords = g->cache == RT3D_CACHE_HOST_CHORDS;  // only the FP64 chords on the host
+    std::vector<long long> sloc(nO);  // segment base of each angle handed to pass 2
+    g->c_angle.assign(1, 0);
+    g->c_ray.assign(1, 0);
+    g->c_seg.assign(1, 0);
+    g->s_angle_chunk_seg.assign(nO, 0);
+    if (host) {
+        const long long cap = std::max(
+            1LL, (d.stream_bytes > 0 ? d.stream_bytes : (1LL << 30)) / (chords ? 8 : 24));
+        for (int o = 0; o < nO; ++o) {
+            if (sbase[o] > g->c_seg.back() && sbase[o] + nseg[o] - g->c_seg.back() > cap) {
+                g->c_angle.push_back(o);
+                g->c_ray.push_back(rbase[o]);
+                g->c_seg.push_back(sbase[o]);
+            }
+            g->s_angle_chunk_seg[o] = g->c_seg.back();
+            sloc[o] = sbase[o] - g->c_seg.back();
+        }
+    } else {
+        sloc = sbase;
+    }
+    g->c_angle.push_back(nO);
+    g->c_ray.push_back(tr);
+    g->c_seg.push_back(tsg);
+    const int nch = (int)g->c_angle.size() - 1;
+    long long maxc = 0;
+    for (int c = 0; c < nch; ++c) maxc = std::max(maxc, g->c_seg[c + 1] - g->c_seg[c]);
+    const int nslots = g->cache == RT3D_CACHE_HOST_STREAMED || chords ? 2 : 0;
     {
-        // the cache: 28 bytes per ray, 24 per segment
+        // the cache: 28 bytes per ray on the device; 24 per segment on the
+        // device, or in pinned host memory with device buffers of the largest chunk
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot));
-        const long long need = 28LL * tr + 24LL * tsg;
+        const long long need = 28LL * tr + (!host  ? 24LL * tsg
+                                            : chords ? 16LL * tsg + 8LL * (nslots + 1) * maxc
+                                                     : 24LL * (nslots + 1) * maxc);
         if ((unsigned long long)need > fr)
             return fail(RT3D_ENOMEM,
-                        "spherical cache of %lld rays and %lld segments needs %lld bytes, %zu free "
-                        "(build scratch %lld bytes for %d angles at a time)",
+                        "spherical cache of %lld rays and %lld segments needs %lld device bytes, "
+                        "%zu free (build scratch %lld bytes for %d angles at a time)",
                         tr, tsg, need, fr, g->dev_bytes, chunk);
+        if (host) {
+            const long long hneed = (chords ? 8LL : 24LL) * tsg, havail = host_memory_available();
+            if (havail >= 0 && hneed > havail / 2)
+                return fail(RT3D_ENOMEM,
+                            "host records of %lld segments need %lld bytes, more than half of "
+                            "the %lld bytes of host memory available",
+                            tsg, hneed, havail);
+        }
     }
     long long *d_rbase = nullptr, *d_sbase = nullptr;
     TRY(g->alloc(&d_rbase, nO));
     TRY(g->alloc(&d_sbase, nO));
     CK(cudaMemcpyAsync(d_rbase, rbase.data(), sizeof(long long) * nO, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_sbase, sbase.data(), sizeof(long long) * nO, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_sbase, sloc.data(), sizeof(long long) * nO, cudaMemcpyHostToDevice, s));
     TRY(g->alloc(&g->s_ray_off, tr));
     TRY(g->alloc(&g->s_ray_len, tr));
     TRY(g->alloc(&g->s_ray_angle, tr));
     TRY(g->alloc(&g->s_ray_launch, tr));
     TRY(g->alloc(&g->s_ray_kind, tr));
     TRY(g->alloc(&g->s_ray_face, tr));
-    TRY(g->alloc(&g->s_rec, tsg));
-    TRY(g->alloc(&g->s_len64, tsg));
+    // host modes: pass 2 writes groups of consecutive residency chunks into a
+    // transient staging buffer (at most 16 GiB or a quarter of the free
+    // memory, at least the largest chunk), so that its launches keep the
+    // device full, with segment offsets relative to the group; each group is
+    // copied to the host records and the ray offsets are moved to their
+    // chunk's origin at the end
+    std::vector<int> grp(1, 0);  // residency chunks [grp[i], grp[i+1]) form group i
+    float4 *stage_rec = nullptr;
+    double *stage_len64 = nullptr;
+    long long stage_seg = 0;
+    long long *d_shift = nullptr;
+    if (host) {
+        if (chords) TRY(g->alloc(&g->s_rec, tsg));
+        else TRY(g->alloc_host(&g->h_rec, &g->s_rec, tsg));
+        TRY(g->alloc_host(&g->h_len64, &g->s_len64, tsg));
+        for (int k = 0; k < nslots; ++k) {
+            if (!chords) TRY(g->alloc(&g->slot_rec[k], maxc));
+            TRY(g->alloc(&g->slot_len64[k], maxc));
+        }
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        stage_seg = std::max(maxc, std::min(tsg, std::min<long long>(16LL << 30, (long long)(fr / 4)) / 24));
+        for (int c = 0; c < nch; ++c)
+            if (g->c_seg[c + 1] - g->c_seg[grp.back()] > stage_seg) grp.push_back(c);
+        grp.push_back(nch);
+        std::vector<long long> shift(nO);
+        for (size_t i = 0; i + 1 < grp.size(); ++i)
+            for (int c = grp[i]; c < grp[i + 1]; ++c)
+                for (int o = g->c_angle[c]; o < g->c_angle[c + 1]; ++o) {
+                    sloc[o] = sbase[o] - g->c_seg[grp[i]];
+                    shift[o] = g->c_seg[c] - g->c_seg[grp[i]];
+                }
+        TRY(g->alloc(&stage_rec, stage_seg));
+        TRY(g->alloc(&stage_len64, stage_seg));
+        TRY(g->alloc(&d_shift, nO));
+        CK(cudaMemcpyAsync(d_shift, shift.data(), sizeof(long long) * nO, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_sbase, sloc.data(), sizeof(long long) * nO, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // shift and sloc leave scope before the copies run otherwise
+    } else {
+        TRY(g->alloc(&g->s_rec, tsg));
+        TRY(g->alloc(&g->s_len64, tsg));
+        grp.push_back(nch);
+    }
     bp.pass = 2;
     bp.ray_base = d_rbase;
     bp.seg_base = d_sbase;
@@ -726,13 +959,29 @@ rt3d_status sph_build(rt3d_grid *g) {
     bp.ray_launch = g->s_ray_launch;
     bp.ray_kind = g->s_ray_kind;
     bp.ray_face = g->s_ray_face;
-    bp.rec = g->s_rec;
-    bp.len64 = g->s_len64;
-    for (int o0 = 0; o0 < nO; o0 += chunk) {
-        bp.o0 = o0;
-        bp.nchunk = std::min(chunk, nO - o0);
-        CK(launch_sph_build(bp, s));
+    bp.rec = host ? stage_rec : g->s_rec;
+    bp.len64 = host ? stage_len64 : g->s_len64;
+    for (size_t i = 0; i + 1 < grp.size(); ++i) {
+        const int a0 = g->c_angle[grp[i]], a1 = g->c_angle[grp[i + 1]];
+        for (int o0 = a0; o0 < a1; o0 += chunk) {
+            bp.o0 = o0;
+            bp.nchunk = std::min(chunk, a1 - o0);
+            CK(launch_sph_build(bp, s));
+        }
+        if (host) {
+            // in stream order: the next group's build waits for this copy
+            const long long g0 = g->c_seg[grp[i]], ns = g->c_seg[grp[i + 1]] - g0;
+            if (chords)
+                CK(cudaMemcpyAsync(g->s_rec + g0, stage_rec, sizeof(float4) * ns,
+                                   cudaMemcpyDeviceToDevice, s));
+            else
+                CK(cudaMemcpyAsync(g->h_rec + g0, stage_rec, sizeof(float4) * ns,
+                                   cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(g->h_len64 + g0, stage_len64, sizeof(double) * ns,
+                               cudaMemcpyDeviceToHost, s));
+        }
     }
+    if (host) CKL(launch_rebase_ray_off(g->s_ray_off, g->s_ray_angle, d_shift, tr, s));
     CK(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (herr == 3) return fail(RT3D_EINVAL, "a Lambda* window exceeds 9 points");
@@ -741,6 +990,29 @@ rt3d_status sph_build(rt3d_grid *g) {
     g->segments = tsg;
     g->tpl.kmax = bp.ncap;
     if (tr > (long long)INT32_MAX) return fail(RT3D_EINVAL, "too many spherical rays");
+    // the build scratch (and the mapped mode's build buffer) is not needed again
+    g->release(hit, (size_t)chunk * words);
+    g->release(tbuf, (size_t)chunk * bp.ncap);
+    g->release(den, (size_t)chunk * N);
+    g->release(d_nrays, nO);
+    g->release(d_nseg, nO);
+    g->release(d_err, 1);
+    g->release(d_rbase, nO);
+    g->release(d_sbase, nO);
+    g->release(d_dir, g->dir.size());
+    g->release(d_wt, g->wt.size());
+    g->release(stage_rec, (size_t)stage_seg);
+    g->release(stage_len64, (size_t)stage_seg);
+    g->release(d_shift, nO);
+    if (host) {
+        CK(cudaStreamCreateWithFlags(&g->cstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&g->c_fork, cudaEventDisableTiming));
+        for (int k = 0; k < 2; ++k) {
+            CK(cudaEventCreateWithFlags(&g->c_copied[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&g->c_free[k], cudaEventDisableTiming));
+            CK(cudaEventRecord(g->c_free[k], s));
+        }
+    }
     return alloc_work(g);
 }
 
@@ -774,6 +1046,12 @@ rt3d_status validate_desc(const rt3d_grid_desc *d) {
     if (d->nlambda > 1) return fail(RT3D_EINVAL, "nlambda > 1 is not supported by this call");
     if (d->accel != RT3D_ACCEL_NONE && d->accel != RT3D_ACCEL_KRYLOV)
         return fail(RT3D_EINVAL, "bad accel %d", d->accel);
+    if (d->cache != RT3D_CACHE_DEVICE && d->cache != RT3D_CACHE_HOST_STREAMED &&
+        d->cache != RT3D_CACHE_HOST_MAPPED && d->cache != RT3D_CACHE_HOST_CHORDS)
+        return fail(RT3D_EINVAL, "bad cache mode %d", d->cache);
+    if (d->cache != RT3D_CACHE_DEVICE && d->geometry != RT3D_SPHERICAL)
+        return fail(RT3D_EINVAL, "a host-resident cache needs the spherical grid");
+    if (d->stream_bytes < 0) return fail(RT3D_EINVAL, "negative stream_bytes");
     return RT3D_OK;
 }
 
@@ -790,6 +1068,7 @@ rt3d_status grid_build(rt3d_grid *g) {
     g->parab = d.interp == RT3D_PARABOLIC;
     g->a64 = g->fs64;
     g->sph = d.geometry == RT3D_SPHERICAL;
+    g->cache = d.cache;
     if (g->sph) g->per = Periodic{false, false, true};
 
     // Direction set in FP64 on the host (midpoints in mu and phi, Sec. 3.1).
@@ -1415,6 +1694,9 @@ rt3d_status rt3d_grid_get_info(const rt3d_grid *g, rt3d_grid_info *info) {
     info->fs_shape.branchless = g->fs_shape.branchless;
     for (int i = 0; i < RT3D_FS_TUNE_SHAPES; ++i) info->fs_tune_ms[i] = g->fs_tune_ms[i];
     info->sm_count = device_sm_count();
+    info->cache = g->cache;
+    info->host_bytes = g->host_bytes;
+    info->cache_chunks = g->sph ? (int)g->c_angle.size() - 1 : 1;
     return RT3D_OK;
 }
 
@@ -1489,9 +1771,21 @@ rt3d_status rt3d_grid_sph_ray(const rt3d_grid *gc, int angle, int index, int *K,
     }
     *K = k;
     std::vector<float4> rec(vox ? k : 0);
-    if (vox) CK(cudaMemcpyAsync(rec.data(), g->s_rec + off, sizeof(float4) * k, cudaMemcpyDeviceToHost, g->stream));
-    if (len) CK(cudaMemcpyAsync(len, g->s_len64 + off, sizeof(double) * k, cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
+    if (g->cache != RT3D_CACHE_DEVICE) {
+        // host records (or chords); the offset is relative to the angle's chunk
+        off += g->s_angle_chunk_seg[angle];
+        if (vox && g->h_rec) std::memcpy(rec.data(), g->h_rec + off, sizeof(float4) * k);
+        if (vox && !g->h_rec) {
+            CK(cudaMemcpyAsync(rec.data(), g->s_rec + off, sizeof(float4) * k,
+                               cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+        }
+        if (len) std::memcpy(len, g->h_len64 + off, sizeof(double) * k);
+    } else {
+        if (vox) CK(cudaMemcpyAsync(rec.data(), g->s_rec + off, sizeof(float4) * k, cudaMemcpyDeviceToHost, g->stream));
+        if (len) CK(cudaMemcpyAsync(len, g->s_len64 + off, sizeof(double) * k, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+    }
     for (int i = 0; vox && i < k; ++i) {
         int rep;
         std::memcpy(&rep, &rec[i].x, sizeof rep);

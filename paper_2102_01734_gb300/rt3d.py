@@ -35,6 +35,7 @@ LINEAR, PARABOLIC = 0, 1
 FP64, FP32_FS_FP64_ALI, FP32_FS_FF_REFINE = 0, 1, 2
 ACCEL_NONE, ACCEL_KRYLOV = 0, 1
 OS_JACOBI, OS_GAUSS_SEIDEL, OS_BICGSTAB = 0, 1, 2
+CACHE_DEVICE, CACHE_HOST_STREAMED, CACHE_HOST_MAPPED, CACHE_HOST_CHORDS = 0, 1, 2, 3
 
 _c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 
@@ -43,7 +44,7 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("geometry", _c_int), ("n", _c_int * 3), ("ntheta", _c_int), ("nphi", _c_int),
                 ("interp", _c_int), ("precision", _c_int), ("nlambda", _c_int),
                 ("cuda_stream", _vp), ("accel", _c_int), ("r_in", _c_double),
-                ("r_out", _c_double)]
+                ("r_out", _c_double), ("cache", _c_int), ("stream_bytes", ctypes.c_longlong)]
 
 
 class BC(ctypes.Structure):
@@ -111,7 +112,8 @@ class BatchStats(ctypes.Structure):
 class GridInfo(ctypes.Structure):
     _fields_ = [("nangles", _c_int), ("kmax", _c_int), ("segments", ctypes.c_longlong),
                 ("device_bytes", ctypes.c_longlong), ("fs_shape", FsShape),
-                ("fs_tune_ms", ctypes.c_float * FS_TUNE_SHAPES), ("sm_count", _c_int)]
+                ("fs_tune_ms", ctypes.c_float * FS_TUNE_SHAPES), ("sm_count", _c_int),
+                ("cache", _c_int), ("host_bytes", ctypes.c_longlong), ("cache_chunks", _c_int)]
 
 
 class RT3DError(RuntimeError):
@@ -250,7 +252,8 @@ def _stream_handle(stream):
 # ------------------------------------------------------------- the C ABI
 def grid_create(n, ntheta: int, nphi: int, interp: int = LINEAR, precision: int = FP64,
                 stream=None, geometry: int = CARTESIAN_PERIODIC_XY, accel: int = ACCEL_KRYLOV,
-                r_in: float = 1.0, r_out: float = 1.3):
+                r_in: float = 1.0, r_out: float = 1.3, cache: int = CACHE_DEVICE,
+                stream_bytes: int = 0):
     lib = load()
     if np.isscalar(n):
         n = (int(n),) * 3
@@ -262,6 +265,7 @@ def grid_create(n, ntheta: int, nphi: int, interp: int = LINEAR, precision: int 
     d.cuda_stream = _stream_handle(stream)
     d.accel = int(accel)
     d.r_in, d.r_out = float(r_in), float(r_out)
+    d.cache, d.stream_bytes = int(cache), int(stream_bytes)
     h = _vp()
     _check(lib.rt3d_grid_create(ctypes.byref(d), ctypes.byref(h)))
     return h
@@ -453,14 +457,16 @@ class Grid:
     """Owning wrapper of an rt3d_grid handle."""
 
     def __init__(self, n, ntheta, nphi, interp=LINEAR, precision=FP64, stream=None,
-                 accel=ACCEL_KRYLOV, geometry=CARTESIAN_PERIODIC_XY, r_in=1.0, r_out=1.3):
+                 accel=ACCEL_KRYLOV, geometry=CARTESIAN_PERIODIC_XY, r_in=1.0, r_out=1.3,
+                 cache=CACHE_DEVICE, stream_bytes=0):
         if np.isscalar(n):
             n = (int(n),) * 3
         self.n = tuple(int(v) for v in n)
         self.shape = (self.n[2], self.n[1], self.n[0])
         self.N = self.n[0] * self.n[1] * self.n[2]
         self.handle = grid_create(n, ntheta, nphi, interp, precision, stream, geometry=geometry,
-                                  accel=accel, r_in=r_in, r_out=r_out)
+                                  accel=accel, r_in=r_in, r_out=r_out, cache=cache,
+                                  stream_bytes=stream_bytes)
 
     def sph_ray(self, angle, index, cap=4096):
         return grid_sph_ray(self.handle, angle, index, cap)

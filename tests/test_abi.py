@@ -42,6 +42,21 @@ def test_bad_descriptor_is_einval(lib, n, nth, nph, interp, prec):
     assert rt3d.last_error()
 
 
+@pytest.mark.parametrize("geometry,cache,stream_bytes", [
+    (rt3d.CARTESIAN_PERIODIC_XY, rt3d.CACHE_HOST_STREAMED, 0),  # host cache: spherical only
+    (rt3d.CARTESIAN_PERIODIC_XY, rt3d.CACHE_HOST_MAPPED, 0),
+    (rt3d.CARTESIAN_PERIODIC_XY, rt3d.CACHE_HOST_CHORDS, 0),
+    (rt3d.SPHERICAL, 4, 0),                                     # no such mode
+    (rt3d.SPHERICAL, rt3d.CACHE_HOST_STREAMED, -1),             # negative chunk size
+])
+def test_bad_cache_mode_is_einval(lib, geometry, cache, stream_bytes):
+    with pytest.raises(rt3d.RT3DError) as ei:
+        rt3d.grid_create((8, 6, 8), 2, 4, stream=0, geometry=geometry, cache=cache,
+                         stream_bytes=stream_bytes)
+    assert ei.value.status == rt3d.EINVAL
+    assert "cache" in rt3d.last_error() or "stream_bytes" in rt3d.last_error()
+
+
 def test_null_arguments_are_einval(lib):
     assert lib.rt3d_grid_create(None, None) == rt3d.EINVAL
     assert lib.rt3d_formal_solution(None, None, None, None, None, None) == rt3d.EINVAL
@@ -52,7 +67,8 @@ def test_null_arguments_are_einval(lib):
     assert ctypes.sizeof(st) == (4 * 4 + 6 * 8 + 8 + 8 + 8 + 4 + 2 * 16 * 4 + 4 + 2 * 16 * 8
                                  + 4 + 4 + 8)
     assert lib.rt3d_formal_solution_ff(None, None, None, None, None) == rt3d.EINVAL
-    assert ctypes.sizeof(rt3d.GridInfo) == 2 * 4 + 2 * 8 + 4 * 4 + 8 * 4 + 4 + 4  # + sm_count, padding
+    # + sm_count, cache, host_bytes, cache_chunks (+4 padding)
+    assert ctypes.sizeof(rt3d.GridInfo) == 2 * 4 + 2 * 8 + 4 * 4 + 8 * 4 + 4 + 4 + 8 + 4 + 4
     assert lib.rt3d_grid_set_fs_shape(None, None) == rt3d.EINVAL
     assert lib.rt3d_grid_invalidate_lstar(None) == rt3d.EINVAL
     assert lib.rt3d_grid_set_os_solver(None, rt3d.OS_JACOBI) == rt3d.EINVAL

@@ -2,6 +2,7 @@
 boundary-condition struct, and the argument checks that happen before any
 device work."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -52,9 +53,44 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(rt3d.BC) == 6 * 8
     assert rt3d.BC.I_bottom_grad.offset == 5 * 8
     # rt3d_grid_desc: geometry, n[3], ntheta, nphi, interp, precision,
-    # nlambda (9 ints, +4 padding), stream pointer, accel (+4), r_in, r_out
-    assert ctypes.sizeof(rt3d.GridDesc) == 9 * 4 + 4 + 8 + 4 + 4 + 2 * 8
+    # nlambda (9 ints, +4 padding), stream pointer, accel (+4), r_in, r_out,
+    # cache (+4), stream_bytes
+    assert ctypes.sizeof(rt3d.GridDesc) == 9 * 4 + 4 + 8 + 4 + 4 + 2 * 8 + 4 + 4 + 8
     assert rt3d.FS_TUNE_SHAPES == 8
+
+
+STRUCTS = {"GridDesc": "rt3d_grid_desc", "BC": "rt3d_bc", "SolveStats": "rt3d_solve_stats",
+           "FsShape": "rt3d_fs_shape", "GridInfo": "rt3d_grid_info",
+           "BatchStats": "rt3d_batch_stats", "LineStats": "rt3d_line_stats"}
+
+
+def test_every_struct_matches_the_compiled_header(tmp_path):
+    """Size and the offset of every field of each ctypes struct against the
+    C compiler's layout of include/rt3d.h (gcc on this host)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rt3d.h"', "int main(void) {"]
+    for py, c in STRUCTS.items():
+        lines.append(f'printf("{py} size %zu\\n", sizeof({c}));')
+        for name, _ in getattr(rt3d, py)._fields_:
+            lines.append(f'printf("{py} {name} %zu\\n", offsetof({c}, {name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(rt3d.HEADER), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    seen = 0
+    for line in out.splitlines():
+        py, key, val = line.split()
+        cls = getattr(rt3d, py)
+        want = ctypes.sizeof(cls) if key == "size" else getattr(cls, key).offset
+        assert int(val) == want, (py, key, int(val), want)
+        seen += 1
+    assert seen == sum(1 + len(getattr(rt3d, py)._fields_) for py in STRUCTS)
 
 
 def test_line_solve_checks_lengths_before_the_library(lib):
