@@ -70,6 +70,7 @@ FS_KERNEL = {1: "fs_fast_kernel", 2: "fs_pair_kernel", 4: "fs_quad_kernel"}
 # The FP32 formal-solution kernel's sources: the DRAM traffic recorded in
 # its profile summary applies only while they are unchanged.
 FS_SOURCES = ("paper_2102_01734_gb300/csrc/fs.cu", "paper_2102_01734_gb300/csrc/fs_step.cuh",
+              "paper_2102_01734_gb300/csrc/fs64_step.cuh",
               "paper_2102_01734_gb300/csrc/rt3d_internal.cuh")
 FS_PROFILE = "profiles/fs_pair_kernel_box129_field.md"
 FS_PROFILE_KERNEL = "fs_pair_kernel"

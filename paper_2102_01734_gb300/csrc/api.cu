@@ -436,14 +436,20 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         sp.I_out = base.I_top;
         sp.I_irr = base.I_irr;
         sp.homogeneous = base.homogeneous;
-        const bool sfast = !fp64 && !with_lstar;
+        // without Lambda*: the record kernels (FP32 or FP64) into the
+        // replicated Jrep, folded after
+        const bool sfast = !with_lstar;
         if (!sfast) CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
         if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
         TRY(collect_events(g));
         CK(cudaEventRecord(g->ev0, g->stream));
+        auto launch = [&](const SphFsParams &q, cudaStream_t ks) -> cudaError_t {
+            if (!sfast) return launch_sph_fs(q, fp64, g->parab, with_lstar, ks);
+            return fp64 ? launch_sph_fs64_fast(q, g->Jrep, g->parab, ks)
+                        : launch_sph_fs_fast(q, g->Jrep, g->parab, ks);
+        };
         if (g->cache == RT3D_CACHE_DEVICE) {
-            if (sfast) CK(launch_sph_fs_fast(sp, g->Jrep, g->parab, g->stream));
-            else CK(launch_sph_fs(sp, fp64, g->parab, with_lstar, g->stream));
+            CK(launch(sp, g->stream));
             ++g->launches;
         } else {
             // host records, chunk by chunk of solid angles: the streamed mode
@@ -489,8 +495,7 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
                     CK(cudaStreamWaitEvent(g->stream, g->c_copied[k], 0));
                 }
                 cudaStream_t ks = alt && k ? g->cstream : g->stream;
-                if (sfast) CK(launch_sph_fs_fast(cp, g->Jrep, g->parab, ks));
-                else CK(launch_sph_fs(cp, fp64, g->parab, with_lstar, ks));
+                CK(launch(cp, ks));
                 ++g->launches;
                 if (copy) CK(cudaEventRecord(g->c_free[k], g->stream));
             }

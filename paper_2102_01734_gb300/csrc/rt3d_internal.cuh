@@ -423,6 +423,9 @@ cudaError_t launch_sph_fs(const SphFsParams &p, bool fp64, bool parabolic, bool 
 // entry; fold afterwards)
 cudaError_t launch_sph_fs_fast(const SphFsParams &p, double *Jrep, bool parabolic,
                                cudaStream_t s);
+// the same in FP64 (the Cartesian FP64 kernel's per-point step)
+cudaError_t launch_sph_fs64_fast(const SphFsParams &p, double *Jrep, bool parabolic,
+                                 cudaStream_t s);
 // the cell (r + nr (t + nt p)) of a replicated index r + 2 nr (t + 2 nt p)
 __host__ __device__ inline int sph_cell_of_rep(int rep, int nr, int nt) {
     const int q = rep / (2 * nr), p = q / (2 * nt);

@@ -16,6 +16,7 @@
 // weight w l / (chord sum of the cell for this angle) and the Lambda* window
 // (neighbourhood in index space, periodic in phi only).
 #include "fs_step.cuh"
+#include "fs64_step.cuh"
 
 namespace rt3d {
 
@@ -656,7 +657,84 @@ __global__ void __launch_bounds__(128) sph_fs_fast_kernel(SphFsParams p, double 
         atomicAdd(Jrep + st.vc, __longlong_as_double(0x7ff8000000000000LL));
 }
 
+// FP64 formal solution without Lambda* on the spherical cache: the per-point
+// step of the Cartesian FP64 kernel (fs64_fast_kernel: the update in
+// difference form, FP32-seeded reciprocals, the fitted series for small
+// optical depths, branch tests on high words) over the per-segment records,
+// one ray per thread in the builder's order. Half chord l/2 from the FP64
+// chord (exact), J weight the record's two-float sum; contributions reduced
+// at the replicated index (folded afterwards).
+template <bool PARAB>
+__global__ void __launch_bounds__(128) sph_fs64_fast_kernel(SphFsParams p, double *__restrict__ Jrep) {
+    const long long ray = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (ray >= p.nrays) return;
+    const long long s0 = p.ray_off[ray];
+    const int K = p.ray_len[ray];
+    const int kind = p.ray_kind[ray];
+    const float4 *__restrict__ rr = p.rec + s0;
+    const double *__restrict__ l64 = p.len64 + s0;
+    const double2 *__restrict__ chiS = static_cast<const double2 *>(p.chiS);
+    double I = 0.0;
+    if (!p.homogeneous) {
+        if (kind == 2) I = p.core_face ? p.core_face[p.ray_face[ray]] : p.I_core;
+        else if (kind == 1) I = p.I_irr;
+        else I = p.I_out;
+    }
+    float4 r = __ldg(rr);
+    int vc = __float_as_int(r.x);
+    const double2 cs = chiS[vc];
+    double hc = cs.x * (0.5 * __ldg(l64));  // half the optical depth of the point's chord
+    double cwc = (double)r.y + (double)r.w;
+    double u = hc;  // the entry interval: chi_{-1} l_{-1} = 0
+    double Sc = cs.y, Sp = cs.y, dS = 0.0;  // S_{-1} = S_0
+    double ru = PARAB ? recip64(hc) : 0.0;
+    for (int k = 1; k < K; ++k) {
+        r = __ldg(rr + k);
+        const int vn = __float_as_int(r.x);
+        const double2 cn = chiS[vn];
+        const double hn = cn.x * (0.5 * __ldg(l64 + k));
+        const double dSn = cn.y - Sc;
+        const double w = hc + hn;
+        const IntervalDE f = interval64<PARAB>(u, ru);
+        double In = fma(f.e0, Sp - I, I);
+        In = fma(f.a, dS, In);
+        if (PARAB) {
+            const double rw = recip64(w);
+            const double q = u * rw;
+            if (hi_below(u, 0x3FF00000) && hi_below(q, 0x40100000)) {
+                double fw = 1.0;
+                if (!hi_below(u, 0x3FE00000)) fw = fma(-2.0, u, 2.0);
+                if (!hi_below(q, 0x40000000)) fw *= fma(-0.5, q, 2.0);
+                const double sd = fw * (u * recip64(u + w)) * f.d;
+                In = fma(sd, fma(-q, dSn, dS), In);
+            }
+            ru = rw;
+        }
+        I = In;
+        atomicAdd(Jrep + vc, cwc * I);
+        u = w;
+        hc = hn;
+        Sp = Sc;
+        Sc = cn.y;
+        dS = dSn;
+        vc = vn;
+        cwc = (double)r.y + (double)r.w;
+    }
+    const IntervalDE f = interval64<PARAB>(u, ru);
+    I = fma(f.a, dS, fma(f.e0, Sp - I, I));
+    atomicAdd(Jrep + vc, cwc * I);
+}
+
 }  // namespace
+
+cudaError_t launch_sph_fs64_fast(const SphFsParams &p, double *Jrep, bool parabolic,
+                                 cudaStream_t s) {
+    const int threads = 128;
+    const long long blocks = (p.nrays + threads - 1) / threads;
+    if (parabolic) sph_fs64_fast_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(p, Jrep);
+    else sph_fs64_fast_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(p, Jrep);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sph_fs_fast(const SphFsParams &p, double *Jrep, bool parabolic,
                                cudaStream_t s) {

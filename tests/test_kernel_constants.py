@@ -69,7 +69,7 @@ def test_fp32_fit_on_unit_interval():
 
 
 def test_fp64_fit_on_half_interval():
-    body = _function_body("fs.cu", "__device__ __forceinline__ IntervalDE interval64(")
+    body = _function_body("fs64_step.cuh", "__device__ __forceinline__ IntervalDE interval64(")
     coefs = [float(x) for x in re.findall(r"(?:double p =|fma\(p, u,) " + NUM, body)]
     assert len(coefs) == 10  # degree 9
     worst = 0.0
