@@ -81,6 +81,11 @@ def _load():
         lib.orc_fs_sph.argtypes = [c_int, c_int, c_int, c_double, c_double, c_int, c_int, c_int,
                                    _dp, _dp, _dp, c_double, c_double, _dp, _dp]
         lib.orc_fs_sph.restype = c_int
+        lib.orc_fs_sph_bc.argtypes = [c_int, c_int, c_int, c_double, c_double, c_int, c_int,
+                                      c_int, _dp, _dp, _dp, _dp, _dp, c_double, c_double, _dp, _dp]
+        lib.orc_fs_sph_bc.restype = c_int
+        lib.orc_diffusion_bc_sph.argtypes = [c_int, c_int, c_int, c_double, c_double, _dp, _dp,
+                                             _dp, _dp]
         _lib = lib
     return _lib
 
@@ -350,19 +355,37 @@ def sph_rays(n, ntheta, nphi, o, r_in=1.0, r_out=1.3):
 
 
 def fs_sph(chi, S, B, ntheta, nphi, parabolic=False, I_out=0.0, I_irr=0.0, lstar=False,
-           r_in=1.0, r_out=1.3):
+           r_in=1.0, r_out=1.3, core_face=None, core_grad=None):
     """Formal solution on the spherical grid; arrays shaped (np, nt, nr)
-    (r fastest: v = ir + nr (it + nt ip))."""
+    (r fastest: v = ir + nr (it + nt ip)). Rays from the core start with B of
+    their first cell, or, with core_face (np, nt), with core_face + mu
+    core_grad (the diffusion condition; core_grad optional)."""
     lib = _load()
     chi, S, B = _f64(chi), _f64(S), _f64(B)
     np_, nt, nr = chi.shape
     J = np.zeros(chi.shape)
     L = np.zeros((chi.size, 27)) if lstar else None
-    err = lib.orc_fs_sph(nr, nt, np_, r_in, r_out, ntheta, nphi, int(parabolic), _ptr(chi),
-                         _ptr(S), _ptr(B), float(I_out), float(I_irr), _ptr(J), _ptr(L))
+    cf = None if core_face is None else _f64(core_face)
+    cg = None if core_grad is None else _f64(core_grad)
+    err = lib.orc_fs_sph_bc(nr, nt, np_, r_in, r_out, ntheta, nphi, int(parabolic), _ptr(chi),
+                            _ptr(S), _ptr(B), _ptr(cf), _ptr(cg), float(I_out), float(I_irr),
+                            _ptr(J), _ptr(L))
     if err:
         raise RuntimeError(f"spherical formal solution failed ({err})")
     return (J, L) if lstar else J
+
+
+def diffusion_bc_sph(chi, B, r_in=1.0, r_out=1.3):
+    """Core-face (I_face, grad) of the LTE diffusion inner boundary on the
+    spherical grid, each (np, nt): dB/dtau between the two innermost shells
+    and B carried linearly to the core sphere."""
+    lib = _load()
+    chi, B = _f64(chi), _f64(B)
+    np_, nt, nr = chi.shape
+    I_face, grad = np.zeros((np_, nt)), np.zeros((np_, nt))
+    lib.orc_diffusion_bc_sph(nr, nt, np_, r_in, r_out, _ptr(chi), _ptr(B), _ptr(I_face),
+                             _ptr(grad))
+    return I_face, grad
 
 
 # ------------------------------------------------------------ line transfer

@@ -25,8 +25,10 @@
  *    sign of the cross product with the edge directions of phi.
  *  - points at chord midpoints, dtau, interpolation, J and the Lambda*
  *    window as on the Cartesian grid; entry through the core: I = B of the
- *    first cell; through the outer sphere: I = 0, or I_irr where the entry
- *    point has x > 0 and the direction d_x < 0 (irradiation from +x).
+ *    first cell, or the LTE diffusion condition I = I_face + mu dB/dtau
+ *    (orc_diffusion_bc_sph); through the outer sphere: I = 0, or I_irr where
+ *    the entry point has x > 0 and the direction d_x < 0 (irradiation from
+ *    +x).
  *  - trig tables (cos/sin of the edges and centres) from libm on the host.
  */
 #include <math.h>
@@ -305,15 +307,53 @@ static double sph_dIdS(int k, int j, const double *E, const double *al, const do
     return sum;
 }
 
+/* The LTE diffusion inner boundary on the core sphere (Sec. 3.2: the SP test
+ * case's inner boundary, as on the Cartesian grid), per core face (it, ip),
+ * face index it + nt ip, from the two innermost shells v0 = nr (it + nt ip)
+ * and v1 = v0 + 1:
+ *   dB/dtau = (B(v0) - B(v1)) / (1/2 (chi(v0) + chi(v1)) (rc1 - rc0)),
+ * the one-sided difference over the radial distance of the two cell centres
+ * rc_i = sqrt(r_e[i] r_e[i+1]) (tau increases inward), and
+ *   I_face = B(v0) + chi(v0) (rc0 - r_in) dB/dtau,
+ * B carried linearly from the innermost centre down to the core sphere. One
+ * shell (nr = 1): grad = 0, I_face = B(v0). A ray that enters from the core
+ * in direction d at the point p of the core sphere starts with
+ *   I = I_face + mu dB/dtau,  mu = p . d / r_in,
+ * mu the cosine between the ray and the outward normal of the core. */
+void orc_diffusion_bc_sph(int nr, int nt, int np, double r_in, double r_out, const double *chi,
+                          const double *B, double *I_face, double *grad)
+{
+    orc_sph g;
+    sph_init(&g, nr, nt, np, r_in, r_out);
+    for (int ip = 0; ip < np; ip++)
+        for (int it = 0; it < nt; it++) {
+            const int f = it + nt * ip;
+            const long v0 = (long)nr * f;
+            if (nr < 2) {
+                grad[f] = 0.0;
+                I_face[f] = B[v0];
+                continue;
+            }
+            const double dtau = 0.5 * (chi[v0] + chi[v0 + 1]) * (g.rc[1] - g.rc[0]);
+            grad[f] = (B[v0] - B[v0 + 1]) / dtau;
+            I_face[f] = B[v0] + chi[v0] * (g.rc[0] - r_in) * grad[f];
+        }
+    sph_free(&g);
+}
+
 /* Formal solution on the spherical grid for all solid angles (and the
  * 27-point Lambda* band over the index neighbourhood, periodic in phi):
- * J_v = sum_Omega w (sum_{k in v} l_k I_k) / (sum_{k in v} l_k). B gives the
- * core boundary intensity of the first cell; I_out the incoming intensity at
+ * J_v = sum_Omega w (sum_{k in v} l_k I_k) / (sum_{k in v} l_k). A ray that
+ * enters from the core starts with core_face[f] + mu core_grad[f] (f the core
+ * face of its first cell, mu the cosine at its entry point: the diffusion
+ * condition above) when core_face is given, else with B of its first cell
+ * (core_grad nullable: no gradient term); I_out is the incoming intensity at
  * the outer sphere (0 in the paper's set-up), I_irr the irradiation. lstar
  * nullable [N][27]. Returns 0 or < 0. */
-int orc_fs_sph(int nr, int nt, int np, double r_in, double r_out, int nth, int nph,
-               int parabolic, const double *chi, const double *S, const double *B,
-               double I_out, double I_irr, double *J, double *lstar)
+int orc_fs_sph_bc(int nr, int nt, int np, double r_in, double r_out, int nth, int nph,
+                  int parabolic, const double *chi, const double *S, const double *B,
+                  const double *core_face, const double *core_grad, double I_out, double I_irr,
+                  double *J, double *lstar)
 {
     orc_sph g;
     sph_init(&g, nr, nt, np, r_in, r_out);
@@ -356,8 +396,18 @@ int orc_fs_sph(int nr, int nt, int np, double r_in, double r_out, int nth, int n
                 Sp[k] = S[vox[k]];
             }
             double I0;
-            if (ec) I0 = B[vox[0]];
-            else I0 = (pin[0] > 0.0 && d[0] < 0.0) ? I_irr : I_out;
+            if (ec && core_face) {
+                const int f = vox[0] / nr;  /* it + nt ip of the first cell */
+                I0 = core_face[f];
+                if (core_grad) {
+                    const double mu = (pin[0] * d[0] + pin[1] * d[1] + pin[2] * d[2]) / r_in;
+                    I0 += mu * core_grad[f];
+                }
+            } else if (ec) {
+                I0 = B[vox[0]];
+            } else {
+                I0 = (pin[0] > 0.0 && d[0] < 0.0) ? I_irr : I_out;
+            }
             orc_ray_fs(K, chil, Sp, I0, parabolic, I, E, al, be, ga);
             for (int k = 0; k < K; k++) {
                 num[vox[k]] += len[k] * I[k];
@@ -385,4 +435,12 @@ int orc_fs_sph(int nr, int nt, int np, double r_in, double r_out, int nth, int n
     free(num); free(den); free(numL); free(hit); free(mu); free(phi); free(dir); free(w);
     sph_free(&g);
     return err;
+}
+
+int orc_fs_sph(int nr, int nt, int np, double r_in, double r_out, int nth, int nph,
+               int parabolic, const double *chi, const double *S, const double *B,
+               double I_out, double I_irr, double *J, double *lstar)
+{
+    return orc_fs_sph_bc(nr, nt, np, r_in, r_out, nth, nph, parabolic, chi, S, B, NULL, NULL,
+                         I_out, I_irr, J, lstar);
 }

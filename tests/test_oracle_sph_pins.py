@@ -190,3 +190,106 @@ def test_sph_lambda_star_on_coarse_cells():
     assert np.max(np.abs(diag)) < 1e-14
     assert np.max(off) < 1e-14
     assert np.min(off) < -1e-3  # the effect is real at this resolution
+
+
+# ---- the LTE diffusion inner boundary on the core sphere (Sec. 3.2)
+
+def _radial_centres(nr):
+    re = R_IN * (R_OUT / R_IN) ** (np.arange(nr + 1) / nr)
+    re[0], re[-1] = R_IN, R_OUT
+    return np.sqrt(re[:-1] * re[1:])
+
+
+def test_sph_diffusion_faces_exact_for_a_linear_profile():
+    """B linear in the radial optical depth with chi constant along each
+    radius: the one-sided difference is the exact dB/dtau and the carried
+    value the exact B on the core sphere; one shell: no gradient."""
+    n = (6, 5, 8)
+    nr, nt, np_ = n
+    rc = _radial_centres(nr)
+    rng = np.random.default_rng(0)
+    chic = 10 ** rng.uniform(-1, 1, (np_, nt))
+    a = rng.uniform(0.5, 2, (np_, nt))
+    b = rng.uniform(-1, 3, (np_, nt))
+    chi = np.broadcast_to(chic[:, :, None], chi_shape := (np_, nt, nr)).copy()
+    tau = chic[:, :, None] * (R_OUT - rc[None, None, :])
+    B = a[:, :, None] + b[:, :, None] * tau
+    I_face, grad = oracle.diffusion_bc_sph(chi, B)
+    assert np.allclose(grad, b, rtol=1e-12, atol=1e-12)
+    assert np.allclose(I_face, a + b * chic * (R_OUT - R_IN), rtol=1e-13, atol=1e-13)
+    I1, g1 = oracle.diffusion_bc_sph(chi[:, :, :1], B[:, :, :1])
+    assert np.array_equal(g1, np.zeros((np_, nt))) and np.array_equal(I1, B[:, :, 0])
+    assert chi.shape == chi_shape
+    # chi of the two innermost shells enters dB/dtau through their mean (a
+    # swap leaves it), the carried face value through the innermost alone
+    chi2 = 10 ** rng.uniform(-1, 1, chi.shape)
+    sw = chi2.copy()
+    sw[:, :, 0], sw[:, :, 1] = chi2[:, :, 1], chi2[:, :, 0]
+    Ia, ga = oracle.diffusion_bc_sph(chi2, B)
+    Ib, gb = oracle.diffusion_bc_sph(sw, B)
+    assert np.allclose(ga, gb, rtol=1e-14, atol=0)
+    assert np.allclose(Ia - B[:, :, 0], chi2[:, :, 0] * (rc[0] - R_IN) * ga, rtol=1e-13)
+    assert np.allclose(Ib - B[:, :, 0], chi2[:, :, 1] * (rc[0] - R_IN) * gb, rtol=1e-13)
+    assert not np.allclose(Ia, Ib, rtol=1e-6)
+
+
+def test_sph_diffusion_gradient_term_brute_force():
+    """Optically thin (chi = 1e-10), S = 0, I_face = 0: every ray keeps its
+    entry intensity, so J of a cell is the chord-weighted mean over the rays
+    of each angle of mu g for the rays from the core, with mu recomputed here
+    from the impact parameter |p x d| of the entry point (not the oracle's
+    dot product)."""
+    n = (4, 3, 6)
+    nr, nt, np_ = n
+    nth, nph = 2, 4
+    rng = np.random.default_rng(5)
+    g = rng.uniform(0.5, 2.0, (np_, nt))
+    chi = np.full((np_, nt, nr), 1e-10)
+    zero = np.zeros(chi.shape)
+    J = oracle.fs_sph(chi, zero, zero, nth, nph, False, core_face=np.zeros((np_, nt)),
+                      core_grad=g)
+    mu, phi, d, w = oracle.directions(nth, nph)
+    N = nr * nt * np_
+    Jb = np.zeros(N)
+    ncore = 0
+    for o in range(nth * nph):
+        num, den = np.zeros(N), np.zeros(N)
+        for v in oracle.sph_rays(n, nth, nph, o):
+            vox, ln, core, pin = oracle.sph_trace(n, d[o], int(v))
+            I0 = 0.0
+            if core:
+                p = np.linalg.norm(np.cross(pin, d[o]))
+                m = math.sqrt(max(0.0, 1.0 - (p / R_IN) ** 2))
+                f = vox[0] // nr
+                I0 = m * g.reshape(-1)[f]
+                ncore += 1
+            np.add.at(num, vox, ln * I0)
+            np.add.at(den, vox, ln)
+        Jb += w[o] * num / den
+    assert ncore > 0
+    assert np.allclose(J.reshape(-1), Jb, rtol=1e-8, atol=1e-12)
+    assert np.max(J) > 0.1
+
+
+@pytest.mark.parametrize("nr", [12, 24])
+def test_sph_diffusion_boundary_in_the_grey_lte_limit(nr):
+    """Grey LTE atmosphere (S = B = 3/4 (tau + 2/3), chi ~ r^-12, innermost
+    shell of optical thickness ~1): entering with I = B of the first cell
+    leaves the innermost mean intensity 16 % below B; the diffusion condition
+    brings it within 4 % (the remainder is the curvature of the shell), and
+    closer with finer shells."""
+    n = (nr, 4, 8)
+    rc = _radial_centres(nr)
+    chi = np.broadcast_to(12 * rc ** -12.0, (8, 4, nr)).copy()
+    tau = rc ** -11.0 - R_OUT ** -11.0
+    B = np.broadcast_to(0.75 * (tau + 2.0 / 3.0), (8, 4, nr)).copy()
+    I_face, grad = oracle.diffusion_bc_sph(chi, B)
+    Jd = oracle.fs_sph(chi, B, B, 4, 8, True, core_face=I_face, core_grad=grad)
+    Jp = oracle.fs_sph(chi, B, B, 4, 8, True)
+    dd = np.mean(Jd[:, :, 0] / B[:, :, 0] - 1)
+    dp = np.mean(Jp[:, :, 0] / B[:, :, 0] - 1)
+    assert dp < -0.15
+    assert abs(dd) < 0.04 and abs(dd) < 0.25 * abs(dp)
+    # the gradient term is what does it: the carried face value alone is not enough
+    Jf = oracle.fs_sph(chi, B, B, 4, 8, True, core_face=I_face)
+    assert np.mean(Jf[:, :, 0] / B[:, :, 0] - 1) < -0.1
