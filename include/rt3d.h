@@ -142,17 +142,21 @@ typedef struct {
     const double *I_bottom_face;
     double I_irr;     /* RT3D_SPHERICAL: irradiation entering the outer sphere at
                          points with x > 0 along directions with d_x < 0 */
-    const double *I_bottom_grad; /* nullable double[ny][nx] (Cartesian grids; RT3D_EINVAL
-                         on a spherical one): the diffusion inner boundary, where a
+    const double *I_bottom_grad; /* nullable double[ny][nx] (spherical grids:
+                         [nphi][ntheta]): the diffusion inner boundary, where a
                          characteristic with direction cosine mu > 0 enters with
                          I = I_bottom (or its face value) + mu I_bottom_grad, the
                          gradient being dB/dtau at the boundary with tau the vertical
-                         optical depth growing inward (rt3d_diffusion_bc) */
+                         (radial) optical depth growing inward (rt3d_diffusion_bc) */
 } rt3d_bc;
 /* On a spherical grid I_top (or I_top_face, unused) is the intensity entering
  * the outer sphere outside the irradiated part, I_bottom / I_bottom_face
  * ([nphi][ntheta], index it + nt ip) the intensity leaving the core into the
- * first cell of a characteristic. */
+ * first cell of a characteristic; with I_bottom_grad a characteristic leaves
+ * the core with I_bottom + mu I_bottom_grad, mu the cosine between it and the
+ * core's outward normal at its entry point (computed per characteristic on
+ * the device at every formal solution; 12 bytes per characteristic,
+ * allocated on first use). */
 
 typedef struct {
     int iterations;     /* ALI iterations of the main loop */
@@ -333,11 +337,15 @@ rt3d_status rt3d_formal_solution(rt3d_grid *grid, const double *chi, const doubl
  * face, half a voxel below the innermost centre, where the characteristics
  * enter; nz = 1 gives grad = 0 and I_face = B[l][0][f]. Pass them as
  * rt3d_bc's I_bottom_face and I_bottom_grad. chi, B: double[nlambda][N];
- * I_face, grad: double[nlambda][ny][nx], written. All four must be memory of
- * the grid's device (or managed memory); the kernel runs on the grid's
- * stream, which the call does not synchronise. RT3D_EINVAL for a NULL
- * argument, nlambda < 1, a spherical grid or a pointer that is not device
- * memory. */
+ * I_face, grad: double[nlambda][ny][nx], written. On a spherical grid the
+ * faces are the core's, double[nlambda][nphi][ntheta] (index it + nt ip):
+ * dB/dtau = (B0 - B1) / (1/2 (chi0 + chi1) (rc1 - rc0)) between the two
+ * innermost shells (centres rc_i = sqrt(r_e[i] r_e[i+1])) and
+ * I_face = B0 + chi0 (rc0 - r_in) dB/dtau, B carried down to the core sphere
+ * (nr = 1: grad = 0). All four must be memory of the grid's device (or
+ * managed memory); the kernel runs on the grid's stream, which the call does
+ * not synchronise. RT3D_EINVAL for a NULL argument, nlambda < 1 or a pointer
+ * that is not device memory. */
 rt3d_status rt3d_diffusion_bc(rt3d_grid *grid, int nlambda, const double *chi, const double *B,
                               double *I_face, double *grad);
 

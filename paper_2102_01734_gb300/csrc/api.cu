@@ -16,6 +16,7 @@
 
 #include "rt3d_internal.cuh"
 #include "stream.cuh"
+#include "sph_bc.cuh"
 
 using namespace rt3d;
 
@@ -177,6 +178,13 @@ struct rt3d_grid {
     // slot; c_fork: the formal solution began); without copies the chunks'
     // kernels alternate between the grid's stream and cstream
     int cache = RT3D_CACHE_DEVICE;
+    // diffusion inner boundary: the directions on the device, the radial
+    // cell centres on the host, and (allocated on first use) every ray's
+    // entry intensity with the identity index the kernels read it through
+    double *s_dir = nullptr;
+    std::vector<double> s_rc_h;
+    double *s_ray_I0 = nullptr;
+    int *s_ident = nullptr;
     float4 *h_rec = nullptr;
     double *h_len64 = nullptr;
     std::vector<int> c_angle;
@@ -338,12 +346,10 @@ rt3d_status fs_params(rt3d_grid *g, const rt3d_bc *bc, bool fp64, bool homogeneo
         const double *tf = nullptr, *bf = nullptr;
         const size_t nf = (size_t)g->nx * g->ny;
         const size_t nfb = g->sph ? (size_t)g->ny * g->nz : nf;  // spherical core face
-        if (g->sph && bc->I_bottom_grad)
-            return fail(RT3D_EINVAL, "I_bottom_grad needs a Cartesian grid");
         if (!g->sph) TRY(stage_in(g, bc->I_top_face, nf, g->top, &tf));
         TRY(stage_in(g, bc->I_bottom_face, nfb, g->bot, &bf));
         const double *gf = nullptr;
-        if (!g->sph) TRY(stage_in(g, bc->I_bottom_grad, nf, g->bgrad_face, &gf));
+        TRY(stage_in(g, bc->I_bottom_grad, nfb, g->bgrad_face, &gf));
         q.top_face = tf;
         q.bot_face = bf;
         q.bot_grad = gf;
@@ -436,6 +442,21 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
         sp.I_out = base.I_top;
         sp.I_irr = base.I_irr;
         sp.homogeneous = base.homogeneous;
+        if (base.bot_grad && !base.homogeneous) {
+            // diffusion condition on the core: every ray's entry intensity,
+            // read by the kernels as a per-ray core face
+            if (!g->s_ray_I0) {
+                TRY(g->alloc(&g->s_ray_I0, g->s_nrays));
+                TRY(g->alloc(&g->s_ident, g->s_nrays));
+            }
+            SphEntryParams ep{g->s_nrays, g->nx, g->ny, g->desc.r_in, g->s_ray_launch,
+                              g->s_ray_angle, g->s_ray_kind, g->s_ray_face, g->s_rc,
+                              g->s_stc, g->s_ctc, g->s_cpc, g->s_spc, g->s_dir};
+            CKL(launch_sph_entry(ep, base.bot_face, base.I_bot, base.bot_grad, g->s_ray_I0,
+                                 g->s_ident, g->stream));
+            sp.core_face = g->s_ray_I0;
+            sp.ray_face = g->s_ident;
+        }
         // without Lambda*: the record kernels (FP32 or FP64) into the
         // replicated Jrep, folded after
         const bool sfast = !with_lstar;
@@ -473,10 +494,10 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
                 SphFsParams cp = sp;
                 const long long r0 = g->c_ray[c], s0 = g->c_seg[c], ns = g->c_seg[c + 1] - s0;
                 cp.nrays = g->c_ray[c + 1] - r0;
-                cp.ray_off = g->s_ray_off + r0;
-                cp.ray_len = g->s_ray_len + r0;
-                cp.ray_kind = g->s_ray_kind + r0;
-                cp.ray_face = g->s_ray_face + r0;
+                cp.ray_off = sp.ray_off + r0;
+                cp.ray_len = sp.ray_len + r0;
+                cp.ray_kind = sp.ray_kind + r0;
+                cp.ray_face = sp.ray_face + r0;
                 const int k = c & 1;
                 cp.rec = g->s_rec + s0;
                 cp.len64 = g->s_len64 + s0;
@@ -680,7 +701,7 @@ rt3d_status alloc_work(rt3d_grid *g) {
     TRY(g->alloc(&g->lstar, 27 * N));
     TRY(g->alloc(&g->top, nf));
     TRY(g->alloc(&g->bot, nf));
-    if (!g->sph) TRY(g->alloc(&g->bgrad_face, nf));
+    TRY(g->alloc(&g->bgrad_face, nf));
     TRY(g->alloc(&g->dJ_dev, 2));
     TRY(g->alloc(reinterpret_cast<double2 **>(&g->chiS64), 4 * N));
     TRY(g->alloc(reinterpret_cast<float2 **>(&g->chiS32), 4 * N));
@@ -1004,7 +1025,8 @@ rt3d_status sph_build(rt3d_grid *g) {
     g->release(d_err, 1);
     g->release(d_rbase, nO);
     g->release(d_sbase, nO);
-    g->release(d_dir, g->dir.size());
+    g->s_dir = d_dir;  // kept for the diffusion boundary's entry cosines
+    g->s_rc_h = rc;
     g->release(d_wt, g->wt.size());
     g->release(stage_rec, (size_t)stage_seg);
     g->release(stage_len64, (size_t)stage_seg);
@@ -1868,9 +1890,14 @@ rt3d_status rt3d_diffusion_bc(rt3d_grid *g, int nl, const double *chi, const dou
                               double *I_face, double *grad) {
     if (!g || !chi || !B || !I_face || !grad) return fail(RT3D_EINVAL, "NULL argument");
     if (nl < 1) return fail(RT3D_EINVAL, "nlambda %d < 1", nl);
-    if (g->sph) return fail(RT3D_EINVAL, "the diffusion boundary arrays need a Cartesian grid");
     if (!is_device_ptr(chi) || !is_device_ptr(B) || !is_device_ptr(I_face) || !is_device_ptr(grad))
         return fail(RT3D_EINVAL, "chi, B, I_face and grad must be memory of the grid's device");
+    if (g->sph) {
+        const double rc0 = g->s_rc_h[0], rc1 = g->nx > 1 ? g->s_rc_h[1] : rc0;
+        CKL(launch_sph_diffusion_bc(g->nx, g->ny, g->nz, nl, rc0, rc1, g->desc.r_in, chi, B,
+                                    I_face, grad, g->stream));
+        return RT3D_OK;
+    }
     CKL(launch_diffusion_bc(g->nx, g->ny, g->nz, nl, chi, B, I_face, grad, g->stream));
     return RT3D_OK;
 }

@@ -355,12 +355,16 @@ def formal_solution_ff(h, chi, S, bc=None, J_out=None):
     return J_out
 
 
-def diffusion_bc(h, chi, B):
+def diffusion_bc(h, chi, B, spherical=False):
     """Bottom-face (I_bottom, I_bottom_grad) of the diffusion inner boundary
     from device tensors chi, B of shape (nz, ny, nx) or (n_lambda, nz, ny, nx);
-    returns two device tensors of shape (ny, nx) or (n_lambda, ny, nx)."""
+    returns two device tensors of shape (ny, nx) or (n_lambda, ny, nx). On a
+    spherical grid (arrays (nphi, ntheta, nr)) the core faces, (nphi, ntheta)."""
     nl = 1 if chi.dim() == 3 else int(chi.shape[0])
-    face_shape = tuple(chi.shape[:-3]) + tuple(chi.shape[-2:])
+    if spherical:
+        face_shape = tuple(chi.shape[:-1])
+    else:
+        face_shape = tuple(chi.shape[:-3]) + tuple(chi.shape[-2:])
     I_face = torch.empty(face_shape, dtype=torch.float64, device=chi.device)
     grad = torch.empty_like(I_face)
     _check(load().rt3d_diffusion_bc(h, nl, _ptr(chi), _ptr(B), _ptr(I_face), _ptr(grad)))
@@ -462,6 +466,7 @@ class Grid:
         if np.isscalar(n):
             n = (int(n),) * 3
         self.n = tuple(int(v) for v in n)
+        self.geometry = geometry
         self.shape = (self.n[2], self.n[1], self.n[0])
         self.N = self.n[0] * self.n[1] * self.n[2]
         self.handle = grid_create(n, ntheta, nphi, interp, precision, stream, geometry=geometry,
@@ -511,7 +516,7 @@ class Grid:
         return J
 
     def diffusion_bc(self, chi, B):
-        return diffusion_bc(self.handle, chi, B)
+        return diffusion_bc(self.handle, chi, B, spherical=self.geometry == SPHERICAL)
 
     def os_solve(self, lstar, eps, r, max_sweeps=50, tol=1e-3):
         dJ = _empty_like(r, r.shape)
