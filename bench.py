@@ -711,7 +711,8 @@ def run_spherical(args):
     link_gbs = pinned_h2d_gbs(args, e0, e1) if any(c != "device" for c in names) else 0.0
     for cname in names:
         res = {}
-        for name, prec in (("fp32", rt3d.FP32_FS_FP64_ALI), ("fp64", rt3d.FP64)):
+        mixed = rt3d.FP32_FS_FF_REFINE if args.sph_refine == "ff" else rt3d.FP32_FS_FP64_ALI
+        for name, prec in (("fp32", mixed), ("fp64", rt3d.FP64)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, prec, geometry=rt3d.SPHERICAL,
@@ -751,6 +752,16 @@ def run_spherical(args):
                 res[f"fs_{name}_h2d_bytes"] = hb
                 res[f"fs_{name}_h2d_gbs"] = hb / (ms / 1e3) / 1e9
             if name == "fp32":
+                g.formal_solution_ff(tchi, tB, tbc)
+                torch.cuda.synchronize()
+                times = []
+                for _ in range(3):
+                    e0.record()
+                    g.formal_solution_ff(tchi, tB, tbc)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                res["fs_ff_ms"] = min(times)
                 J = tB.clone()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -758,7 +769,8 @@ def run_spherical(args):
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
                 res["solve"] = {"seconds": dt, "solves_per_s": 1.0 / dt, "fs_fp32": st["fs_fp32"],
-                                "fs_fp64": st["fs_fp64"], "est_error": st["est_error"],
+                                "fs_fp64": st["fs_fp64"], "fs_ff": st["fs_ff"],
+                                "refine": args.sph_refine, "est_error": st["est_error"],
                                 "residual64": st["residual64"],
                                 "segments_per_s": (st["fs_fp32"] + st["fs_fp64"]) * info["segments"] / dt,
                                 "note": "includes the Lambda* build"}
@@ -984,6 +996,8 @@ def main():
                          "streamed (host records copied per chunk of solid angles), mapped "
                          "(host records read in place), chords (FP32 records on the device, "
                          "FP64 chords streamed from the host)")
+    ap.add_argument("--sph-refine", choices=("ff", "fp64"), default="ff",
+                    help="spherical solve's refinement residuals: float-float or FP64")
     ap.add_argument("--sph-stream-bytes", type=int, default=0,
                     help="host cache modes: largest chunk of records in bytes (0: 1 GiB)")
     ap.add_argument("--line", action="store_true",

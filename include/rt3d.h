@@ -72,7 +72,7 @@ enum {
                                   formal solution (rt3d_formal_solution_ff) and only
                                   the residual that certifies J from an FP64 formal
                                   solution (the plain ALI's defect correction keeps
-                                  FP64 residuals); Cartesian grids only */
+                                  FP64 residuals) */
 };
 
 /* Residency of the spherical geometry cache (Sec. 4.3: the LargeGPU mode keeps
@@ -352,10 +352,13 @@ rt3d_status rt3d_diffusion_bc(rt3d_grid *grid, int nlambda, const double *chi, c
 /* The formal solution without Lambda* in float-float arithmetic (not in the
  * paper: FP64-class accuracy, about 1e-13 relative, on the FP32 pipe; GB300's
  * FP64 rate is about 1/64 of its FP32 rate). Same arguments, layouts and
- * error behaviour as rt3d_formal_solution without lstar_out; Cartesian grids
- * of any precision (RT3D_EINVAL for a spherical grid). The first call
- * allocates the split step records (16 bytes per cached point) and the split
- * replicated (chi, S) (64 bytes per voxel). */
+ * error behaviour as rt3d_formal_solution without lstar_out; grids of any
+ * precision and geometry. The first call allocates the split replicated
+ * (chi, S) (64 bytes per voxel) and, on a Cartesian grid, the split step
+ * records (16 bytes per cached point); a spherical grid splits its FP64
+ * chords per point instead (its records already hold the J weight as a
+ * float-float pair) and reads them like the FP64 formal solution, in every
+ * cache residency. */
 rt3d_status rt3d_formal_solution_ff(rt3d_grid *grid, const double *chi, const double *S,
                                     const rt3d_bc *bc, double *J_out);
 

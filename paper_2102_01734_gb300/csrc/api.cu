@@ -17,6 +17,7 @@
 #include "rt3d_internal.cuh"
 #include "stream.cuh"
 #include "sph_bc.cuh"
+#include "sph_ff.cuh"
 
 using namespace rt3d;
 
@@ -412,6 +413,129 @@ rt3d_status fs_tune(rt3d_grid *g, const FsParams &p) {
     return RT3D_OK;
 }
 
+// One formal solution on the spherical cache into g->Jfs (Lambda* into
+// g->lstar when requested): kind 0 FP32, 1 FP64, 2 float-float (without
+// Lambda*); chiS the replicated (chi, S) of that kind. The FP64 and
+// float-float kernels read the FP64 chords, which the host residencies copy
+// or read in place with the records.
+rt3d_status run_fs_sph(rt3d_grid *g, const FsParams &base, const void *chiS, int kind,
+                       bool with_lstar) {
+    const bool fp64 = kind != 0;
+    SphFsParams sp{};
+    sp.nrays = g->s_nrays;
+    sp.N = (int)g->N;
+    sp.ray_off = g->s_ray_off;
+    sp.ray_len = g->s_ray_len;
+    sp.ray_kind = g->s_ray_kind;
+    sp.ray_face = g->s_ray_face;
+    sp.nr = g->nx;
+    sp.nt = g->ny;
+    sp.np = g->nz;
+    sp.rec = g->s_rec;
+    sp.len64 = g->s_len64;
+    sp.chiS = chiS;
+    sp.J = g->Jfs;
+    sp.lstar = with_lstar ? g->lstar : nullptr;
+    sp.core_face = base.bot_face;
+    sp.I_core = base.I_bot;
+    sp.I_out = base.I_top;
+    sp.I_irr = base.I_irr;
+    sp.homogeneous = base.homogeneous;
+    if (base.bot_grad && !base.homogeneous) {
+        // diffusion condition on the core: every ray's entry intensity,
+        // read by the kernels as a per-ray core face
+        if (!g->s_ray_I0) {
+            TRY(g->alloc(&g->s_ray_I0, g->s_nrays));
+            TRY(g->alloc(&g->s_ident, g->s_nrays));
+        }
+        SphEntryParams ep{g->s_nrays, g->nx, g->ny, g->desc.r_in, g->s_ray_launch,
+                          g->s_ray_angle, g->s_ray_kind, g->s_ray_face, g->s_rc,
+                          g->s_stc, g->s_ctc, g->s_cpc, g->s_spc, g->s_dir};
+        CKL(launch_sph_entry(ep, base.bot_face, base.I_bot, base.bot_grad, g->s_ray_I0,
+                             g->s_ident, g->stream));
+        sp.core_face = g->s_ray_I0;
+        sp.ray_face = g->s_ident;
+    }
+    // without Lambda*: the record kernels (FP32 or FP64) into the
+    // replicated Jrep, folded after
+    const bool sfast = !with_lstar;
+    if (!sfast) CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
+    if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
+    TRY(collect_events(g));
+    CK(cudaEventRecord(g->ev0, g->stream));
+    auto launch = [&](const SphFsParams &q, cudaStream_t ks) -> cudaError_t {
+        if (!sfast) return launch_sph_fs(q, fp64, g->parab, with_lstar, ks);
+        if (kind == 2)
+            return launch_sph_fsff(q, static_cast<const float4 *>(chiS), g->Jrep, g->parab, ks);
+        return fp64 ? launch_sph_fs64_fast(q, g->Jrep, g->parab, ks)
+                    : launch_sph_fs_fast(q, g->Jrep, g->parab, ks);
+    };
+    if (g->cache == RT3D_CACHE_DEVICE) {
+        CK(launch(sp, g->stream));
+        ++g->launches;
+    } else {
+        // host records, chunk by chunk of solid angles: the streamed mode
+        // copies chunk c into slot c % 2 on the copy stream once the
+        // kernel of chunk c - 2 has released the slot, and the kernel of
+        // chunk c waits for its copy; the mapped mode reads the chunk in
+        // place; the chords mode reads the records on the device and
+        // streams the FP64 chords, which only the FP64 kernel reads.
+        // (In the mapped and chords modes cp.len64 is never read by the
+        // FP32 kernels.)
+        const bool chords = g->cache == RT3D_CACHE_HOST_CHORDS;
+        const bool copy = g->cache == RT3D_CACHE_HOST_STREAMED || (chords && fp64);
+        // without copies the chunks' kernels alternate between the grid's
+        // stream and the second stream, so that the tail of one overlaps
+        // the next (they only add into J and Lambda*)
+        const bool alt = !copy;
+        CK(cudaEventRecord(g->c_fork, g->stream));
+        CK(cudaStreamWaitEvent(g->cstream, g->c_fork, 0));
+        const int nch = (int)g->c_angle.size() - 1;
+        for (int c = 0; c < nch; ++c) {
+            SphFsParams cp = sp;
+            const long long r0 = g->c_ray[c], s0 = g->c_seg[c], ns = g->c_seg[c + 1] - s0;
+            cp.nrays = g->c_ray[c + 1] - r0;
+            cp.ray_off = sp.ray_off + r0;
+            cp.ray_len = sp.ray_len + r0;
+            cp.ray_kind = sp.ray_kind + r0;
+            cp.ray_face = sp.ray_face + r0;
+            const int k = c & 1;
+            cp.rec = g->s_rec + s0;
+            cp.len64 = g->s_len64 + s0;
+            if (copy) {
+                CK(cudaStreamWaitEvent(g->cstream, g->c_free[k], 0));
+                if (!chords) {
+                    CK(cudaMemcpyAsync(g->slot_rec[k], g->h_rec + s0, sizeof(float4) * ns,
+                                       cudaMemcpyHostToDevice, g->cstream));
+                    cp.rec = g->slot_rec[k];
+                }
+                if (fp64)
+                    CK(cudaMemcpyAsync(g->slot_len64[k], g->h_len64 + s0, sizeof(double) * ns,
+                                       cudaMemcpyHostToDevice, g->cstream));
+                cp.len64 = g->slot_len64[k];
+                CK(cudaEventRecord(g->c_copied[k], g->cstream));
+                CK(cudaStreamWaitEvent(g->stream, g->c_copied[k], 0));
+            }
+            cudaStream_t ks = alt && k ? g->cstream : g->stream;
+            CK(launch(cp, ks));
+            ++g->launches;
+            if (copy) CK(cudaEventRecord(g->c_free[k], g->stream));
+        }
+        if (alt) {  // join
+            CK(cudaEventRecord(g->c_copied[0], g->cstream));
+            CK(cudaStreamWaitEvent(g->stream, g->c_copied[0], 0));
+        }
+    }
+    CK(cudaEventRecord(g->ev1, g->stream));
+    g->ev_pending = kind == 2 ? 2 : fp64 ? 1 : (with_lstar ? 3 : 0);
+    if (!fp64 && with_lstar) ++g->fs_lstar32;
+    if (sfast) {
+        CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
+        ++g->launches;
+    }
+    return RT3D_OK;
+}
+
 // One formal solution of the packed (chi, S) of the given precision into
 // g->Jfs (zeroed here); Lambda* into g->lstar when requested.
 rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lstar) {
@@ -421,119 +545,7 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
     p.cw = fp64 ? (const void *)g->tpl.cw64 : (const void *)g->tpl.cw32;
     p.J = g->Jfs;
     p.lstar = with_lstar ? g->lstar : nullptr;
-    if (g->sph) {
-        SphFsParams sp{};
-        sp.nrays = g->s_nrays;
-        sp.N = (int)g->N;
-        sp.ray_off = g->s_ray_off;
-        sp.ray_len = g->s_ray_len;
-        sp.ray_kind = g->s_ray_kind;
-        sp.ray_face = g->s_ray_face;
-        sp.nr = g->nx;
-        sp.nt = g->ny;
-        sp.np = g->nz;
-        sp.rec = g->s_rec;
-        sp.len64 = g->s_len64;
-        sp.chiS = p.chiS;
-        sp.J = g->Jfs;
-        sp.lstar = p.lstar;
-        sp.core_face = base.bot_face;
-        sp.I_core = base.I_bot;
-        sp.I_out = base.I_top;
-        sp.I_irr = base.I_irr;
-        sp.homogeneous = base.homogeneous;
-        if (base.bot_grad && !base.homogeneous) {
-            // diffusion condition on the core: every ray's entry intensity,
-            // read by the kernels as a per-ray core face
-            if (!g->s_ray_I0) {
-                TRY(g->alloc(&g->s_ray_I0, g->s_nrays));
-                TRY(g->alloc(&g->s_ident, g->s_nrays));
-            }
-            SphEntryParams ep{g->s_nrays, g->nx, g->ny, g->desc.r_in, g->s_ray_launch,
-                              g->s_ray_angle, g->s_ray_kind, g->s_ray_face, g->s_rc,
-                              g->s_stc, g->s_ctc, g->s_cpc, g->s_spc, g->s_dir};
-            CKL(launch_sph_entry(ep, base.bot_face, base.I_bot, base.bot_grad, g->s_ray_I0,
-                                 g->s_ident, g->stream));
-            sp.core_face = g->s_ray_I0;
-            sp.ray_face = g->s_ident;
-        }
-        // without Lambda*: the record kernels (FP32 or FP64) into the
-        // replicated Jrep, folded after
-        const bool sfast = !with_lstar;
-        if (!sfast) CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
-        if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
-        TRY(collect_events(g));
-        CK(cudaEventRecord(g->ev0, g->stream));
-        auto launch = [&](const SphFsParams &q, cudaStream_t ks) -> cudaError_t {
-            if (!sfast) return launch_sph_fs(q, fp64, g->parab, with_lstar, ks);
-            return fp64 ? launch_sph_fs64_fast(q, g->Jrep, g->parab, ks)
-                        : launch_sph_fs_fast(q, g->Jrep, g->parab, ks);
-        };
-        if (g->cache == RT3D_CACHE_DEVICE) {
-            CK(launch(sp, g->stream));
-            ++g->launches;
-        } else {
-            // host records, chunk by chunk of solid angles: the streamed mode
-            // copies chunk c into slot c % 2 on the copy stream once the
-            // kernel of chunk c - 2 has released the slot, and the kernel of
-            // chunk c waits for its copy; the mapped mode reads the chunk in
-            // place; the chords mode reads the records on the device and
-            // streams the FP64 chords, which only the FP64 kernel reads.
-            // (In the mapped and chords modes cp.len64 is never read by the
-            // FP32 kernels.)
-            const bool chords = g->cache == RT3D_CACHE_HOST_CHORDS;
-            const bool copy = g->cache == RT3D_CACHE_HOST_STREAMED || (chords && fp64);
-            // without copies the chunks' kernels alternate between the grid's
-            // stream and the second stream, so that the tail of one overlaps
-            // the next (they only add into J and Lambda*)
-            const bool alt = !copy;
-            CK(cudaEventRecord(g->c_fork, g->stream));
-            CK(cudaStreamWaitEvent(g->cstream, g->c_fork, 0));
-            const int nch = (int)g->c_angle.size() - 1;
-            for (int c = 0; c < nch; ++c) {
-                SphFsParams cp = sp;
-                const long long r0 = g->c_ray[c], s0 = g->c_seg[c], ns = g->c_seg[c + 1] - s0;
-                cp.nrays = g->c_ray[c + 1] - r0;
-                cp.ray_off = sp.ray_off + r0;
-                cp.ray_len = sp.ray_len + r0;
-                cp.ray_kind = sp.ray_kind + r0;
-                cp.ray_face = sp.ray_face + r0;
-                const int k = c & 1;
-                cp.rec = g->s_rec + s0;
-                cp.len64 = g->s_len64 + s0;
-                if (copy) {
-                    CK(cudaStreamWaitEvent(g->cstream, g->c_free[k], 0));
-                    if (!chords) {
-                        CK(cudaMemcpyAsync(g->slot_rec[k], g->h_rec + s0, sizeof(float4) * ns,
-                                           cudaMemcpyHostToDevice, g->cstream));
-                        cp.rec = g->slot_rec[k];
-                    }
-                    if (fp64)
-                        CK(cudaMemcpyAsync(g->slot_len64[k], g->h_len64 + s0, sizeof(double) * ns,
-                                           cudaMemcpyHostToDevice, g->cstream));
-                    cp.len64 = g->slot_len64[k];
-                    CK(cudaEventRecord(g->c_copied[k], g->cstream));
-                    CK(cudaStreamWaitEvent(g->stream, g->c_copied[k], 0));
-                }
-                cudaStream_t ks = alt && k ? g->cstream : g->stream;
-                CK(launch(cp, ks));
-                ++g->launches;
-                if (copy) CK(cudaEventRecord(g->c_free[k], g->stream));
-            }
-            if (alt) {  // join
-                CK(cudaEventRecord(g->c_copied[0], g->cstream));
-                CK(cudaStreamWaitEvent(g->stream, g->c_copied[0], 0));
-            }
-        }
-        CK(cudaEventRecord(g->ev1, g->stream));
-        g->ev_pending = fp64 ? 1 : (with_lstar ? 3 : 0);
-        if (!fp64 && with_lstar) ++g->fs_lstar32;
-        if (sfast) {
-            CK(launch_fold(g->nx, g->ny, g->nz, g->Jrep, g->Jfs, g->stream));
-            ++g->launches;
-        }
-        return RT3D_OK;
-    }
+    if (g->sph) return run_fs_sph(g, base, p.chiS, fp64 ? 1 : 0, with_lstar);
     // without Lambda*: the replicated-accumulation kernels (J folded after)
     const bool fast = !with_lstar;
     if (fast && !fp64 && g->fs_shape.block == 0) TRY(fs_tune(g, p));
@@ -559,7 +571,13 @@ rt3d_status run_fs(rt3d_grid *g, const FsParams &base, bool fp64, bool with_lsta
 // is given) into g->Jfs; allocates its split inputs on first use.
 rt3d_status run_fs_ff(rt3d_grid *g, const FsParams &base, const double *chi, const double *src,
                       const double *eps, const double *B) {
-    if (g->sph) return fail(RT3D_EINVAL, "the float-float formal solution needs the Cartesian grid");
+    if (g->sph) {
+        // the records carry the float-float J weight and the FP32 half chord;
+        // only the split (chi, S) is needed
+        if (!g->chiSff) TRY(g->alloc(&g->chiSff, 4 * (size_t)g->N));
+        CKL(launch_pack_ff(g->nx, g->ny, g->nz, chi, src, eps, B, g->chiSff, g->stream));
+        return run_fs_sph(g, base, g->chiSff, 2, false);
+    }
     if (!g->recff) {
         TRY(g->alloc(&g->recff, (size_t)g->tpl.total));
         TRY(g->alloc(&g->chiSff, 4 * (size_t)g->N));
@@ -1068,8 +1086,6 @@ rt3d_status validate_desc(const rt3d_grid_desc *d) {
     if (d->precision != RT3D_FP64 && d->precision != RT3D_FP32_FS_FP64_ALI &&
         d->precision != RT3D_FP32_FS_FF_REFINE)
         return fail(RT3D_EINVAL, "bad precision %d", d->precision);
-    if (d->precision == RT3D_FP32_FS_FF_REFINE && d->geometry == RT3D_SPHERICAL)
-        return fail(RT3D_EINVAL, "float-float refinement needs the Cartesian grid");
     if (d->nlambda > 1) return fail(RT3D_EINVAL, "nlambda > 1 is not supported by this call");
     if (d->accel != RT3D_ACCEL_NONE && d->accel != RT3D_ACCEL_KRYLOV)
         return fail(RT3D_EINVAL, "bad accel %d", d->accel);

@@ -228,6 +228,8 @@ def test_sph_formal_solution_with_diffusion_boundary(rt3d, parabolic):
             hbc = {"I_top": 0.0, "I_irr": 10.0, "I_bottom": I_face, "I_bottom_grad": grad}
             J = g.formal_solution(dev(chi), dev(S), hbc)
             assert relerr(J.cpu().numpy(), Jo) < tol, (cache, prec)
+            J = g.formal_solution_ff(dev(chi), dev(S), bc)
+            assert relerr(J.cpu().numpy(), Jo) < 1e-11, (cache, prec)
             g.close()
 
 

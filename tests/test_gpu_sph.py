@@ -83,6 +83,11 @@ def test_sph_fs_parity(rt3d, parabolic):
             J2 = g.formal_solution(dev(chi), dev(S), dbc)
             err = np.max(np.abs(J2.cpu().numpy() - Jo) / np.abs(Jo))
             assert err < tol, (prec, err)
+        # float-float (any precision of grid)
+        for _ in range(2):
+            Jf = g.formal_solution_ff(dev(chi), dev(S), dbc)
+            err = np.max(np.abs(Jf.cpu().numpy() - Jo) / np.abs(Jo))
+            assert err < 1e-11, (prec, err)
 
 
 def test_sph_solve_matches_direct_solution(rt3d):
@@ -105,7 +110,7 @@ def test_sph_solve_matches_direct_solution(rt3d):
     ef = eps.reshape(-1)
     rhs = M @ (ef * B.reshape(-1)) + Jbc
     Jd = np.linalg.solve(np.eye(N) - M * (1 - ef)[None, :], rhs).reshape(chi.shape)
-    for prec in (rt3d.FP64, rt3d.FP32_FS_FP64_ALI):
+    for prec in (rt3d.FP64, rt3d.FP32_FS_FP64_ALI, rt3d.FP32_FS_FF_REFINE):
         for accel in (rt3d.ACCEL_NONE, rt3d.ACCEL_KRYLOV):
             g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, prec, accel=accel,
                           geometry=rt3d.SPHERICAL)

@@ -133,6 +133,9 @@ def test_host_cache_formal_solutions(rt3d, parabolic):
                 J2 = g.formal_solution(dev(chi), dev(S), dbc).cpu().numpy()
                 assert np.max(np.abs(J2 - Jo) / np.abs(Jo)) < tol, (name, prec)
                 assert np.max(np.abs(J2 - Jd2) / np.abs(Jd2)) < 1e-12, (name, prec)
+            # float-float: streams or reads the FP64 chords like the FP64 kernel
+            Jf = g.formal_solution_ff(dev(chi), dev(S), dbc).cpu().numpy()
+            assert np.max(np.abs(Jf - Jo) / np.abs(Jo)) < 1e-11, (name, prec)
             g.close()
 
 
@@ -158,7 +161,7 @@ def test_host_cache_solve_matches_direct_solution(rt3d):
     Jd = np.linalg.solve(np.eye(N) - M * (1 - ef)[None, :], rhs).reshape(chi.shape)
     seg = segments(rt3d, n, nth, nph)
     for name, mode, per in modes(rt3d):
-        for prec in (rt3d.FP64, rt3d.FP32_FS_FP64_ALI):
+        for prec in (rt3d.FP64, rt3d.FP32_FS_FP64_ALI, rt3d.FP32_FS_FF_REFINE):
             for accel in (rt3d.ACCEL_NONE, rt3d.ACCEL_KRYLOV):
                 g = rt3d.Grid(n, nth, nph, rt3d.PARABOLIC, prec, accel=accel,
                               geometry=rt3d.SPHERICAL, cache=mode, stream_bytes=per * seg // 4)
