@@ -456,8 +456,8 @@ rt3d_status run_fs_sph(rt3d_grid *g, const FsParams &base, const void *chiS, int
         sp.core_face = g->s_ray_I0;
         sp.ray_face = g->s_ident;
     }
-    // without Lambda*: the record kernels (FP32 or FP64) into the
-    // replicated Jrep, folded after
+    // without Lambda*: the record kernels (FP32, FP64 or float-float) into
+    // the replicated Jrep, folded after
     const bool sfast = !with_lstar;
     if (!sfast) CK(cudaMemsetAsync(g->Jfs, 0, sizeof(double) * g->N, g->stream));
     if (with_lstar) CK(cudaMemsetAsync(g->lstar, 0, sizeof(double) * 27 * g->N, g->stream));
@@ -479,9 +479,9 @@ rt3d_status run_fs_sph(rt3d_grid *g, const FsParams &base, const void *chiS, int
         // kernel of chunk c - 2 has released the slot, and the kernel of
         // chunk c waits for its copy; the mapped mode reads the chunk in
         // place; the chords mode reads the records on the device and
-        // streams the FP64 chords, which only the FP64 kernel reads.
-        // (In the mapped and chords modes cp.len64 is never read by the
-        // FP32 kernels.)
+        // streams the FP64 chords, which only the FP64 and float-float
+        // kernels read (fp64 here covers both; the FP32 kernels never read
+        // cp.len64).
         const bool chords = g->cache == RT3D_CACHE_HOST_CHORDS;
         const bool copy = g->cache == RT3D_CACHE_HOST_STREAMED || (chords && fp64);
         // without copies the chunks' kernels alternate between the grid's
