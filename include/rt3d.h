@@ -310,8 +310,9 @@ rt3d_status rt3d_grid_template(const rt3d_grid *grid, int angle, int *K, int32_t
 /* One characteristic of the spherical grid's cache: ray `index` (0-based) of
  * solid angle `angle`: points K (in/out capacity), cells vox[K], FP64 chords
  * len[K], the voxel that launched it, and its boundary kind (0 outer sphere,
- * 1 outer sphere irradiated, 2 core). Host memory. Returns RT3D_EINVAL past
- * the last ray of the angle. */
+ * 1 outer sphere irradiated, 2 core). Host memory. The same in every cache
+ * residency (RT3D_CACHE_*). Returns RT3D_EINVAL past the last ray of the
+ * angle. */
 rt3d_status rt3d_grid_sph_ray(const rt3d_grid *grid, int angle, int index, int *K, int32_t *vox,
                               double *len, int *launch, int *kind);
 
